@@ -1,0 +1,114 @@
+"""Independent restatements used only to pin the loop oracle (test infrastructure).
+
+Nothing here shares code with paircorr_ref.c: the distance bins are recomputed
+from a threshold table, and the pair sums are obtained by different algorithms:
+
+* lattice_fft_corr  -- on (periodic or open) lattices the ordered-pair sum over a
+  bin equals a sum over displacement vectors d of the lattice cross-correlation
+  X_d(t) = sum_i sum_{s,t0,a} S_{i,a}(t0+t) S_{i+d,a}(t0), evaluated with FFTs in
+  space and time (FP64).  This is the momentum-space route the paper mentions for
+  periodic lattices (Section 1, Section 3 opening paragraph).
+* separable_phase_sum -- the phase form of Eq. 3 with Eq. 6 factorises through
+  cos(a-b) = cos a cos b + sin a sin b into per-site transforms
+  F^c(q,f) = sum_i cos(q.r_i) S_i(f), F^s likewise (a non-uniform DFT), so
+  sum_ij cos(q.(r_i-r_j)) G_ij(t) = sum_{s,t0,a} F^c(t0+t) F^c(t0) + F^s(t0+t) F^s(t0).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def bins_from_thresholds(d2, w, n_bins):
+    """bin = number of k in 1..n_bins with (k w)^2 <= d2 (>= n_bins means dropped)."""
+    thr = (np.arange(1, n_bins + 1, dtype=np.float64) * w) ** 2
+    return np.searchsorted(thr, np.asarray(d2, np.float64), side="right")
+
+
+def _grid(traj, coords, L):
+    """Scatter a [N][S][F][3] trajectory onto a dense [S][F][3][Lz][Ly][Lx] grid."""
+    N, S, F, _ = traj.shape
+    Lx, Ly, Lz = (int(v) for v in L)
+    g = np.zeros((S, F, 3, Lz, Ly, Lx), np.float64)
+    g[:, :, :, coords[:, 2], coords[:, 1], coords[:, 0]] = np.transpose(traj, (1, 2, 3, 0))
+    return g
+
+
+def lattice_fft_corr(traj, T0, t_list, coords, L, periodic, w, n_bins):
+    """Binned C_sum[t][b] on a full lattice via FFT cross-correlation (FP64)."""
+    tr = np.asarray(traj, np.float64)
+    if tr.ndim == 3:
+        tr = tr[:, None]
+    N, S, F, _ = tr.shape
+    Lx, Ly, Lz = (int(v) for v in L)
+    assert N == Lx * Ly * Lz, "FFT check needs every lattice point occupied"
+    pad = (Lz, Ly, Lx) if periodic else tuple(2 * v if v > 1 else 1 for v in (Lz, Ly, Lx))
+    g = _grid(tr, coords, L)
+    # spatial transform of every frame
+    G = np.fft.fftn(g, s=pad, axes=(3, 4, 5))          # [S][F][3][pz][py][px]
+    t_list = np.atleast_1d(t_list)
+    # temporal cross-correlation sum_{t0<T0} conj(G(t0+t)) G(t0) for each t, via FFT in f
+    nf = 1
+    while nf < F + T0:
+        nf *= 2
+    A = np.fft.fft(G, n=nf, axis=1)
+    Bt = G.copy()
+    Bt[:, T0:] = 0.0
+    B = np.fft.fft(Bt, n=nf, axis=1)
+    # corr[t] = sum_t0 conj(G[t0+t]) G[t0]  ->  ifft(conj(A) * B) at lag -t ... use explicit form:
+    # sum_t0 conj(a[t0+t]) b[t0] = ifft(A * conj(B))[t]^*  (for lag t >= 0)
+    Xhat = np.fft.ifft(A * np.conj(B), axis=1)          # [S][nf][3][...]: sum_t0 a[t0+t] conj(b[t0])
+    Xhat = Xhat[:, t_list].sum(axis=(0, 2))               # [n_t][pz][py][px], a = G, b = G
+    # Xhat[t](k) = sum_{s,t0,a} G_k(t0+t) conj(G_k(t0)).  Spatially,
+    # X_d = sum_x a(x) b(x+d) = (1/V) sum_k conj(A_k) B_k e^{ikd}
+    X = np.fft.ifftn(np.conj(Xhat), axes=(1, 2, 3)).real  # [n_t][pz][py][px]
+    # displacement vectors of every grid offset and their squared distance
+    dz, dy, dx = np.meshgrid(np.arange(pad[0]), np.arange(pad[1]), np.arange(pad[2]), indexing="ij")
+    comps = []
+    for d, Lv, P in ((dx, Lx, pad[2]), (dy, Ly, pad[1]), (dz, Lz, pad[0])):
+        if periodic:
+            comps.append(np.minimum(d, Lv - d))
+        else:
+            comps.append(np.where(d < P - d, d, P - d))   # signed offset magnitude for open grids
+    d2 = comps[0] ** 2 + comps[1] ** 2 + comps[2] ** 2
+    b = bins_from_thresholds(d2, w, n_bins)
+    out = np.zeros((len(t_list), n_bins))
+    for k in range(n_bins):
+        m = b == k
+        if m.any():
+            out[:, k] = X[:, m].sum(axis=1)
+    return out
+
+
+def separable_phase_sum(traj, T0, t_list, pos, q, center=False):
+    """Sq_sum[t][q] = sum_ij cos(q.(r_i-r_j)) G_ij(t) through the factorised transform."""
+    tr = np.asarray(traj, np.float64)
+    if tr.ndim == 3:
+        tr = tr[:, None]
+    N, S, F, _ = tr.shape
+    r = np.asarray(pos, np.float64)
+    ph = r @ np.asarray(q, np.float64).T            # [N][n_q]
+    c, s = np.cos(ph), np.sin(ph)
+    t_list = np.atleast_1d(t_list)
+    out = np.zeros((len(t_list), len(q)))
+    B = tr[:, :, :T0]                               # [N][S][T0][3]
+    if center:
+        B = B - B.mean(axis=(1, 2), keepdims=True)
+    Fc_B = np.einsum("iq,isfa->qsfa", c, B)
+    Fs_B = np.einsum("iq,isfa->qsfa", s, B)
+    for k, t in enumerate(t_list):
+        A = tr[:, :, t:t + T0]
+        if center:
+            A = A - A.mean(axis=(1, 2), keepdims=True)
+        Fc_A = np.einsum("iq,isfa->qsfa", c, A)
+        Fs_A = np.einsum("iq,isfa->qsfa", s, A)
+        out[k] = (Fc_A * Fc_B).sum(axis=(1, 2, 3)) + (Fs_A * Fs_B).sum(axis=(1, 2, 3))
+    return out
+
+
+def total_moment_corr(traj, T0, t_list):
+    """q = 0 closed form: sum_ij G_ij(t) = sum_{s,t0} M(t0+t) . M(t0), M = sum_i S_i."""
+    tr = np.asarray(traj, np.float64)
+    if tr.ndim == 3:
+        tr = tr[:, None]
+    M = tr.sum(axis=0)                              # [S][F][3]
+    return np.array([(M[:, t:t + T0] * M[:, :T0]).sum() for t in np.atleast_1d(t_list)])
