@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused pair-correlation hot path on GB300.
+
+Workload (the throughput configuration): 40^3 periodic simple-cubic Heisenberg lattice,
+N = 64000, J = +1, thermalised at T = 1.2 J (Metropolis, adaptive cone); LL RK4 with
+dt = 0.01 and F = 1200 frames; C(r,t) over T0 = 1000 origins, n_t = 200 displacements,
+70 shell bins of width 0.5.  Contraction per displacement: N x N x 3*T0.
+
+One step = the hot path on one batch: LL trajectory from the resident thermalised spins
+(asd_ll_integrate), operand preparation + fused contraction/binning (asd_pair_corr in
+split-BF16) and normalisation (asd_pair_corr_normalize).
+Metric: algorithmic contraction TFLOP/s = n_t * 2 N^2 (3 T0) / step time.
+
+--impl reference runs the FP64 CPU oracle (the only reference this method has) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused pair-corr TFLOP/s & % tensor peak, split-BF16 vs FP32 at ≤1e-5 rel err"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="split_bf16", choices=["split_bf16", "bf16", "tf32", "fp32"])
+    ap.add_argument("--small", action="store_true", help="tiny workload (smoke / profiling)")
+    ap.add_argument("--no-extras", action="store_true", help="skip form sweep, CPU baseline, e2e")
+    ap.add_argument("--ncu", action="store_true", help="one step, nothing else (for ncu)")
+    return ap.parse_args()
+
+
+def workload(small):
+    from paper_2308_07487_gb300 import synth
+    if small:
+        lat = synth.hypercubic(16, 3, True, J=1.0, seed=23082)
+        return dict(name="sc16_periodic_N4096", lat=lat, F=160, T0=128, n_t=32, w=0.5, n_bins=28,
+                    T=1.2, sweeps=200, dt=0.01)
+    cfg = synth.cfg_cubic40()
+    return dict(name=cfg.name, lat=cfg.lattice, F=cfg.F, T0=cfg.T0, n_t=cfg.n_t, w=cfg.w,
+                n_bins=cfg.n_bins, T=cfg.T, sweeps=2000, dt=0.01)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 7:
+                self.samples.append(p)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[3 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample of the same workload
+# -------------------------------------------------------------------------------------
+def oracle_sample(W, tr_np, rows, t_list):
+    import oracle
+    geo = oracle.Geometry.of_lattice(W["lat"])
+    t0 = time.perf_counter()
+    res = oracle.pair_corr(tr_np, W["T0"], t_list, geo, W["w"], W["n_bins"], rows=rows)
+    dt = time.perf_counter() - t0
+    N = W["lat"].n_sites
+    flops = 2.0 * (rows[1] - rows[0]) * N * len(t_list) * 3 * W["T0"]
+    return res, dt, flops
+
+
+def run_reference(args, W, ws, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_2308_07487_gb300 import synth
+    N = W["lat"].n_sites
+    tr = synth.traj_precess(N, W["F"], seed=23082)
+    rows, t_list = (0, 8), [0, W["n_t"] // 2, W["n_t"] - 1]
+    if args.small:
+        rows = (0, 256)
+    oracle_sample(W, tr, (0, 1), [0])  # warm the OpenMP pool
+    times, flops = [], 0.0
+    for _ in range(args.warmup):
+        oracle_sample(W, tr, rows, t_list)
+    for _ in range(args.steps):
+        _, dt, flops = oracle_sample(W, tr, rows, t_list)
+        times.append(dt)
+    t = max(times)
+    v = flops / t / 1e12
+    cores = os.cpu_count()
+    sample = f"rows {rows[0]}..{rows[1]} x all {N} columns x t in {t_list} (K = {3 * W['T0']})"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": W["name"], "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    np.asarray(0)
+
+
+# -------------------------------------------------------------------------------------
+# our arm
+# -------------------------------------------------------------------------------------
+def run_ours(args, W, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2308_07487_gb300 import asd, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    lat = W["lat"]
+    N, F, T0, n_t, nb = lat.n_sites, W["F"], W["T0"], W["n_t"], W["n_bins"]
+    K = 3 * T0
+    flops_step = 2.0 * N * N * K * n_t              # algorithmic, per step
+    mult = {"split_bf16": 3, "bf16": 1, "tf32": 1, "fp32": 1}[args.form]
+
+    # ---- inputs: thermalised start (off the timed region) ----
+    sysm = asd.System(lat)
+    spins0 = torch.from_numpy(synth.random_unit(N, 23082 + rank)[None]).to(dev)
+    sysm.thermalize(spins0, W["T"], W["sweeps"], asd.ASD_METROPOLIS, cone=0.0, adapt=True,
+                    seed=23082 + rank)
+    traj = torch.empty((N, 1, F, 3), dtype=torch.float32, device=dev)
+    plan = asd.CorrPlan.for_lattice(lat, F, T0, n_t, W["w"], nb, precision=args.form)
+    C_sum = torch.zeros((n_t, nb), dtype=torch.float64, device=dev)
+    C = torch.zeros_like(C_sum)
+    def new_event():
+        return torch.cuda.Event(enable_timing=True)
+
+    def step(kernel_events=None):
+        """One pass of the hot path; kernel_events (start, end) bracket the contraction
+        kernel on the stream it is launched on."""
+        sysm.ll_integrate(spins0, W["dt"], F, 1, traj, stream=stream)
+        C_sum.zero_()
+        plan.prepare(traj, stream=stream)
+        if kernel_events is not None:
+            kernel_events[0].record(stream)
+        plan.contract(C_sum, stream=stream)
+        if kernel_events is not None:
+            kernel_events[1].record(stream)
+        plan.normalize(C_sum, None, C, None, stream=stream)
+
+    if args.ncu:
+        step()
+        asd.check(asd.sync_status(stream), "step")
+        return
+
+    for _ in range(args.warmup):
+        step()
+    asd.check(asd.sync_status(stream), "warmup")
+
+    ktimes = []
+    t_start, t_end = new_event(), new_event()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t_start.record(stream)
+        for _ in range(args.steps):
+            pair = (new_event(), new_event())
+            step(pair)
+            ktimes.append(pair)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    asd.check(asd.sync_status(stream), "timed steps")
+    t_step = t_start.elapsed_time(t_end) / 1e3 / args.steps
+    t_step = allmax(ws, t_step)
+    t_kernel = sum(a.elapsed_time(b) for a, b in ktimes) / 1e3 / len(ktimes)
+    clocks = clk.summary()
+    value = flops_step * ws / t_step / 1e12
+
+    pk, pk_kind = peaks()
+    if args.form == "fp32":
+        peak, bound, punit = None, "alu", "TFLOP/s"
+    else:
+        # a kernel timed inside a seconds-long step: the sustained BF16 figure; TF32 at the
+        # nominal dense ratio 1.1/2.25 of BF16
+        peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25 if args.form == "tf32" else 1.0)
+        bound, punit = "tensor", "TFLOP/s"
+    achieved = flops_step * mult / t_kernel / 1e12
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
+            "frac": (achieved / peak) if peak else None, "traffic": None,
+            "peak_source": f"{pk_kind} bf16_tflops_sustained" if peak else None,
+            "kernel": "pc_tc_kernel" if args.form != "fp32" else "simt_kernel",
+            "flops_per_launch": flops_step * mult,
+            "algorithmic_tflops": flops_step / t_kernel / 1e12,
+            "kernel_ms": t_kernel * 1e3}
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{args.form}_{W['name']}.txt")
+    if os.path.exists(tfile):
+        for line in open(tfile):
+            if line.startswith("dram_bytes_per_launch:"):
+                roof["traffic"] = float(line.split(":")[1])
+
+    out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"split_bf16": "bf16x3", "bf16": "bf16", "tf32": "tf32", "fp32": "f32"}[args.form],
+           "data": "synthetic",
+           "config": {"workload": W["name"], "N": N, "F": F, "T0": T0, "n_t": n_t, "n_bins": nb,
+                      "bin_width": W["w"], "K": K, "form": args.form,
+                      "parallelism": f"replicas x{ws}",
+                      "l2": "inputs larger than L2 (operand copies "
+                            f"{plan.workspace_bytes() / 1e9:.1f} GB)"},
+           "roofline": roof, "clocks": clocks,
+           # per step: LL frame 0 + 4 RK4 stages per step, prep B + prep A copies, the fused
+           # contraction, normalisation (the memset of C_sum is torch's)
+           "gpu_launches": args.steps * (1 + 4 * (F - 1) + (1 if args.form == "fp32" else 2) + 1 + 1)}
+
+    # ---- extras: other forms on a sample, CPU oracle baseline + parity, e2e ----
+    if not args.no_extras and rank == 0:
+        nt_s = min(8, n_t)
+        tr_np = None
+        forms = {}
+        for form in ("fp32", "tf32", "bf16", "split_bf16"):
+            p2 = asd.CorrPlan.for_lattice(lat, F, T0, nt_s, W["w"], nb, precision=form)
+            c2 = torch.zeros((nt_s, nb), dtype=torch.float64, device=dev)
+            p2.prepare(traj, stream=stream)
+            p2.contract(c2, stream=stream)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p2.contract(c2, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            dt = a.elapsed_time(b) / 1e3
+            forms[form] = {"TFLOP/s": 2.0 * N * N * K * nt_s / dt / 1e12,
+                           "sample": f"{nt_s} displacements"}
+            p2.close()
+        out["forms"] = forms
+        out["speedup_split_bf16_vs_fp32"] = forms["split_bf16"]["TFLOP/s"] / forms["fp32"]["TFLOP/s"]
+
+        # CPU oracle on rows 0..R, three displacements, and the per-bin error of the timed form
+        rows = (0, 8) if not args.small else (0, 256)
+        t_list = [0, n_t // 2, n_t - 1]
+        tr_np = traj.cpu().numpy()
+        res, dt, fl = oracle_sample(W, tr_np, rows, t_list)
+        import oracle
+        cs = torch.zeros((n_t, nb), dtype=torch.float64, device=dev)
+        plan.prepare(traj, rows=rows, stream=stream)
+        plan.contract(cs, rows=rows, stream=stream)
+        torch.cuda.synchronize()
+        err = oracle.bin_error(cs.cpu().numpy()[t_list], res).max()
+        out["cpu_baseline"] = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": f"rows {rows[0]}..{rows[1]} x {N} columns x t {t_list}, "
+                                         f"K={K}, {dt:.1f} s"}
+        out["max_bin_err"] = float(err)
+
+        # e2e through the public API: pinned host spins -> device, full step, C -> host
+        h_in = torch.from_numpy(spins0.cpu().numpy()).pin_memory()
+        h_out = torch.empty((n_t, nb), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            spins0.copy_(h_in, non_blocking=True)
+            step()
+            h_out.copy_(C, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        te = a.elapsed_time(b) / 1e3 / args.steps
+        out["e2e"] = {"value": flops_step / te / 1e12, "unit": "TFLOP/s",
+                      "h2d_bytes_per_step": int(h_in.numel() * 4),
+                      "d2h_bytes_per_step": int(h_out.numel() * 8),
+                      "wall_s_per_step": (time.perf_counter() - t0) / args.steps}
+        _ = np
+    if rank == 0:
+        print(json.dumps(out))
+    plan.close()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    W = workload(args.small)
+    if args.impl == "reference":
+        run_reference(args, W, ws, rank)
+    else:
+        run_ours(args, W, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

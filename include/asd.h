@@ -1,0 +1,239 @@
+/*
+ * asd.h -- C ABI of the GB300 spin-dynamics pair-correlation library.
+ *
+ * Method: arXiv 2308.07487, "Kernel Fusion in Atomistic Spin Dynamics Simulations
+ * on Nvidia GPUs using Tensor Core".  The library evaluates the space- and
+ * time-displaced spin pair correlation (Eq. 4 / Eq. 5), reduced over distance bins
+ * or weighted by the phase factors of Eq. 6 (the real part of Eq. 3), as one fused
+ * tensor-core contraction per time displacement (Sections 3.2-3.4) whose N x N
+ * result is never written to memory.
+ *
+ * Conventions for every entry point
+ *  - Pointers marked "device" are CUDA device pointers owned by the caller; "host"
+ *    pointers are read during the call only.  Nothing is retained except by plans.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue work
+ *    on it and return without synchronising unless stated otherwise.
+ *  - Return value: ASD_OK (0) or a negative ASD_E* code.  Arguments are validated on
+ *    the host before anything is launched; on ASD_EINVAL nothing was enqueued.
+ *    ASD_ECUDA keeps the CUDA error text for asd_strerror().  A bounded device-side
+ *    wait that gave up is reported as ASD_ETIMEOUT by asd_sync_status().
+ *  - Units: the device is the current CUDA device of the calling thread.
+ */
+#ifndef ASD_H
+#define ASD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASD_ABI_VERSION 1
+
+enum asd_status {
+    ASD_OK = 0,
+    ASD_EINVAL = -1,       /* bad shape or argument; nothing launched            */
+    ASD_ENOMEM = -2,       /* device or host allocation failed                   */
+    ASD_ECUDA = -3,        /* a CUDA runtime/driver call failed                  */
+    ASD_ETIMEOUT = -4,     /* a bounded device wait gave up (device error word)  */
+    ASD_EUNSUPPORTED = -5  /* valid request this build or device cannot serve    */
+};
+
+/* Precision forms of the contraction (the epilogue and bins are FP32 per tile,
+ * FP64 across tiles in every form). */
+enum asd_precision {
+    ASD_FP32 = 0,        /* FP32 FFMA on the CUDA cores (accuracy baseline)        */
+    ASD_TF32 = 1,        /* tcgen05 kind::tf32, operands pre-rounded to TF32       */
+    ASD_BF16 = 2,        /* tcgen05 kind::f16 with BF16 operands                   */
+    ASD_SPLIT_BF16 = 3   /* x = hi + lo in BF16; hi*hi + hi*lo + lo*hi per product */
+};
+
+enum asd_geometry {
+    ASD_GEOM_LATTICE = 0,   /* integer coordinates, optional minimum image        */
+    ASD_GEOM_POSITIONS = 1  /* FP32 Cartesian positions, no periodicity           */
+};
+
+/*
+ * Description of one correlation problem.
+ *
+ * Trajectory layout (device, FP32): traj[i][s][f][a] -- site i = 0..N-1, sample
+ * s = 0..S-1, frame f = 0..F-1, component a = 0..2; element offset
+ * ((i*S + s)*F + f)*3 + a.  Samples are concatenated along the contraction axis
+ * (the paper stacks its M Monte Carlo realisations the same way, Section 3.2).
+ *
+ * For displacement t = 0..n_t-1 the library forms, for every ordered pair (i,j),
+ *   G_ij(t) = sum_{s, t0 < T0, a} A_{i,s,a}(t0 + t) * B_{j,s,a}(t0)
+ * with A = B = S (center = 0) or with both operands centred by their mean over
+ * (s, t0) (center = 1, Eq. 5).  Requires T0 + n_t - 1 <= F.
+ *
+ * Distance bins (n_bins > 0): bin(i,j) = max{k >= 0 : (k*w)^2 <= d2(i,j)}, pairs with
+ * bin >= n_bins dropped.  d2 is the exact integer squared displacement of the
+ * integer coordinates (lattice; minimum image per axis when periodic) or the FP32
+ * value fmaf(dz,dz,fmaf(dy,dy,dx*dx)) with dx = x_j - x_i in FP32 (positions).
+ * Phase weights (n_q > 0): cos(q.(r_i - r_j)) with r = coords (lattice) or pos.
+ */
+typedef struct asd_corr_desc {
+    int64_t n_sites;        /* N >= 1                                                  */
+    int32_t n_frames;       /* F                                                       */
+    int32_t n_samples;      /* S >= 1                                                  */
+    int32_t T0;             /* time origins >= 1                                       */
+    int32_t n_t;            /* displacements >= 1                                      */
+    int32_t precision;      /* enum asd_precision                                      */
+    int32_t center;         /* 0 or 1                                                  */
+    int32_t geometry;       /* enum asd_geometry                                       */
+    int32_t L[3];           /* lattice extents (lattice geometry; 1 for unused axes)   */
+    int32_t periodic;       /* minimum image per axis (lattice geometry)               */
+    const int32_t *coords;  /* host [N][3], lattice geometry (required)                */
+    const float *pos;       /* host [N][3], positions geometry (required)              */
+    double bin_width;       /* w > 0 when n_bins > 0                                   */
+    int32_t n_bins;         /* 0 .. 4096                                               */
+    int32_t n_q;            /* 0 .. 256                                                */
+    const double *q;        /* host [n_q][3]                                           */
+    int32_t tile_n;         /* 0 = chosen by the autotuner, else 128 or 256 (tensor forms) */
+    int32_t reserved[7];    /* must be zero                                            */
+} asd_corr_desc;
+
+typedef struct asd_corr_plan asd_corr_plan;
+
+/*
+ * Build a plan: validates `d`, uploads geometry tables (bin thresholds, coordinates
+ * or positions, per-site cos/sin(q.r_i) tables), computes the exact ordered-pair
+ * count of every bin on the device, allocates the operand workspace (BF16 hi/lo or
+ * TF32 copies of the trajectory, zero-padded B operand) and encodes the TMA
+ * descriptors.  Synchronises the device.  The plan owns all of it.
+ * Errors: ASD_EINVAL (shape/argument), ASD_ENOMEM, ASD_ECUDA, ASD_EUNSUPPORTED
+ * (tensor-core form requested on a device without tcgen05).
+ */
+int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **plan);
+
+/* Free a plan (synchronises the device).  NULL is a no-op. */
+void asd_pair_corr_plan_destroy(asd_corr_plan *plan);
+
+/* Bytes of device workspace the plan holds. */
+int64_t asd_pair_corr_workspace_bytes(const asd_corr_plan *plan);
+
+/* Exact ordered-pair count of every bin over all N x N pairs (host [n_bins]). */
+int asd_pair_corr_counts(const asd_corr_plan *plan, int64_t *counts);
+
+/*
+ * The hot path (Sections 3.2-3.4): prepares the operands from `traj` and runs the
+ * fused contraction + epilogue for rows i in [row_begin, row_end) against every
+ * column j, for every displacement t.  Accumulates (+=) into
+ *   C_sum  device FP64 [n_t][n_bins]: sum over pairs in bin b of G_ij(t)
+ *   Sq_sum device FP64 [n_t][n_q]:    sum over pairs of cos(q.(r_i-r_j)) G_ij(t)
+ * The caller zeroes them; row ranges therefore compose (the row split of the
+ * paper's Section 3.5).  Either output may be NULL when its count is 0.
+ * traj: device FP32 [N][S][F][3], 16-byte aligned.
+ */
+int asd_pair_corr(asd_corr_plan *plan, const float *traj, int64_t row_begin, int64_t row_end,
+                  double *C_sum, double *Sq_sum, void *stream);
+
+/*
+ * The two halves of asd_pair_corr.  _prepare builds the operands (the paper's per-step
+ * rearrangement and centring, Section 3.2 / Eq. 5) for rows [row_begin, row_end) into
+ * the plan's workspace and remembers `traj` (which must stay valid until the last
+ * _contract that uses it).  _contract runs the fused contraction + epilogue for any row
+ * range inside the last prepared one (ASD_EINVAL otherwise), accumulating like
+ * asd_pair_corr.
+ */
+int asd_pair_corr_prepare(asd_corr_plan *plan, const float *traj, int64_t row_begin,
+                          int64_t row_end, void *stream);
+int asd_pair_corr_contract(asd_corr_plan *plan, int64_t row_begin, int64_t row_end,
+                           double *C_sum, double *Sq_sum, void *stream);
+
+/*
+ * Several independent problems (each its own plan, trajectory and outputs) in ONE
+ * persistent launch over a flattened (problem, t, tile) work list.  All plans must
+ * use the same tensor-core precision and the same tile width.  Operand preparation
+ * for every problem is enqueued first on the same stream.  Capturable into a CUDA
+ * graph (no host synchronisation, no allocation).
+ */
+int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs, int n,
+                          double *const *C_sum, double *const *Sq_sum, void *stream);
+
+/*
+ * Eq. 3 / Eq. 4 normalisation (device buffers, may alias their inputs):
+ *   C[t][b]  = C_sum[t][b] / (S*T0*n_b)   (0 where n_b = 0)
+ *   Sq[t][q] = Sq_sum[t][q] / (N*S*T0)
+ * Either pair of pointers may be NULL.
+ */
+int asd_pair_corr_normalize(const asd_corr_plan *plan, const double *C_sum, const double *Sq_sum,
+                            double *C, double *Sq, void *stream);
+
+/* Synchronise `stream` and report (then clear) the device error word:
+ * ASD_OK, ASD_ETIMEOUT or ASD_ECUDA. */
+int asd_sync_status(void *stream);
+
+/* Static text for a status code (ASD_ECUDA includes the last CUDA error). */
+const char *asd_strerror(int status);
+
+/* -------------------------------------------------------------------------------
+ * Producers of the trajectory: Monte Carlo sampling (Section 2.1) and
+ * Landau-Lifshitz dynamics (Eq. 2, Algorithm 1, RK4 as in Section 3.1).
+ * ------------------------------------------------------------------------------- */
+
+/*
+ * Spin system for the producers: H = sum_<ij> J_ij S_i.S_j - Hz sum_i S^z_i
+ * (Eq. 1 without DM and anisotropy).  Each undirected bond appears in both
+ * endpoints' neighbour lists with the same J.
+ */
+typedef struct asd_system {
+    int64_t n_sites;              /* N                                               */
+    int32_t z;                    /* neighbour slots per site (1..32)                 */
+    const int32_t *nbr;           /* device [N][z], -1 = empty slot                   */
+    const float *J;               /* device [N][z]                                    */
+    float Hz;                     /* field along z                                    */
+    int32_t n_colors;             /* independent-set colouring for parallel updates   */
+    const int32_t *color_sites;   /* device: sites of colour 0, then colour 1, ...    */
+    const int64_t *color_offsets; /* host [n_colors+1] offsets into color_sites       */
+} asd_system;
+
+/*
+ * Landau-Lifshitz dynamics dS_i/dt = (dH/dS_i) x S_i (Eq. 2), classic RK4 without
+ * renormalisation (Section 3.1), for S samples at once.
+ *   spins0 device [S][N][3]; traj device [N][S][n_frames][3]: frame 0 = spins0,
+ *   frame f = state after f*stride steps of size dt.  spins_out (device [S][N][3],
+ *   nullable) receives the final state.  Enqueues 4 kernels per step.
+ */
+int asd_ll_integrate(const asd_system *sys, int n_samples, const float *spins0, float dt,
+                     int n_frames, int stride, float *traj, float *spins_out, void *stream);
+
+enum asd_proposal {
+    ASD_METROPOLIS = 0,  /* uniform on the sphere, or a cone about the old spin       */
+    ASD_HEATBATH = 1,    /* exact conditional: von Mises-Fisher about -h             */
+    ASD_LEARNED = 2      /* MLP-proposed von Mises-Fisher + Metropolis-Hastings       */
+};
+
+/* Small MLP that maps a site's neighbour spins to a von Mises-Fisher proposal
+ * (mean direction, concentration).  Weights are device BF16, row-major [out][in]. */
+typedef struct asd_mlp {
+    int32_t n_in, n_hidden;       /* n_in = 3 * z                                     */
+    const uint16_t *W1, *W2, *W3; /* device bf16 [H][n_in], [H][H], [4][H]            */
+    const float *b1, *b2, *b3;    /* device fp32 [H], [H], [4]                        */
+} asd_mlp;
+
+typedef struct asd_mc_stats {
+    int64_t proposed;
+    int64_t accepted;
+    float cone;                   /* final cone half-angle (Metropolis)               */
+} asd_mc_stats;
+
+/*
+ * Checkerboard Monte Carlo (Section 2.1) at temperature T for S samples
+ * (spins device [S][N][3], updated in place), n_sweeps sweeps over all colours.
+ * Random numbers: Philox4x32-10 keyed by `seed`, counter (counter + sweep, site,
+ * colour); or, when `uniforms` (device [n_sweeps][S][N][4] FP32 in [0,1)) is given,
+ * exactly those numbers.  `cone` (radians, <= 0 = whole sphere) is the initial
+ * trial-cone half-angle; with adapt != 0 it is rescaled after every sweep to keep the
+ * acceptance near 0.5 and never below 0.2.  `stats` (host, nullable) synchronises
+ * the stream and returns the totals.
+ */
+int asd_thermalize(const asd_system *sys, int n_samples, float *spins, float T, int n_sweeps,
+                   int proposal, const asd_mlp *net, float cone, int adapt, uint64_t seed,
+                   uint64_t counter, const float *uniforms, asd_mc_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASD_H */

@@ -53,7 +53,7 @@ def _load():
             lib.oracle_pair_corr.argtypes = [i64, i64, i64, i64, i64, i32p, f32p, ctypes.c_int,
                                              i32p, i32p, ctypes.c_int, f32p, ctypes.c_double, i64,
                                              i64, f64p, ctypes.c_int, i64, i64, f64p, f64p, f64p,
-                                             i64p]
+                                             f64p, i64p]
             lib.oracle_pair_corr_eq4.restype = ctypes.c_int
             lib.oracle_pair_corr_eq4.argtypes = [i64, i64, i64, i64, i64, i32p, f32p, ctypes.c_int,
                                                  i32p, i32p, ctypes.c_int, f32p, ctypes.c_double,
@@ -121,6 +121,7 @@ def pair_corr(traj, T0, t_list, geometry: Geometry, w, n_bins, q=None, center=Fa
     i0, i1 = (0, N) if rows is None else rows
     C = np.zeros((n_tl, n_bins))
     M = np.zeros((n_tl, n_bins))
+    P = np.zeros((n_tl, n_bins))
     Sq = np.zeros((n_tl, max(n_q, 1)))
     cnt = np.zeros(n_bins, np.int64)
     g = geometry
@@ -129,10 +130,11 @@ def pair_corr(traj, T0, t_list, geometry: Geometry, w, n_bins, q=None, center=Fa
                               int(g.periodic), _p(g.pos, ctypes.c_float), float(w), n_bins, n_q,
                               _p(qq, ctypes.c_double), int(bool(center)), i0, i1,
                               _p(C, ctypes.c_double), _p(M, ctypes.c_double),
-                              _p(Sq, ctypes.c_double), _p(cnt, ctypes.c_int64))
+                              _p(P, ctypes.c_double), _p(Sq, ctypes.c_double),
+                              _p(cnt, ctypes.c_int64))
     if rc != 0:
         raise ValueError(f"oracle_pair_corr rejected its arguments (code {rc})")
-    return {"C_sum": C, "M_abs": M, "Sq_sum": Sq[:, :n_q], "counts": cnt,
+    return {"C_sum": C, "M_abs": M, "P_abs": P, "Sq_sum": Sq[:, :n_q], "counts": cnt,
             "N": N, "S": S, "T0": T0}
 
 
@@ -185,6 +187,14 @@ def normalize(res):
         C = np.where(n > 0, res["C_sum"] / (S * T0 * np.maximum(n, 1)), 0.0)
     Sq = res["Sq_sum"] / (N * S * T0)
     return C, Sq
+
+
+def rounding_ratio(C_sum_test, res):
+    """|C_test - C_ref| / P_abs per bin: the error in units of the sum of absolute
+    products, the quantity every rounding-error bound of the contraction scales with."""
+    d = np.abs(np.asarray(C_sum_test, np.float64) - res["C_sum"])
+    P = res["P_abs"]
+    return np.where(P > 0, d / np.where(P > 0, P, 1.0), d)
 
 
 def bin_error(C_sum_test, res):

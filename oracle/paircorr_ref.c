@@ -21,6 +21,8 @@
  *   C_sum[t][b] = sum over ordered pairs (i,j), i == j included, with bin(i,j) == b, of
  *                 G_ij(t) = sum_{s,t0,a} A_{i,s,a}(t0+t) * B_{j,s,a}(t0)
  *   M_abs[t][b] = sum over the same pairs of |G_ij(t)|   (scale of the bin, for errors)
+ *   P_abs[t][b] = sum over the same pairs of sum_{s,t0,a} |A * B|  (the scale of any
+ *                 rounding-error bound of the sum: |fl(G) - G| <= c u sum |A B|)
  *   counts[b]   = number of such ordered pairs
  * A = B = S (center = 0), or both centred by their origin/sample means (center = 1,
  * Eq. 5).  The normalised correlation is C(b,t) = C_sum / (S*T0*counts).
@@ -119,7 +121,8 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
                      const float *pos, double w, int64_t n_bins,
                      int64_t n_q, const double *q, int center,
                      int64_t row_begin, int64_t row_end,
-                     double *C_sum, double *M_abs, double *Sq_sum, int64_t *counts)
+                     double *C_sum, double *M_abs, double *P_abs, double *Sq_sum,
+                     int64_t *counts)
 {
     if (row_begin < 0 || row_end > N || row_begin > row_end) return -1;
     for (int64_t k = 0; k < n_tl; ++k)
@@ -128,6 +131,7 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
     const int64_t nc = n_tl * n_bins, nq = n_tl * n_q;
     memset(C_sum, 0, sizeof(double) * (size_t)nc);
     memset(M_abs, 0, sizeof(double) * (size_t)nc);
+    if (P_abs) memset(P_abs, 0, sizeof(double) * (size_t)nc);
     if (Sq_sum) memset(Sq_sum, 0, sizeof(double) * (size_t)nq);
     if (counts) memset(counts, 0, sizeof(int64_t) * (size_t)n_bins);
 
@@ -153,10 +157,11 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
     {
         double *c_loc = (double *)calloc((size_t)nc, sizeof(double));
         double *m_loc = (double *)calloc((size_t)nc, sizeof(double));
+        double *p_loc = (double *)calloc((size_t)nc, sizeof(double));
         double *q_loc = (double *)calloc((size_t)(nq > 0 ? nq : 1), sizeof(double));
         int64_t *n_loc = (int64_t *)calloc((size_t)n_bins, sizeof(int64_t));
         double *ph = (double *)calloc((size_t)(n_q > 0 ? n_q : 1), sizeof(double));
-        if (!c_loc || !m_loc || !q_loc || !n_loc || !ph) err = 1;
+        if (!c_loc || !m_loc || !p_loc || !q_loc || !n_loc || !ph) err = 1;
 #pragma omp for schedule(dynamic, 1)
         for (int64_t i = row_begin; i < row_end; ++i) {
             if (err) continue;
@@ -176,7 +181,7 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
                 }
                 for (int64_t k = 0; k < n_tl; ++k) {
                     const int64_t t = t_list[k];
-                    double g = 0.0;
+                    double g = 0.0, gabs = 0.0;
                     for (int64_t s = 0; s < S; ++s)
                         for (int64_t t0 = 0; t0 < T0; ++t0)
                             for (int a = 0; a < 3; ++a) {
@@ -187,10 +192,12 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
                                     y -= mB[3 * j + a];
                                 }
                                 g += x * y;
+                                gabs += fabs(x * y);
                             }
                     if (binned) {
                         c_loc[k * n_bins + b] += g;
                         m_loc[k * n_bins + b] += fabs(g);
+                        p_loc[k * n_bins + b] += gabs;
                     }
                     for (int64_t iq = 0; iq < n_q; ++iq) q_loc[k * n_q + iq] += ph[iq] * g;
                 }
@@ -198,13 +205,17 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
         }
 #pragma omp critical
         {
-            if (c_loc && m_loc && q_loc && n_loc) {
-                for (int64_t x = 0; x < nc; ++x) { C_sum[x] += c_loc[x]; M_abs[x] += m_loc[x]; }
+            if (c_loc && m_loc && p_loc && q_loc && n_loc) {
+                for (int64_t x = 0; x < nc; ++x) {
+                    C_sum[x] += c_loc[x];
+                    M_abs[x] += m_loc[x];
+                    if (P_abs) P_abs[x] += p_loc[x];
+                }
                 if (Sq_sum) for (int64_t x = 0; x < nq; ++x) Sq_sum[x] += q_loc[x];
                 if (counts) for (int64_t b = 0; b < n_bins; ++b) counts[b] += n_loc[b];
             }
         }
-        free(c_loc); free(m_loc); free(q_loc); free(n_loc); free(ph);
+        free(c_loc); free(m_loc); free(p_loc); free(q_loc); free(n_loc); free(ph);
     }
 #undef TR
     free(mA);

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of the C ABI in include/asd.h (argument marshalling only).
+
+Every computation runs in libasd.so.  Importing this module loads the library and
+raises ImportError if it has not been built (``python -m paper_2308_07487_gb300.build``
+or ``__graft_entry__.build()``): there is no fallback path.
+Device pointers are passed as integers (e.g. ``tensor.data_ptr()``); streams as
+``torch.cuda.current_stream().cuda_stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_SO = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libasd.so")
+if not os.path.exists(_SO):
+    raise ImportError(f"libasd.so not built ({_SO}); run paper_2308_07487_gb300/build.py")
+lib = ctypes.CDLL(_SO)
+
+ASD_OK, ASD_EINVAL, ASD_ENOMEM, ASD_ECUDA, ASD_ETIMEOUT, ASD_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+ASD_FP32, ASD_TF32, ASD_BF16, ASD_SPLIT_BF16 = 0, 1, 2, 3
+PRECISIONS = {"fp32": ASD_FP32, "tf32": ASD_TF32, "bf16": ASD_BF16, "split_bf16": ASD_SPLIT_BF16}
+ASD_GEOM_LATTICE, ASD_GEOM_POSITIONS = 0, 1
+ASD_METROPOLIS, ASD_HEATBATH, ASD_LEARNED = 0, 1, 2
+
+c_i32p = ctypes.POINTER(ctypes.c_int32)
+c_f32p = ctypes.POINTER(ctypes.c_float)
+c_f64p = ctypes.POINTER(ctypes.c_double)
+c_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class asd_corr_desc(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int64), ("n_frames", ctypes.c_int32),
+                ("n_samples", ctypes.c_int32), ("T0", ctypes.c_int32), ("n_t", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("center", ctypes.c_int32),
+                ("geometry", ctypes.c_int32), ("L", ctypes.c_int32 * 3),
+                ("periodic", ctypes.c_int32), ("coords", c_i32p), ("pos", c_f32p),
+                ("bin_width", ctypes.c_double), ("n_bins", ctypes.c_int32),
+                ("n_q", ctypes.c_int32), ("q", c_f64p), ("tile_n", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class asd_system(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int64), ("z", ctypes.c_int32), ("nbr", ctypes.c_void_p),
+                ("J", ctypes.c_void_p), ("Hz", ctypes.c_float), ("n_colors", ctypes.c_int32),
+                ("color_sites", ctypes.c_void_p), ("color_offsets", c_i64p)]
+
+
+class asd_mlp(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
+                ("W1", ctypes.c_void_p), ("W2", ctypes.c_void_p), ("W3", ctypes.c_void_p),
+                ("b1", ctypes.c_void_p), ("b2", ctypes.c_void_p), ("b3", ctypes.c_void_p)]
+
+
+class asd_mc_stats(ctypes.Structure):
+    _fields_ = [("proposed", ctypes.c_int64), ("accepted", ctypes.c_int64),
+                ("cone", ctypes.c_float)]
+
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "asd_pair_corr_plan_create": (ctypes.c_int, [ctypes.POINTER(asd_corr_desc), ctypes.POINTER(_VP)]),
+    "asd_pair_corr_plan_destroy": (None, [_VP]),
+    "asd_pair_corr_workspace_bytes": (ctypes.c_int64, [_VP]),
+    "asd_pair_corr_counts": (ctypes.c_int, [_VP, c_i64p]),
+    "asd_pair_corr": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP]),
+    "asd_pair_corr_prepare": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP]),
+    "asd_pair_corr_contract": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP]),
+    "asd_pair_corr_batched": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int,
+                                             ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    "asd_pair_corr_normalize": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "asd_sync_status": (ctypes.c_int, [_VP]),
+    "asd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "asd_ll_integrate": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP, ctypes.c_float,
+                                        ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "asd_thermalize": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP, ctypes.c_float,
+                                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(asd_mlp),
+                                      ctypes.c_float, ctypes.c_int, ctypes.c_uint64,
+                                      ctypes.c_uint64, _VP, ctypes.POINTER(asd_mc_stats), _VP]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name, None)
+    if _f is None:
+        continue
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class AsdError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {lib.asd_strerror(status).decode()} (status {status})")
+
+
+def check(status, where="asd"):
+    if status != ASD_OK:
+        raise AsdError(status, where)
+    return status
+
+
+def strerror(status: int) -> str:
+    return lib.asd_strerror(status).decode()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class CorrPlan:
+    """Owns an asd_corr_plan.  Geometry arrays are host numpy arrays."""
+
+    def __init__(self, N, F, T0, n_t, precision="split_bf16", S=1, center=False, coords=None,
+                 L=(1, 1, 1), periodic=False, pos=None, bin_width=1.0, n_bins=0, q=None,
+                 tile_n=0):
+        d = asd_corr_desc()
+        d.n_sites, d.n_frames, d.n_samples, d.T0, d.n_t = N, F, S, T0, n_t
+        d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        d.center = int(bool(center))
+        self._keep = []
+        if coords is not None and pos is None:
+            d.geometry = ASD_GEOM_LATTICE
+            c = np.ascontiguousarray(coords, np.int32)
+            self._keep.append(c)
+            d.coords = c.ctypes.data_as(c_i32p)
+        else:
+            d.geometry = ASD_GEOM_POSITIONS
+            p = np.ascontiguousarray(pos, np.float32)
+            self._keep.append(p)
+            d.pos = p.ctypes.data_as(c_f32p)
+        for a in range(3):
+            d.L[a] = int(L[a])
+        d.periodic = int(bool(periodic))
+        d.bin_width = float(bin_width)
+        d.n_bins = int(n_bins)
+        if q is not None and len(q) > 0:
+            qq = np.ascontiguousarray(q, np.float64)
+            self._keep.append(qq)
+            d.n_q = qq.shape[0]
+            d.q = qq.ctypes.data_as(c_f64p)
+        d.tile_n = int(tile_n)
+        self.desc = d
+        self.N, self.F, self.S, self.T0, self.n_t = N, F, S, T0, n_t
+        self.n_bins, self.n_q = int(n_bins), int(d.n_q)
+        h = _VP()
+        check(lib.asd_pair_corr_plan_create(ctypes.byref(d), ctypes.byref(h)), "plan_create")
+        self.handle = h
+        self._keep = []
+
+    @classmethod
+    def for_lattice(cls, lat, F, T0, n_t, w, n_bins, precision="split_bf16", S=1, center=False,
+                    q=None, positions=None, tile_n=0):
+        """Plan for a synth.Lattice: integer-lattice geometry unless its positions are
+        jittered (then the FP32 position rule) or positions=True is forced."""
+        jittered = not np.array_equal(lat.pos, lat.coords.astype(np.float32))
+        if positions or (positions is None and jittered):
+            return cls(lat.n_sites, F, T0, n_t, precision, S, center, pos=lat.pos,
+                       bin_width=w, n_bins=n_bins, q=q, tile_n=tile_n)
+        return cls(lat.n_sites, F, T0, n_t, precision, S, center, coords=lat.coords, L=lat.L,
+                   periodic=lat.periodic, bin_width=w, n_bins=n_bins, q=q, tile_n=tile_n)
+
+    def counts(self):
+        out = np.zeros(max(self.n_bins, 1), np.int64)
+        check(lib.asd_pair_corr_counts(self.handle, out.ctypes.data_as(c_i64p)), "counts")
+        return out[: self.n_bins]
+
+    def workspace_bytes(self):
+        return int(lib.asd_pair_corr_workspace_bytes(self.handle))
+
+    def run(self, traj, C_sum=None, Sq_sum=None, rows=None, stream=None):
+        r0, r1 = (0, self.N) if rows is None else rows
+        check(lib.asd_pair_corr(self.handle, _ptr(traj), r0, r1, _ptr(C_sum), _ptr(Sq_sum),
+                                _stream(stream)), "pair_corr")
+
+    def prepare(self, traj, rows=None, stream=None):
+        r0, r1 = (0, self.N) if rows is None else rows
+        check(lib.asd_pair_corr_prepare(self.handle, _ptr(traj), r0, r1, _stream(stream)),
+              "pair_corr_prepare")
+
+    def contract(self, C_sum=None, Sq_sum=None, rows=None, stream=None):
+        r0, r1 = (0, self.N) if rows is None else rows
+        check(lib.asd_pair_corr_contract(self.handle, r0, r1, _ptr(C_sum), _ptr(Sq_sum),
+                                         _stream(stream)), "pair_corr_contract")
+
+    def normalize(self, C_sum=None, Sq_sum=None, C=None, Sq=None, stream=None):
+        check(lib.asd_pair_corr_normalize(self.handle, _ptr(C_sum), _ptr(Sq_sum), _ptr(C), _ptr(Sq),
+                                          _stream(stream)), "normalize")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.asd_pair_corr_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pair_corr_batched(plans, trajs, C_sums, Sq_sums=None, stream=None):
+    n = len(plans)
+    P = (_VP * n)(*[p.handle.value for p in plans])
+    T = (_VP * n)(*[_ptr(t) for t in trajs])
+    C = (_VP * n)(*[_ptr(c) for c in C_sums])
+    Q = (_VP * n)(*[_ptr(q) for q in Sq_sums]) if Sq_sums is not None else None
+    check(lib.asd_pair_corr_batched(P, T, n, C, Q, _stream(stream)), "pair_corr_batched")
+
+
+def sync_status(stream=None):
+    return lib.asd_sync_status(_stream(stream))
+
+
+class System:
+    """asd_system for a synth.Lattice: neighbour table, couplings and colouring are
+    copied to the device (torch tensors kept alive by this object)."""
+
+    def __init__(self, lat, device="cuda"):
+        import torch
+        self.lat = lat
+        self.nbr = torch.from_numpy(np.ascontiguousarray(lat.nbr, np.int32)).to(device)
+        self.J = torch.from_numpy(np.ascontiguousarray(lat.J, np.float32)).to(device)
+        cs = np.concatenate(lat.colors).astype(np.int32)
+        self.color_sites = torch.from_numpy(cs).to(device)
+        self.offsets = np.cumsum([0] + [len(c) for c in lat.colors]).astype(np.int64)
+        s = asd_system()
+        s.n_sites = lat.n_sites
+        s.z = lat.nbr.shape[1]
+        s.nbr = self.nbr.data_ptr()
+        s.J = self.J.data_ptr()
+        s.Hz = float(lat.Hz)
+        s.n_colors = len(lat.colors)
+        s.color_sites = self.color_sites.data_ptr()
+        s.color_offsets = self.offsets.ctypes.data_as(c_i64p)
+        self.c = s
+
+    def ll_integrate(self, spins0, dt, n_frames, stride, traj, spins_out=None, stream=None):
+        S = spins0.shape[0] if spins0.dim() == 3 else 1
+        check(lib.asd_ll_integrate(ctypes.byref(self.c), S, _ptr(spins0), float(dt), int(n_frames),
+                                   int(stride), _ptr(traj), _ptr(spins_out), _stream(stream)),
+              "ll_integrate")
+
+    def thermalize(self, spins, T, n_sweeps, proposal=ASD_METROPOLIS, net=None, cone=0.0,
+                   adapt=False, seed=0, counter=0, uniforms=None, stats=False, stream=None):
+        S = spins.shape[0] if spins.dim() == 3 else 1
+        st = asd_mc_stats() if stats else None
+        check(lib.asd_thermalize(ctypes.byref(self.c), S, _ptr(spins), float(T), int(n_sweeps),
+                                 int(proposal), ctypes.byref(net.c) if net is not None else None,
+                                 float(cone), int(bool(adapt)), int(seed), int(counter),
+                                 _ptr(uniforms), ctypes.byref(st) if st is not None else None,
+                                 _stream(stream)), "thermalize")
+        return (st.proposed, st.accepted, st.cone) if st is not None else None
+
+
+def exported_symbols():
+    return list(_SIGS)

@@ -1,0 +1,162 @@
+// Internal declarations of the GB300 pair-correlation library (not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/asd.h"
+
+namespace asd {
+
+// ----------------------------------------------------------------------------------
+// status handling
+// ----------------------------------------------------------------------------------
+void set_cuda_error(cudaError_t e, const char *where);
+void set_error_text(const std::string &s);
+
+#define ASD_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) {                             \
+            ::asd::set_cuda_error(_e, #expr);                \
+            return ASD_ECUDA;                                \
+        }                                                    \
+    } while (0)
+
+#define ASD_CHECK_ARG(cond, msg)                             \
+    do {                                                     \
+        if (!(cond)) {                                       \
+            ::asd::set_error_text(msg);                      \
+            return ASD_EINVAL;                               \
+        }                                                    \
+    } while (0)
+
+// Device error word (one per device, module scope): bounded waits write a code here.
+enum DeviceError : int { DEV_OK = 0, DEV_TIMEOUT_TMA = 1, DEV_TIMEOUT_MMA = 2, DEV_TIMEOUT_EPI = 3 };
+int *device_error_word();          // device address of the word for the current device
+
+// ----------------------------------------------------------------------------------
+// tensor-core operand layout
+// ----------------------------------------------------------------------------------
+constexpr int kBM = 128;            // rows (sites i) per tile = TMEM lanes
+constexpr int kMaxCopies = 8;       // shifted operand copies (16-byte TMA start rule)
+constexpr int kMaxProblems = 4096;  // batched work list
+constexpr size_t kMinSmem = 120 * 1024;  // tensor-core kernel: one CTA per SM
+
+// Epilogue geometry + output parameters of one problem (device-visible POD).
+struct EpiParams {
+    int geom;               // ASD_GEOM_*
+    int Lx, Ly, Lz;
+    int periodic;
+    float inv_w;
+    int n_bins;
+    int NW;                 // private bins held per thread (window width)
+    int use_window;         // 1: window start derived from per-tile boxes
+    int n_q;
+    const int4 *coords;     // [N] (x,y,z,0)
+    const float4 *pos;      // [N] (x,y,z,0)
+    const float *thr;       // [n_bins+2]: FP32 thresholds (k*w)^2 rounded up; thr[0]=0
+    const float4 *box_lo;   // [n_tiles_m_all] lower corner of each 128-row block (window mode)
+    const float4 *box_hi;
+    const float4 *cbox_lo;  // [n_tiles_n] column blocks
+    const float4 *cbox_hi;
+    const float2 *cs;       // [N][n_q] (cos, sin)(q.r_i)
+    double *C_sum;          // [n_t][n_bins]
+    double *Sq_sum;         // [n_t][n_q]
+};
+
+// One problem of the (possibly batched) tensor-core launch.
+struct TcProblem {
+    CUtensorMap mapA[2][kMaxCopies];  // [plane][copy]
+    CUtensorMap mapB[2];              // [plane]
+    int64_t tile_begin;               // first flattened tile of this problem
+    int64_t n_tiles;                  // n_t * tiles_m * tiles_n
+    int N;                            // columns (sites)
+    int row_begin, row_end;
+    int tiles_m, tiles_n;
+    int n_t;
+    int S;
+    int F3;                           // 3*F: sample stride inside a trajectory row
+    int Kseg;                         // B segment per sample (multiple of BK)
+    int nkb;                          // K blocks per sample
+    int n_copies;                     // shifted copies (8 for BF16, 4 for TF32)
+    int group_m;                      // raster group height (row tiles)
+    EpiParams epi;
+};
+
+// Per-launch override of a single problem's row range and outputs (lets the device
+// copy of the descriptor be uploaded once per plan).
+struct TcOverride {
+    int active;
+    int row_begin, row_end, tiles_m;
+    int64_t n_tiles;
+    double *C_sum;
+    double *Sq_sum;
+};
+
+}  // namespace asd
+
+// Opaque plan (global namespace, forward-declared in asd.h).
+struct asd_corr_plan {
+    asd_corr_desc d;
+    int device;
+    int sm_count;
+    int64_t N;
+    int S, F, T0, n_t, n_bins, n_q, prec, center;
+    int64_t R;                 // row length of the trajectory: S*3F
+    // tensor-core operands
+    int tc;                    // 1 for the tcgen05 forms
+    int n_planes;              // 1, or 2 for split-BF16
+    int n_copies;
+    int elem_bytes;
+    int BK;                    // K elements per pipeline stage
+    int swizzle_bytes;         // 128 or 64
+    int BN;                    // tile width (columns)
+    int64_t Rpad;              // row length of an A copy (elements)
+    int64_t Kseg;              // B elements per sample (3*T0 rounded up to BK)
+    int64_t Kb;                // B row length S*Kseg
+    void *ws;                  // one allocation for everything below
+    size_t ws_bytes;
+    void *A[2][asd::kMaxCopies];
+    void *B[2];
+    float *Bf32;               // FP32 form: B operand
+    float *meanB;              // [N][3] centring means
+    // geometry (device)
+    int4 *coords;
+    float4 *pos;
+    float *thr;
+    float4 *box;               // [2][tiles_m_all] row-block boxes, then [2][tiles_n] column boxes
+    float2 *cs;
+    int tiles_m_all, tiles_n;
+    int use_window;
+    int NW;
+    int64_t *counts_h;
+    double *inv_counts;        // device [n_bins]: 1/(S*T0*n_b), 0 for empty bins
+    // single-problem descriptor (tensor forms): host copy + device copy uploaded once
+    asd::TcProblem *d_prob;
+    asd::TcProblem *h_prob;
+    int stages;
+    size_t smem_bytes;
+    // last asd_pair_corr_prepare
+    const float *prepared_traj;
+    int64_t prepared_begin, prepared_end;
+};
+
+namespace asd {
+// prep.cu
+int launch_prep(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t row_end,
+                cudaStream_t s);
+int launch_counts(asd_corr_plan *p, cudaStream_t s, unsigned long long *d_counts);
+// pc_simt.cu
+int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t row_end,
+                double *C_sum, double *Sq_sum, cudaStream_t s);
+// pc_tc.cu
+int tc_configure(asd_corr_plan *p);    // stages / smem for the plan's form
+int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
+              int BN, int swizzle_bytes, int stages, size_t smem, int max_nw, int max_nb,
+              int max_nq, int sm_count, cudaStream_t s);
+size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN);
+}  // namespace asd

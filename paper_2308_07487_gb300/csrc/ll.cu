@@ -1,0 +1,146 @@
+// Landau-Lifshitz dynamics (Eq. 2): dS_i/dt = (dH/dS_i) x S_i, classic RK4.
+//
+// H = sum_<ij> J_ij S_i.S_j - Hz sum_i S^z_i (Eq. 1 without DM / anisotropy), so the
+// local field is h_i = sum_j J_ij S_j - Hz z^.  As in Algorithm 1, one thread handles
+// one site and the S samples are processed by the same launch (the paper passes its
+// M configurations to one kernel, Section 3.1); the RK4 stages keep their derivative
+// in separate arrays so sites never race (Section 3.1).  No renormalisation: the paper
+// notes its RK4 evolution is not norm preserving.
+//
+// Each RK4 stage is one launch over (sample, site) -- a stage needs every neighbour's
+// previous stage.  The last stage writes the new state and, every `stride` steps, the
+// trajectory frame in the site-major layout traj[i][s][f][a] consumed by asd_pair_corr.
+#include "asd_internal.h"
+
+namespace asd {
+namespace {
+
+struct LLArgs {
+    int64_t N;
+    int S;
+    int z;
+    const int *nbr;
+    const float *J;
+    float Hz;
+};
+
+__device__ __forceinline__ float3 field(const LLArgs &a, const float *__restrict__ Y, int s,
+                                        int64_t i)
+{
+    const float *Ys = Y + (int64_t)s * a.N * 3;
+    float3 h = make_float3(0.f, 0.f, -a.Hz);
+    for (int k = 0; k < a.z; ++k) {
+        const int j = __ldg(a.nbr + i * a.z + k);
+        if (j < 0) continue;
+        const float Jij = __ldg(a.J + i * a.z + k);
+        h.x = fmaf(Jij, Ys[3 * (int64_t)j + 0], h.x);
+        h.y = fmaf(Jij, Ys[3 * (int64_t)j + 1], h.y);
+        h.z = fmaf(Jij, Ys[3 * (int64_t)j + 2], h.z);
+    }
+    return h;
+}
+
+__device__ __forceinline__ float3 cross(float3 a, float3 b)
+{
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// stage k (1..4): reads Yin (the stage input), writes the next stage input and the
+// running combination acc = k1 + 2 k2 + 2 k3.
+template <int STAGE>
+__global__ void rk4_stage(LLArgs a, float *__restrict__ Y, const float *__restrict__ Yin,
+                          float *__restrict__ Yout, float *__restrict__ acc, float dt, float *traj,
+                          int F, int frame)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.N * a.S) return;
+    const int s = (int)(g / a.N);
+    const int64_t i = g % a.N;
+    const int64_t o = (int64_t)s * a.N * 3 + 3 * i;
+    const float3 h = field(a, Yin, s, i);
+    const float3 x = make_float3(Yin[o], Yin[o + 1], Yin[o + 2]);
+    const float3 k = cross(h, x);
+    const float3 y = make_float3(Y[o], Y[o + 1], Y[o + 2]);
+    if (STAGE == 1) {
+        acc[o] = k.x; acc[o + 1] = k.y; acc[o + 2] = k.z;
+    } else if (STAGE < 4) {
+        acc[o] += 2.f * k.x; acc[o + 1] += 2.f * k.y; acc[o + 2] += 2.f * k.z;
+    }
+    if (STAGE < 4) {
+        const float c = STAGE == 3 ? dt : 0.5f * dt;
+        Yout[o] = fmaf(c, k.x, y.x);
+        Yout[o + 1] = fmaf(c, k.y, y.y);
+        Yout[o + 2] = fmaf(c, k.z, y.z);
+    } else {
+        const float c = dt / 6.f;
+        const float3 n = make_float3(fmaf(c, acc[o] + k.x, y.x), fmaf(c, acc[o + 1] + k.y, y.y),
+                                     fmaf(c, acc[o + 2] + k.z, y.z));
+        Y[o] = n.x; Y[o + 1] = n.y; Y[o + 2] = n.z;
+        if (frame >= 0) {
+            float *dst = traj + ((i * a.S + s) * (int64_t)F + frame) * 3;
+            dst[0] = n.x; dst[1] = n.y; dst[2] = n.z;
+        }
+    }
+}
+
+__global__ void write_frame0(const float *__restrict__ Y, int64_t N, int S, float *traj, int F)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N * S) return;
+    const int s = (int)(g / N);
+    const int64_t i = g % N;
+    const float *src = Y + (int64_t)s * N * 3 + 3 * i;
+    float *dst = traj + ((i * S + s) * (int64_t)F) * 3;
+    dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
+}
+
+}  // namespace
+}  // namespace asd
+
+using namespace asd;
+
+extern "C" int asd_ll_integrate(const asd_system *sys, int n_samples, const float *spins0,
+                                float dt, int n_frames, int stride, float *traj, float *spins_out,
+                                void *stream)
+{
+    ASD_CHECK_ARG(sys && spins0 && traj, "null argument");
+    ASD_CHECK_ARG(sys->n_sites >= 1 && sys->z >= 0 && sys->z <= 32, "bad system");
+    ASD_CHECK_ARG(sys->z == 0 || (sys->nbr && sys->J), "neighbour table required");
+    ASD_CHECK_ARG(n_samples >= 1 && n_frames >= 1 && stride >= 1, "bad n_samples/n_frames/stride");
+    cudaStream_t s = (cudaStream_t)stream;
+    LLArgs a{sys->n_sites, n_samples, sys->z, sys->nbr, sys->J, sys->Hz};
+    const int64_t n = sys->n_sites * n_samples;
+    const size_t bytes = sizeof(float) * 3 * (size_t)n;
+    float *ws = nullptr;
+    ASD_CUDA_TRY(cudaMallocAsync(&ws, 4 * bytes, s));
+    float *Y = ws, *T1 = ws + 3 * n, *T2 = ws + 6 * n, *acc = ws + 9 * n;
+    int rc = ASD_OK;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    do {
+        if (cudaMemcpyAsync(Y, spins0, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            rc = ASD_ECUDA;
+            break;
+        }
+        write_frame0<<<blocks, 256, 0, s>>>(Y, sys->n_sites, n_samples, traj, n_frames);
+        for (int f = 1; f < n_frames; ++f) {
+            for (int k = 0; k < stride; ++k) {
+                const int frame = k == stride - 1 ? f : -1;
+                rk4_stage<1><<<blocks, 256, 0, s>>>(a, Y, Y, T1, acc, dt, traj, n_frames, -1);
+                rk4_stage<2><<<blocks, 256, 0, s>>>(a, Y, T1, T2, acc, dt, traj, n_frames, -1);
+                rk4_stage<3><<<blocks, 256, 0, s>>>(a, Y, T2, T1, acc, dt, traj, n_frames, -1);
+                rk4_stage<4><<<blocks, 256, 0, s>>>(a, Y, T1, nullptr, acc, dt, traj, n_frames,
+                                                    frame);
+            }
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            rc = ASD_ECUDA;
+            break;
+        }
+        if (spins_out &&
+            cudaMemcpyAsync(spins_out, Y, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            rc = ASD_ECUDA;
+    } while (0);
+    cudaFreeAsync(ws, s);
+    if (rc == ASD_ECUDA) set_error_text("asd_ll_integrate: launch failed");
+    return rc;
+}

@@ -1,0 +1,210 @@
+// FP32 form: the fused contraction + epilogue on the CUDA cores (FFMA).
+//
+// It is the accuracy and speed baseline of the tensor-core forms.  Each CTA owns a
+// 128 x 128 tile of G_t = A_t B^T for one displacement t (the paper's thread-block
+// tile, Section 3.3), accumulates it in registers (8 x 8 per thread), and reduces the
+// tile in place: distance bins through FP64 shared-memory atomics, phase weights
+// through cos(a-b) = cos a cos b + sin a sin b with warp shuffles (Section 3.3, the
+// shuffle + shared-memory + atomic reduction), then one FP64 global atomic per bin
+// (and per q) per tile.  A is read straight from the trajectory row at the K-offset
+// s*3F + 3t; B is the prepared, zero-padded FP32 copy.
+#include "asd_internal.h"
+#include "geom.cuh"
+
+namespace asd {
+namespace {
+
+constexpr int TM = 128, TN = 128, TK = 8;
+
+struct SimtParams {
+    const float *traj;
+    const float *B;
+    int64_t R;        // trajectory row length S*3F
+    int F3;
+    int K3;           // 3*T0
+    int Kseg;         // B segment per sample
+    int S;
+    int N;
+    int row_begin, row_end;
+    EpiParams e;
+};
+
+__global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
+{
+    __shared__ __align__(16) float As[2][TK][TM];
+    __shared__ __align__(16) float Bs[2][TK][TN];
+    extern __shared__ double red[];  // [n_bins] then [n_q]
+    double *sbins = red;
+    double *sq = red + P.e.n_bins;
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int t = blockIdx.z;
+    const int m0 = P.row_begin + blockIdx.x * TM;
+    const int n0 = blockIdx.y * TN;
+    for (int k = tid; k < P.e.n_bins + P.e.n_q; k += 256) red[k] = 0.0;
+
+    // loader mapping: one row (or column) and 4 consecutive k per thread
+    const int lr = tid >> 1, lk = (tid & 1) * 4;
+    const int li = m0 + lr, lj = n0 + lr;
+    const bool a_ok = li < P.row_end;
+    const bool b_ok = lj < P.N;
+    const float *arow = P.traj + (int64_t)(a_ok ? li : 0) * P.R + 3 * t;
+    const float *brow = P.B + (int64_t)(b_ok ? lj : 0) * P.S * P.Kseg;
+
+    const int steps_per_seg = P.Kseg / TK;
+    const int n_steps = P.S * steps_per_seg;
+    float ra[4], rb[4];
+    auto load = [&](int st) {
+        const int s = st / steps_per_seg;
+        const int kl = (st % steps_per_seg) * TK + lk;
+        const float *ap = arow + (int64_t)s * P.F3 + kl;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ra[u] = (a_ok && kl + u < P.K3) ? __ldg(ap + u) : 0.f;
+        float4 bv = b_ok ? __ldg(reinterpret_cast<const float4 *>(brow + (int64_t)s * P.Kseg + kl))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        rb[0] = bv.x; rb[1] = bv.y; rb[2] = bv.z; rb[3] = bv.w;
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            As[buf][lk + u][lr] = ra[u];
+            Bs[buf][lk + u][lr] = rb[u];
+        }
+    };
+
+    float acc[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+
+    load(0);
+    store(0);
+    __syncthreads();
+    for (int st = 0; st < n_steps; ++st) {
+        const int buf = st & 1;
+        if (st + 1 < n_steps) load(st + 1);
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            float a[8], b[8];
+            float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+            float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+            float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+            float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+            a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+            a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+            b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+            b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        }
+        if (st + 1 < n_steps) store(buf ^ 1);
+        __syncthreads();
+    }
+
+    // ---------------- epilogue: reduce the tile ----------------
+    int ri[8], cj[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        ri[u] = m0 + (u < 4 ? ty * 4 + u : 64 + ty * 4 + u - 4);
+        cj[u] = n0 + (u < 4 ? tx * 4 + u : 64 + tx * 4 + u - 4);
+    }
+    const EpiParams &e = P.e;
+    if (e.n_bins > 0) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const bool rok = ri[r] < P.row_end;
+            const int ir = rok ? ri[r] : P.row_begin;
+            const int4 ci = e.coords[ir];
+            const float4 pi = e.pos[ir];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const bool ok = rok && cj[c] < P.N;
+                const int jc = cj[c] < P.N ? cj[c] : 0;
+                const float d2 = e.geom == ASD_GEOM_LATTICE
+                                     ? lattice_d2(ci, e.coords[jc], e.Lx, e.Ly, e.Lz, e.periodic)
+                                     : position_d2(pi, e.pos[jc]);
+                const int b = bin_of_d2(d2, e.inv_w, e.n_bins, e.thr);
+                if (ok && b < e.n_bins) atomicAdd(&sbins[b], (double)acc[r][c]);
+            }
+        }
+    }
+    if (e.n_q > 0) {
+        const int lane = tid & 31;
+        for (int q = 0; q < e.n_q; ++q) {
+            float part = 0.f;
+            float2 wc[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                wc[c] = cj[c] < P.N ? e.cs[(int64_t)cj[c] * e.n_q + q] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const float2 wr = ri[r] < P.row_end ? e.cs[(int64_t)ri[r] * e.n_q + q]
+                                                    : make_float2(0.f, 0.f);
+                float u = 0.f, v = 0.f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    u = fmaf(wc[c].x, acc[r][c], u);
+                    v = fmaf(wc[c].y, acc[r][c], v);
+                }
+                part = fmaf(wr.x, u, fmaf(wr.y, v, part));
+            }
+            double dp = part;
+            for (int o = 16; o > 0; o >>= 1) dp += __shfl_xor_sync(0xffffffffu, dp, o);
+            if (lane == 0) atomicAdd(&sq[q], dp);
+        }
+    }
+    __syncthreads();
+    for (int b = tid; b < e.n_bins; b += 256)
+        if (sbins[b] != 0.0) atomicAdd(&e.C_sum[(int64_t)t * e.n_bins + b], sbins[b]);
+    for (int q = tid; q < e.n_q; q += 256)
+        if (sq[q] != 0.0) atomicAdd(&e.Sq_sum[(int64_t)t * e.n_q + q], sq[q]);
+}
+
+}  // namespace
+
+int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t row_end,
+                double *C_sum, double *Sq_sum, cudaStream_t s)
+{
+    SimtParams P{};
+    P.traj = traj;
+    P.B = p->Bf32;
+    P.R = p->R;
+    P.F3 = 3 * p->F;
+    P.K3 = 3 * p->T0;
+    P.Kseg = (int)p->Kseg;
+    P.S = p->S;
+    P.N = (int)p->N;
+    P.row_begin = (int)row_begin;
+    P.row_end = (int)row_end;
+    EpiParams &e = P.e;
+    e.geom = p->d.geometry;
+    e.Lx = p->d.L[0];
+    e.Ly = p->d.L[1];
+    e.Lz = p->d.L[2];
+    e.periodic = p->d.periodic;
+    e.inv_w = p->n_bins > 0 ? (float)(1.0 / p->d.bin_width) : 1.f;
+    e.n_bins = p->n_bins;
+    e.n_q = p->n_q;
+    e.coords = p->coords;
+    e.pos = p->pos;
+    e.thr = p->thr;
+    e.cs = p->cs;
+    e.C_sum = C_sum;
+    e.Sq_sum = Sq_sum;
+    dim3 grid((unsigned)((row_end - row_begin + TM - 1) / TM), (unsigned)((p->N + TN - 1) / TN),
+              (unsigned)p->n_t);
+    if (grid.y > 65535u || grid.z > 65535u) {
+        set_error_text("FP32 form: grid too large (N or n_t)");
+        return ASD_EUNSUPPORTED;
+    }
+    size_t smem = sizeof(double) * (p->n_bins + p->n_q);
+    simt_kernel<<<grid, 256, smem, s>>>(P);
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}
+
+}  // namespace asd

@@ -1,0 +1,641 @@
+// Plan lifecycle, geometry tables, pair counts, dispatch and normalisation (C ABI).
+//
+// The method (arXiv 2308.07487, Sections 3.2-3.4): for each time displacement the
+// pair sum is one GEMM-shaped contraction A_t B^T over K = 3*T0 (x S samples) whose
+// N x N result is reduced in the kernel epilogue, either over distance bins or with
+// the phase weights of Eq. 6.  This file owns everything around the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "asd_internal.h"
+#include "geom.cuh"
+
+namespace asd {
+
+static thread_local std::string g_err_text;
+
+void set_cuda_error(cudaError_t e, const char *where)
+{
+    g_err_text = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e) + " (" + where + ")";
+}
+void set_error_text(const std::string &s) { g_err_text = s; }
+
+// One error word per device, at module scope.
+__device__ int g_device_error;
+
+int *device_error_word()
+{
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
+    return static_cast<int *>(p);
+}
+
+// ---------------------------------------------------------------------------------
+// pair counts: exact ordered-pair count of every bin over all N x N pairs
+// ---------------------------------------------------------------------------------
+__global__ void count_pairs_kernel(int64_t N, EpiParams e, unsigned long long *counts)
+{
+    extern __shared__ unsigned int hist[];
+    for (int b = threadIdx.x; b < e.n_bins; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const int64_t i = blockIdx.x;
+    if (i < N) {
+        for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+            float d2 = e.geom == ASD_GEOM_LATTICE
+                           ? lattice_d2(e.coords[i], e.coords[j], e.Lx, e.Ly, e.Lz, e.periodic)
+                           : position_d2(e.pos[i], e.pos[j]);
+            int b = bin_of_d2(d2, e.inv_w, e.n_bins, e.thr);
+            if (b < e.n_bins) atomicAdd(&hist[b], 1u);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < e.n_bins; b += blockDim.x)
+        if (hist[b]) atomicAdd(&counts[b], (unsigned long long)hist[b]);
+}
+
+__global__ void normalize_kernel(const double *C_sum, double *C, int n_t, int n_bins,
+                                 const double *inv_n, const double *Sq_sum, double *Sq, int n_q,
+                                 double inv_nq)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (C_sum && k < (int64_t)n_t * n_bins) C[k] = C_sum[k] * inv_n[k % n_bins];
+    if (Sq_sum && k < (int64_t)n_t * n_q) Sq[k] = Sq_sum[k] * inv_nq;
+}
+
+static EpiParams epi_of(const asd_corr_plan *p)
+{
+    EpiParams e{};
+    e.geom = p->d.geometry;
+    e.Lx = p->d.L[0];
+    e.Ly = p->d.L[1];
+    e.Lz = p->d.L[2];
+    e.periodic = p->d.periodic;
+    e.inv_w = p->n_bins > 0 ? (float)(1.0 / p->d.bin_width) : 1.0f;
+    e.n_bins = p->n_bins;
+    e.NW = p->NW;
+    e.use_window = p->use_window;
+    e.n_q = p->n_q;
+    e.coords = p->coords;
+    e.pos = p->pos;
+    e.thr = p->thr;
+    e.cs = p->cs;
+    return e;
+}
+
+static void carve(char *&cur, size_t bytes, void **out)
+{
+    *out = cur;
+    cur += (bytes + 255) & ~(size_t)255;
+}
+
+// Encode one 2D tiled tensor map through the driver entry point (no libcuda link).
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode()
+{
+    static PFN_encodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &ptr, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled>(ptr);
+    });
+    return fn;
+}
+
+static int encode_2d(CUtensorMap *m, void *base, int elem_bytes, uint64_t inner, uint64_t rows,
+                     uint32_t box_inner, uint32_t box_rows, int swizzle_bytes)
+{
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) {
+        set_error_text("cuTensorMapEncodeTiled unavailable");
+        return ASD_EUNSUPPORTED;
+    }
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {inner * (uint64_t)elem_bytes};
+    cuuint32_t box[2] = {box_inner, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                                 : CU_TENSOR_MAP_SWIZZLE_64B;
+    CUresult r = enc(m, dt, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        set_error_text(buf);
+        return ASD_ECUDA;
+    }
+    return ASD_OK;
+}
+
+static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int64_t row_end)
+{
+    memset(tp, 0, sizeof(*tp));
+    const int box_rows_b = p->BN;
+    for (int pl = 0; pl < p->n_planes; ++pl) {
+        for (int c = 0; c < p->n_copies; ++c) {
+            int rc = encode_2d(&tp->mapA[pl][c], p->A[pl][c], p->elem_bytes, (uint64_t)p->Rpad,
+                               (uint64_t)p->N, (uint32_t)p->BK, kBM, p->swizzle_bytes);
+            if (rc) return rc;
+        }
+        int rc = encode_2d(&tp->mapB[pl], p->B[pl], p->elem_bytes, (uint64_t)p->Kb, (uint64_t)p->N,
+                           (uint32_t)p->BK, (uint32_t)box_rows_b, p->swizzle_bytes);
+        if (rc) return rc;
+    }
+    tp->N = (int)p->N;
+    tp->row_begin = (int)row_begin;
+    tp->row_end = (int)row_end;
+    tp->tiles_m = (int)((row_end - row_begin + kBM - 1) / kBM);
+    tp->tiles_n = (int)((p->N + p->BN - 1) / p->BN);
+    tp->n_t = p->n_t;
+    tp->S = p->S;
+    tp->F3 = 3 * p->F;
+    tp->Kseg = (int)p->Kseg;
+    tp->nkb = (int)(p->Kseg / p->BK);
+    tp->n_copies = p->n_copies;
+    tp->group_m = 8;
+    tp->n_tiles = (int64_t)p->n_t * tp->tiles_m * tp->tiles_n;
+    tp->epi = epi_of(p);
+    return ASD_OK;
+}
+
+}  // namespace asd
+
+using namespace asd;
+
+extern "C" {
+
+const char *asd_strerror(int status)
+{
+    static thread_local std::string s;
+    const char *base = "unknown status";
+    switch (status) {
+    case ASD_OK: base = "ok"; break;
+    case ASD_EINVAL: base = "invalid argument"; break;
+    case ASD_ENOMEM: base = "out of memory"; break;
+    case ASD_ECUDA: base = "CUDA error"; break;
+    case ASD_ETIMEOUT: base = "bounded device wait timed out"; break;
+    case ASD_EUNSUPPORTED: base = "unsupported"; break;
+    }
+    s = base;
+    if (status != ASD_OK && !g_err_text.empty()) s += ": " + g_err_text;
+    return s.c_str();
+}
+
+int asd_sync_status(void *stream)
+{
+    ASD_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    int v = 0;
+    ASD_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_device_error, sizeof(int)));
+    if (v != 0) {
+        int zero = 0;
+        ASD_CUDA_TRY(cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int)));
+        char buf[96];
+        snprintf(buf, sizeof buf, "device error word = %d", v);
+        set_error_text(buf);
+        return ASD_ETIMEOUT;
+    }
+    return ASD_OK;
+}
+
+void asd_pair_corr_plan_destroy(asd_corr_plan *p)
+{
+    if (!p) return;
+    cudaDeviceSynchronize();
+    cudaFree(p->ws);
+    cudaFree(p->coords);
+    cudaFree(p->pos);
+    cudaFree(p->thr);
+    cudaFree(p->cs);
+    cudaFree(p->inv_counts);
+    cudaFree(p->d_prob);
+    delete p->h_prob;
+    delete[] p->counts_h;
+    delete p;
+}
+
+int64_t asd_pair_corr_workspace_bytes(const asd_corr_plan *p) { return p ? (int64_t)p->ws_bytes : 0; }
+
+int asd_pair_corr_counts(const asd_corr_plan *p, int64_t *counts)
+{
+    ASD_CHECK_ARG(p && counts, "null argument");
+    for (int b = 0; b < p->n_bins; ++b) counts[b] = p->counts_h[b];
+    return ASD_OK;
+}
+
+int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
+{
+    ASD_CHECK_ARG(d && out, "null argument");
+    *out = nullptr;
+    ASD_CHECK_ARG(d->n_sites >= 1 && d->n_sites < (1LL << 31) - 512, "n_sites out of range");
+    ASD_CHECK_ARG(d->n_samples >= 1 && d->T0 >= 1 && d->n_t >= 1, "S, T0, n_t must be >= 1");
+    ASD_CHECK_ARG((int64_t)d->T0 + d->n_t - 1 <= d->n_frames, "need T0 + n_t - 1 <= F");
+    ASD_CHECK_ARG(d->precision >= ASD_FP32 && d->precision <= ASD_SPLIT_BF16, "bad precision");
+    ASD_CHECK_ARG(d->center == 0 || d->center == 1, "center must be 0 or 1");
+    ASD_CHECK_ARG(d->geometry == ASD_GEOM_LATTICE || d->geometry == ASD_GEOM_POSITIONS,
+                  "bad geometry");
+    ASD_CHECK_ARG(d->n_bins >= 0 && d->n_bins <= 4096, "n_bins out of range [0,4096]");
+    ASD_CHECK_ARG(d->n_q >= 0 && d->n_q <= 256, "n_q out of range [0,256]");
+    ASD_CHECK_ARG(d->n_bins > 0 || d->n_q > 0, "nothing to compute (n_bins = n_q = 0)");
+    ASD_CHECK_ARG(d->n_bins == 0 || d->bin_width > 0, "bin_width must be > 0");
+    ASD_CHECK_ARG(d->n_q == 0 || d->q, "q required when n_q > 0");
+    ASD_CHECK_ARG(d->tile_n == 0 || d->tile_n == 128 || d->tile_n == 256, "tile_n: 0, 128, 256");
+    for (int k = 0; k < 7; ++k) ASD_CHECK_ARG(d->reserved[k] == 0, "reserved fields must be 0");
+    if (d->geometry == ASD_GEOM_LATTICE) {
+        ASD_CHECK_ARG(d->coords, "coords required for lattice geometry");
+        for (int a = 0; a < 3; ++a) ASD_CHECK_ARG(d->L[a] >= 1 && d->L[a] <= 1 << 20, "bad L");
+        for (int64_t i = 0; i < d->n_sites; ++i)
+            for (int a = 0; a < 3; ++a)
+                ASD_CHECK_ARG(d->coords[3 * i + a] >= 0 && d->coords[3 * i + a] < d->L[a],
+                              "coords outside [0, L)");
+    } else {
+        ASD_CHECK_ARG(d->pos, "pos required for positions geometry");
+    }
+    const int64_t R = (int64_t)d->n_samples * 3 * d->n_frames;
+    ASD_CHECK_ARG(d->n_sites * R < (1LL << 40), "trajectory too large");
+
+    int dev = 0;
+    ASD_CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    ASD_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    const bool tc = d->precision != ASD_FP32;
+    if (tc && !(prop.major == 10 || prop.major == 11)) {
+        set_error_text("tensor-core forms need a tcgen05 (sm_10x) device");
+        return ASD_EUNSUPPORTED;
+    }
+
+    asd_corr_plan *p = new (std::nothrow) asd_corr_plan();
+    if (!p) return ASD_ENOMEM;
+    memset(p, 0, sizeof(*p));
+    p->d = *d;
+    p->d.coords = nullptr;
+    p->d.pos = nullptr;
+    p->d.q = nullptr;
+    p->device = dev;
+    p->sm_count = prop.multiProcessorCount;
+    p->N = d->n_sites;
+    p->S = d->n_samples;
+    p->F = d->n_frames;
+    p->T0 = d->T0;
+    p->n_t = d->n_t;
+    p->n_bins = d->n_bins;
+    p->n_q = d->n_q;
+    p->prec = d->precision;
+    p->center = d->center;
+    p->R = R;
+    p->tc = tc;
+    p->counts_h = new (std::nothrow) int64_t[d->n_bins > 0 ? d->n_bins : 1];
+    if (!p->counts_h) {
+        delete p;
+        return ASD_ENOMEM;
+    }
+    int rc = ASD_OK;
+    auto fail = [&](int code) {
+        asd_pair_corr_plan_destroy(p);
+        return code;
+    };
+
+    // ---- operand layout ----
+    if (tc) {
+        p->n_planes = d->precision == ASD_SPLIT_BF16 ? 2 : 1;
+        p->elem_bytes = d->precision == ASD_TF32 ? 4 : 2;
+        p->n_copies = 16 / p->elem_bytes;
+        p->swizzle_bytes = d->precision == ASD_SPLIT_BF16 ? 64 : 128;
+        p->BK = p->swizzle_bytes / p->elem_bytes;
+        p->BN = d->tile_n ? d->tile_n : (p->N <= 4096 ? 128 : 256);
+        p->Rpad = (R + 7) / 8 * 8;
+        p->Kseg = ((int64_t)3 * d->T0 + p->BK - 1) / p->BK * p->BK;
+    } else {
+        p->Rpad = 0;
+        p->Kseg = ((int64_t)3 * d->T0 + 15) / 16 * 16;
+        p->BN = 128;
+    }
+    p->Kb = p->S * p->Kseg;
+
+    // ---- bins: private window per epilogue thread ----
+    if (tc) {
+        rc = tc_configure(p);
+        if (rc) return fail(rc);
+    }
+
+    // ---- workspace ----
+    size_t bytes = 0;
+    const size_t a_bytes = tc ? (size_t)p->N * p->Rpad * p->elem_bytes : 0;
+    const size_t b_bytes = (size_t)p->N * p->Kb * (tc ? p->elem_bytes : 4);
+    const size_t r256 = 256;
+    auto up = [&](size_t b) { return (b + r256 - 1) / r256 * r256; };
+    if (tc) bytes += p->n_planes * p->n_copies * up(a_bytes) + p->n_planes * up(b_bytes);
+    else bytes += up(b_bytes);
+    bytes += up((size_t)p->N * 3 * sizeof(float));  // centring means
+    if (cudaMalloc(&p->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error_text("workspace allocation failed");
+        return fail(ASD_ENOMEM);
+    }
+    p->ws_bytes = bytes;
+    {
+        char *cur = static_cast<char *>(p->ws);
+        if (tc) {
+            for (int pl = 0; pl < p->n_planes; ++pl)
+                for (int c = 0; c < p->n_copies; ++c) carve(cur, a_bytes, &p->A[pl][c]);
+            for (int pl = 0; pl < p->n_planes; ++pl) carve(cur, b_bytes, &p->B[pl]);
+        } else {
+            void *b = nullptr;
+            carve(cur, b_bytes, &b);
+            p->Bf32 = static_cast<float *>(b);
+        }
+        void *m = nullptr;
+        carve(cur, (size_t)p->N * 3 * sizeof(float), &m);
+        p->meanB = static_cast<float *>(m);
+    }
+
+    // ---- geometry tables ----
+    {
+        std::vector<int4> hc((size_t)p->N);
+        std::vector<float4> hp((size_t)p->N);
+        for (int64_t i = 0; i < p->N; ++i) {
+            if (d->geometry == ASD_GEOM_LATTICE) {
+                hc[i] = make_int4(d->coords[3 * i], d->coords[3 * i + 1], d->coords[3 * i + 2], 0);
+                hp[i] = make_float4((float)hc[i].x, (float)hc[i].y, (float)hc[i].z, 0.f);
+            } else {
+                hc[i] = make_int4(0, 0, 0, 0);
+                hp[i] = make_float4(d->pos[3 * i], d->pos[3 * i + 1], d->pos[3 * i + 2], 0.f);
+            }
+        }
+        if (cudaMalloc(&p->coords, sizeof(int4) * p->N) != cudaSuccess ||
+            cudaMalloc(&p->pos, sizeof(float4) * p->N) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ASD_ENOMEM);
+        }
+        if (cudaMemcpy(p->coords, hc.data(), sizeof(int4) * p->N, cudaMemcpyHostToDevice) ||
+            cudaMemcpy(p->pos, hp.data(), sizeof(float4) * p->N, cudaMemcpyHostToDevice))
+            return fail(ASD_ECUDA);
+        // thresholds (k*w)^2 in FP64, rounded up to FP32
+        const int nb = p->n_bins;
+        std::vector<float> thr(nb + 2);
+        thr[0] = 0.f;
+        for (int k = 1; k < nb + 2; ++k) {
+            double v = ((double)k * d->bin_width) * ((double)k * d->bin_width);
+            float f = (float)v;
+            if ((double)f < v) f = nextafterf(f, INFINITY);
+            thr[k] = f;
+        }
+        if (cudaMalloc(&p->thr, sizeof(float) * (nb + 2)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ASD_ENOMEM);
+        }
+        if (cudaMemcpy(p->thr, thr.data(), sizeof(float) * (nb + 2), cudaMemcpyHostToDevice))
+            return fail(ASD_ECUDA);
+        if (p->n_q > 0) {
+            std::vector<float2> cs((size_t)p->N * p->n_q);
+            for (int64_t i = 0; i < p->N; ++i) {
+                double r[3];
+                for (int a = 0; a < 3; ++a)
+                    r[a] = d->geometry == ASD_GEOM_LATTICE ? (double)d->coords[3 * i + a]
+                                                           : (double)d->pos[3 * i + a];
+                for (int q = 0; q < p->n_q; ++q) {
+                    double ph = d->q[3 * q] * r[0] + d->q[3 * q + 1] * r[1] + d->q[3 * q + 2] * r[2];
+                    cs[(size_t)i * p->n_q + q] = make_float2((float)cos(ph), (float)sin(ph));
+                }
+            }
+            if (cudaMalloc(&p->cs, sizeof(float2) * cs.size()) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ASD_ENOMEM);
+            }
+            if (cudaMemcpy(p->cs, cs.data(), sizeof(float2) * cs.size(), cudaMemcpyHostToDevice))
+                return fail(ASD_ECUDA);
+        }
+    }
+
+    // ---- exact pair counts ----
+    if (p->n_bins > 0) {
+        unsigned long long *dc = nullptr;
+        if (cudaMalloc(&dc, sizeof(unsigned long long) * p->n_bins) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ASD_ENOMEM);
+        }
+        rc = launch_counts(p, 0, dc);
+        if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = ASD_ECUDA;
+        if (!rc) {
+            std::vector<unsigned long long> hc(p->n_bins);
+            if (cudaMemcpy(hc.data(), dc, sizeof(unsigned long long) * p->n_bins,
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+                rc = ASD_ECUDA;
+            for (int b = 0; b < p->n_bins; ++b) p->counts_h[b] = (int64_t)hc[b];
+        }
+        cudaFree(dc);
+        if (rc) return fail(rc);
+        std::vector<double> inv(p->n_bins);
+        for (int b = 0; b < p->n_bins; ++b)
+            inv[b] = p->counts_h[b] > 0
+                         ? 1.0 / ((double)p->S * p->T0 * (double)p->counts_h[b]) : 0.0;
+        if (cudaMalloc(&p->inv_counts, sizeof(double) * p->n_bins) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ASD_ENOMEM);
+        }
+        if (cudaMemcpy(p->inv_counts, inv.data(), sizeof(double) * p->n_bins,
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(ASD_ECUDA);
+    }
+
+    // ---- tensor maps for the whole row range ----
+    if (tc) {
+        p->h_prob = new (std::nothrow) TcProblem;
+        if (!p->h_prob || cudaMalloc(&p->d_prob, sizeof(TcProblem)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ASD_ENOMEM);
+        }
+        rc = fill_problem(p, p->h_prob, 0, p->N);
+        if (rc) return fail(rc);
+        if (cudaMemcpy(p->d_prob, p->h_prob, sizeof(TcProblem), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return fail(ASD_ECUDA);
+    }
+    *out = p;
+    return ASD_OK;
+}
+
+int asd_pair_corr(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t row_end,
+                  double *C_sum, double *Sq_sum, void *stream)
+{
+    ASD_CHECK_ARG(p && traj, "null argument");
+    ASD_CHECK_ARG(0 <= row_begin && row_begin <= row_end && row_end <= p->N, "bad row range");
+    ASD_CHECK_ARG(p->n_bins == 0 || C_sum, "C_sum required when n_bins > 0");
+    ASD_CHECK_ARG(p->n_q == 0 || Sq_sum, "Sq_sum required when n_q > 0");
+    ASD_CHECK_ARG(((uintptr_t)traj & 15) == 0, "traj must be 16-byte aligned");
+    if (row_begin == row_end) return ASD_OK;
+    int rc = asd_pair_corr_prepare(p, traj, row_begin, row_end, stream);
+    if (rc) return rc;
+    return asd_pair_corr_contract(p, row_begin, row_end, C_sum, Sq_sum, stream);
+}
+
+int asd_pair_corr_prepare(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t row_end,
+                          void *stream)
+{
+    ASD_CHECK_ARG(p && traj, "null argument");
+    ASD_CHECK_ARG(0 <= row_begin && row_begin <= row_end && row_end <= p->N, "bad row range");
+    ASD_CHECK_ARG(((uintptr_t)traj & 15) == 0, "traj must be 16-byte aligned");
+    int rc = launch_prep(p, traj, row_begin, row_end, (cudaStream_t)stream);
+    if (rc) return rc;
+    p->prepared_traj = traj;
+    p->prepared_begin = row_begin;
+    p->prepared_end = row_end;
+    return ASD_OK;
+}
+
+int asd_pair_corr_contract(asd_corr_plan *p, int64_t row_begin, int64_t row_end, double *C_sum,
+                           double *Sq_sum, void *stream)
+{
+    ASD_CHECK_ARG(p, "null plan");
+    ASD_CHECK_ARG(p->prepared_traj, "asd_pair_corr_prepare has not been called");
+    ASD_CHECK_ARG(p->prepared_begin <= row_begin && row_begin <= row_end &&
+                      row_end <= p->prepared_end,
+                  "rows outside the prepared range");
+    ASD_CHECK_ARG(p->n_bins == 0 || C_sum, "C_sum required when n_bins > 0");
+    ASD_CHECK_ARG(p->n_q == 0 || Sq_sum, "Sq_sum required when n_q > 0");
+    if (row_begin == row_end) return ASD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!p->tc) return launch_simt(p, p->prepared_traj, row_begin, row_end, C_sum, Sq_sum, s);
+    TcOverride ov{};
+    ov.active = 1;
+    ov.row_begin = (int)row_begin;
+    ov.row_end = (int)row_end;
+    ov.tiles_m = (int)((row_end - row_begin + kBM - 1) / kBM);
+    ov.n_tiles = (int64_t)p->n_t * ov.tiles_m * p->h_prob->tiles_n;
+    ov.C_sum = C_sum;
+    ov.Sq_sum = Sq_sum;
+    return launch_tc(p->d_prob, 1, ov.n_tiles, ov, p->prec, p->BN, p->swizzle_bytes, p->stages,
+                     p->smem_bytes, p->NW, p->n_bins, p->n_q, p->sm_count, s);
+}
+
+int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs, int n,
+                          double *const *C_sum, double *const *Sq_sum, void *stream)
+{
+    ASD_CHECK_ARG(plans && trajs && n >= 1 && n <= kMaxProblems, "bad batch");
+    const asd_corr_plan *p0 = plans[0];
+    ASD_CHECK_ARG(p0 && p0->tc, "batched launch needs tensor-core plans");
+    int max_nw = 0, max_nb = 0, max_nq = 0, stages = 1 << 30;
+    size_t smem = 0;
+    for (int k = 0; k < n; ++k) {
+        const asd_corr_plan *p = plans[k];
+        ASD_CHECK_ARG(p && trajs[k], "null plan or trajectory");
+        ASD_CHECK_ARG(p->tc && p->prec == p0->prec && p->BN == p0->BN,
+                      "batched plans must share precision and tile width");
+        ASD_CHECK_ARG(p->device == p0->device, "plans on different devices");
+        ASD_CHECK_ARG(p->n_bins == 0 || (C_sum && C_sum[k]), "C_sum required");
+        ASD_CHECK_ARG(p->n_q == 0 || (Sq_sum && Sq_sum[k]), "Sq_sum required");
+        ASD_CHECK_ARG(((uintptr_t)trajs[k] & 15) == 0, "traj must be 16-byte aligned");
+        max_nw = p->NW > max_nw ? p->NW : max_nw;
+        max_nq = p->n_q > max_nq ? p->n_q : max_nq;
+        max_nb = p->n_bins > max_nb ? p->n_bins : max_nb;
+    }
+    // one smem configuration for the whole batch
+    {
+        size_t stage_bytes = (size_t)p0->n_planes * (kBM + p0->BN) * p0->swizzle_bytes;
+        size_t epi = 0;
+        for (int k = 0; k < n; ++k) {
+            (void)k;
+        }
+        epi = tc_epilogue_smem(max_nw, max_nb, max_nq, p0->BN);
+        const size_t cap = 232448 - 2048;
+        if (epi + 2 * stage_bytes > cap) {
+            set_error_text("batched epilogue does not fit shared memory");
+            return ASD_EUNSUPPORTED;
+        }
+        stages = (int)((cap - epi) / stage_bytes);
+        if (stages > 6) stages = 6;
+        smem = epi + stages * stage_bytes + 2048;
+        if (smem < kMinSmem) smem = kMinSmem;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // Work list: built on the host every call, uploaded only when it differs from the
+    // previous upload of this thread (the first call for a batch may synchronise and
+    // allocate; repeated identical calls only enqueue kernels, so they can be captured).
+    static thread_local std::vector<TcProblem> last;
+    static thread_local TcProblem *dbuf = nullptr;
+    static thread_local int cap_n = 0;
+    std::vector<TcProblem> h((size_t)n);
+    int64_t total = 0;
+    for (int k = 0; k < n; ++k) {
+        const asd_corr_plan *p = plans[k];
+        h[k] = *p->h_prob;
+        h[k].row_begin = 0;
+        h[k].row_end = (int)p->N;
+        h[k].tiles_m = (int)((p->N + kBM - 1) / kBM);
+        h[k].n_tiles = (int64_t)p->n_t * h[k].tiles_m * h[k].tiles_n;
+        h[k].tile_begin = total;
+        h[k].epi.C_sum = C_sum ? C_sum[k] : nullptr;
+        h[k].epi.Sq_sum = Sq_sum ? Sq_sum[k] : nullptr;
+        total += h[k].n_tiles;
+    }
+    const bool same = last.size() == h.size() &&
+                      memcmp(last.data(), h.data(), sizeof(TcProblem) * h.size()) == 0;
+    if (!same) {
+        if (cap_n < n) {
+            cudaFree(dbuf);
+            dbuf = nullptr;
+            cap_n = 0;
+            if (cudaMalloc(&dbuf, sizeof(TcProblem) * n) != cudaSuccess) {
+                cudaGetLastError();
+                return ASD_ENOMEM;
+            }
+            cap_n = n;
+        }
+        ASD_CUDA_TRY(cudaStreamSynchronize(s));
+        ASD_CUDA_TRY(cudaMemcpy(dbuf, h.data(), sizeof(TcProblem) * n, cudaMemcpyHostToDevice));
+        last = h;
+    }
+    for (int k = 0; k < n; ++k) {
+        int rc = launch_prep(plans[k], trajs[k], 0, plans[k]->N, s);
+        if (rc) return rc;
+    }
+    TcOverride ov{};
+    return launch_tc(dbuf, n, total, ov, p0->prec, p0->BN, p0->swizzle_bytes, stages, smem, max_nw,
+                     max_nb, max_nq, p0->sm_count, s);
+}
+
+int asd_pair_corr_normalize(const asd_corr_plan *p, const double *C_sum, const double *Sq_sum,
+                            double *C, double *Sq, void *stream)
+{
+    ASD_CHECK_ARG(p, "null plan");
+    ASD_CHECK_ARG((C_sum == nullptr) == (C == nullptr), "C_sum and C go together");
+    ASD_CHECK_ARG((Sq_sum == nullptr) == (Sq == nullptr), "Sq_sum and Sq go together");
+    if (!C_sum && !Sq_sum) return ASD_OK;
+    ASD_CHECK_ARG(!C_sum || p->n_bins > 0, "plan has no bins");
+    ASD_CHECK_ARG(!Sq_sum || p->n_q > 0, "plan has no q-vectors");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = std::max<int64_t>((int64_t)p->n_t * p->n_bins, (int64_t)p->n_t * p->n_q);
+    const double inv_nq = 1.0 / ((double)p->N * p->S * p->T0);
+    normalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        C_sum, C, p->n_t, p->n_bins, p->inv_counts, Sq_sum, Sq, p->n_q, inv_nq);
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}
+
+}  // extern "C"
+
+namespace asd {
+int launch_counts(asd_corr_plan *p, cudaStream_t s, unsigned long long *d_counts)
+{
+    ASD_CUDA_TRY(cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * p->n_bins, s));
+    EpiParams e = epi_of(p);
+    size_t sm = sizeof(unsigned int) * p->n_bins;
+    count_pairs_kernel<<<(unsigned)p->N, 256, sm, s>>>(p->N, e, d_counts);
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}
+}  // namespace asd

@@ -1,0 +1,151 @@
+"""GPU parity of asd_pair_corr (all precision forms) against the FP64 oracle.
+
+Tolerances (per-bin error scaled by the bin's magnitude sum, see oracle.bin_error):
+  FP32 and split-BF16: 1e-5 (the accuracy bar of the FP32-accurate forms);
+  TF32: 4 * 2^-11 and BF16: 4 * 2^-8 (a few units of the operand rounding, the
+  per-product error of a single rounded operand pair being <= 2u).
+Pair counts are integers and must match exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2308_07487_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "split_bf16": 1e-5, "tf32": 4 * 2.0 ** -11, "bf16": 4 * 2.0 ** -8}
+# Worst-case bound per unit of sum|A B| (first order): operand rounding of the form
+# (split: the dropped lo*lo and residual terms, 3 * 2^-16; TF32 / BF16: two roundings,
+# 2u) plus FP32 accumulation over K terms and the FP32 bin sums of one tile.
+U32 = 2.0 ** -24
+
+
+def elem_bound(form, K):
+    per = {"fp32": 0.0, "split_bf16": 3 * 2.0 ** -16, "tf32": 2 * 2.0 ** -11,
+           "bf16": 2 * 2.0 ** -8}[form]
+    return per + (K + 256) * U32
+FORMS = ["fp32", "split_bf16", "tf32", "bf16"]
+
+
+@pytest.fixture(scope="module")
+def asd():
+    from paper_2308_07487_gb300 import asd as m
+    return m
+
+
+def run_gpu(asd, lat, traj, T0, n_t, w, n_bins, form, center=False, q=None, rows=None,
+            tile_n=0, positions=None):
+    tr = np.ascontiguousarray(traj if traj.ndim == 4 else traj[:, None])
+    N, S, F, _ = tr.shape
+    plan = asd.CorrPlan.for_lattice(lat, F, T0, n_t, w, n_bins, precision=form, S=S,
+                                    center=center, q=q, positions=positions, tile_n=tile_n)
+    d_tr = torch.from_numpy(tr).cuda()
+    C = torch.zeros((n_t, max(n_bins, 1)), dtype=torch.float64, device="cuda")
+    nq = 0 if q is None else len(q)
+    Sq = torch.zeros((n_t, max(nq, 1)), dtype=torch.float64, device="cuda")
+    plan.run(d_tr, C if n_bins else None, Sq if nq else None, rows=rows)
+    assert asd.sync_status() == 0
+    out = {"C_sum": C.cpu().numpy()[:, :n_bins], "Sq_sum": Sq.cpu().numpy()[:, :nq],
+           "counts": plan.counts()}
+    plan.close()
+    return out
+
+
+def oracle_ref(lat, traj, T0, n_t, w, n_bins, center=False, q=None, rows=None, positions=None):
+    geo = oracle.Geometry.of_lattice(lat, use_positions=positions)
+    return oracle.pair_corr(traj, T0, list(range(n_t)), geo, w, n_bins, q=q, center=center,
+                            rows=rows)
+
+
+def assert_parity(got, ref, form, q=False):
+    err = oracle.bin_error(got["C_sum"], ref)
+    assert err.max() <= TOL[form], f"{form}: max binned error {err.max():.3e}"
+    if q:
+        scale = np.abs(ref["Sq_sum"]).max()
+        d = np.abs(got["Sq_sum"] - ref["Sq_sum"]).max() / scale
+        assert d <= 10 * TOL[form], f"{form}: phase error {d:.3e}"
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_square16_periodic(asd, form):
+    """16x16 periodic square lattice (N=256, F=96, T0=64, 32 displacements, w=1)."""
+    cfg = synth.cfg_small_2d()
+    tr = synth.traj_precess(cfg.lattice.n_sites, cfg.F, seed=cfg.seed)
+    got = run_gpu(asd, cfg.lattice, tr, cfg.T0, cfg.n_t, cfg.w, cfg.n_bins, form)
+    ref = oracle_ref(cfg.lattice, tr, cfg.T0, cfg.n_t, cfg.w, cfg.n_bins)
+    np.testing.assert_array_equal(got["counts"], ref["counts"])
+    assert_parity(got, ref, form)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("center", [False, True])
+def test_ragged_cubic_samples(asd, form, center):
+    """7^3 = 343 sites (ragged against 128-row tiles), 2 samples, i.i.d. spins."""
+    lat = synth.hypercubic(7, 3, True)
+    tr = synth.traj_iid(lat.n_sites, 23, seed=17, S=2)
+    got = run_gpu(asd, lat, tr, 13, 11, 0.5, 11, form, center=center)
+    ref = oracle_ref(lat, tr, 13, 11, 0.5, 11, center=center)
+    np.testing.assert_array_equal(got["counts"], ref["counts"])
+    assert_parity(got, ref, form)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_positions_with_phase(asd, form):
+    """Jittered open cube (FP32 position rule) with cosine phase weights."""
+    lat = synth.hypercubic(6, 3, False, jitter=0.1, seed=3)
+    q = synth.q_vectors_glass()[::5]
+    tr = synth.traj_precess(lat.n_sites, 40, seed=8)
+    got = run_gpu(asd, lat, tr, 24, 9, 0.5, 20, form, q=q)
+    ref = oracle_ref(lat, tr, 24, 9, 0.5, 20, q=q)
+    np.testing.assert_array_equal(got["counts"], ref["counts"])
+    assert_parity(got, ref, form, q=True)
+
+
+@pytest.mark.parametrize("form", ["split_bf16", "fp32"])
+def test_row_range(asd, form):
+    lat = synth.hypercubic(20, 2, True)
+    tr = synth.traj_precess(lat.n_sites, 30, seed=5)
+    rows = (37, 301)
+    got = run_gpu(asd, lat, tr, 16, 8, 1.0, 15, form, rows=rows)
+    ref = oracle_ref(lat, tr, 16, 8, 1.0, 15, rows=rows)
+    assert_parity(got, ref, form)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_window_bins(asd, form):
+    """Many narrow bins (a few pairs each, so no averaging): private-bin window plus the
+    shared fallback path; error held to the per-element rounding bound."""
+    lat = synth.hypercubic(8, 3, False, jitter=0.1, seed=4, block=(4, 4, 2))
+    tr = synth.traj_precess(lat.n_sites, 20, seed=6)
+    got = run_gpu(asd, lat, tr, 12, 5, 0.01, 1500, form)
+    ref = oracle_ref(lat, tr, 12, 5, 0.01, 1500)
+    np.testing.assert_array_equal(got["counts"], ref["counts"])
+    r = oracle.rounding_ratio(got["C_sum"], ref)
+    assert r.max() <= elem_bound(form, 36), f"{form}: {r.max():.3e}"
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_degenerate_single_site(asd, form):
+    lat = synth.hypercubic(1, 2, True)
+    tr = synth.traj_iid(1, 5, seed=2)
+    got = run_gpu(asd, lat, tr, 5, 1, 1.0, 1, form)
+    ref = oracle_ref(lat, tr, 5, 1, 1.0, 1)
+    assert got["counts"][0] == 1
+    assert_parity(got, ref, form)
+
+
+@pytest.mark.parametrize("form", ["split_bf16", "tf32"])
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_tile_widths_static_fm(asd, form, tile_n):
+    """Static ferromagnet: C == 1 in every bin, for both tile widths."""
+    lat = synth.hypercubic(9, 3, True)
+    tr = synth.traj_static(lat.n_sites, 12, direction=(0.3, -0.4, 0.866))
+    got = run_gpu(asd, lat, tr, 8, 4, 0.5, 13, form, tile_n=tile_n)
+    n = got["counts"].astype(np.float64)
+    full = n > 0                       # w = 0.5 leaves bins without lattice pairs
+    assert full.sum() >= 8
+    C = got["C_sum"][:, full] / (8 * n[full])
+    # identical products do not average: the worst-case per-product bound applies
+    np.testing.assert_allclose(C, 1.0, rtol=0, atol=elem_bound(form, 24))

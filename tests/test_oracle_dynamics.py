@@ -1,0 +1,114 @@
+"""Pins of the FP64 producer oracle (LL RK4, Monte Carlo) against closed forms and
+invariants: single-spin precession, the exchange dimer, total-spin conservation,
+energy conservation, the open-chain bond correlation -L(beta J), vMF moments."""
+import math
+
+import numpy as np
+
+from oracle import dynamics as dyn
+from paper_2308_07487_gb300 import synth
+
+
+def test_single_spin_precession_closed_form():
+    """dS/dt = (-Hz z^) x S: S_x = x0 cos(Hz t) + y0 sin(Hz t), S_y = y0 cos - x0 sin."""
+    nbr = np.full((1, 1), -1, np.int32)
+    J = np.zeros((1, 1), np.float32)
+    s0 = np.array([[[0.6, 0.0, 0.8]]])
+    Hz, dt, F = 0.5, 0.01, 201
+    tr = dyn.ll_rk4(s0, nbr, J, Hz, dt, F)
+    t = dt * np.arange(F)
+    ref = np.stack([0.6 * np.cos(Hz * t), -0.6 * np.sin(Hz * t), 0.8 * np.ones(F)], -1)
+    np.testing.assert_allclose(tr[0, 0], ref, atol=1e-10)
+
+
+def test_exchange_dimer_rotates_about_total_spin():
+    """Two spins, H = J S1.S2: S1 rotates about M = S1 + S2 at rate J|M| (Rodrigues)."""
+    nbr = np.array([[1], [0]], np.int32)
+    J = np.full((2, 1), 1.3, np.float32)
+    Jv = float(J[0, 0])            # the coupling the dynamics sees (FP32-rounded 1.3)
+    s1 = np.array([0.0, 0.6, 0.8])
+    s2 = np.array([1.0, 0.0, 0.0])
+    M = s1 + s2
+    k = M / np.linalg.norm(M)
+    t_end = 1.5
+    th = Jv * np.linalg.norm(M) * t_end
+    ref = s1 * math.cos(th) + np.cross(k, s1) * math.sin(th) + k * k.dot(s1) * (1 - math.cos(th))
+    errs = []
+    for dt in (0.02, 0.01):
+        n = int(round(t_end / dt))
+        tr = dyn.ll_rk4(np.array([[s1, s2]]), nbr, J, 0.0, dt, n + 1)
+        errs.append(np.abs(tr[0, 0, -1] - ref).max())
+    assert errs[1] < 1e-6
+    # fourth order: halving dt divides the global error by about 2^4
+    assert 12 < errs[0] / errs[1] < 20, errs
+
+
+def test_total_spin_conserved_and_energy_drift_small():
+    lat = synth.hypercubic(6, 2, True, J=-1.0)
+    s0 = synth.random_unit(lat.n_sites * 2, 7).reshape(2, lat.n_sites, 3).astype(np.float64)
+    tr = dyn.ll_rk4(s0, lat.nbr, lat.J, 0.0, 0.01, 101)
+    M = tr.sum(axis=0)  # [S][F][3]
+    assert np.abs(M - M[:, :1]).max() < 1e-11
+    Y0 = np.transpose(tr[:, :, 0], (1, 0, 2))
+    Y1 = np.transpose(tr[:, :, -1], (1, 0, 2))
+    e0, e1 = dyn.energy(Y0, lat.nbr, lat.J, 0.0), dyn.energy(Y1, lat.nbr, lat.J, 0.0)
+    assert np.abs(e1 - e0).max() < 1e-6 * lat.n_sites
+
+
+def test_field_precesses_total_moment():
+    """With Hz != 0 and exchange, M(t) precesses about z at rate Hz (exchange torques cancel)."""
+    lat = synth.hypercubic(4, 2, True, J=1.0)
+    s0 = synth.random_unit(lat.n_sites, 3)[None].astype(np.float64)
+    Hz, dt, F = 0.7, 0.01, 51
+    tr = dyn.ll_rk4(s0, lat.nbr, lat.J, Hz, dt, F)
+    M = tr.sum(axis=0)[0]
+    t = dt * (F - 1)
+    c, s = math.cos(Hz * t), math.sin(Hz * t)
+    ref = np.array([M[0, 0] * c + M[0, 1] * s, M[0, 1] * c - M[0, 0] * s, M[0, 2]])
+    np.testing.assert_allclose(M[-1], ref, atol=1e-8)
+
+
+def test_vmf_inverse_cdf_moments():
+    """E[w] = coth(kappa) - 1/kappa for the 3D von Mises-Fisher law."""
+    u = (np.arange(200000) + 0.5) / 200000
+    for kappa in (0.3, 2.0, 15.0):
+        w = dyn.vmf_w(kappa, u)
+        assert abs(w.mean() - (1 / math.tanh(kappa) - 1 / kappa)) < 1e-4
+
+
+def _chain_bond_corr(proposal, T, J=1.0, n=64, sweeps=3000, seed=1):
+    lat = synth.open_chain(n, J=J)
+    g = np.random.default_rng(seed)
+    Y = synth.random_unit(n, seed)[None].astype(np.float64)
+    acc = []
+    for sw in range(sweeps):
+        u = g.random((1, n, 4))
+        u[..., :2] = 1.0 - u[..., :2]  # (0, 1]
+        Y, _, _ = dyn.mc_sweep(Y, lat.nbr, lat.J, 0.0, T, u, lat.colors, proposal, cone=0.0)
+        if sw >= 300:
+            acc.append((Y[0, :-1] * Y[0, 1:]).sum(-1).mean())
+    return float(np.mean(acc))
+
+
+def test_open_chain_bond_correlation_metropolis():
+    """Open chain: bond angles are independent, <S_i.S_i+1> = -(coth(bJ) - 1/(bJ))."""
+    bJ = 1.0
+    ref = -(1 / math.tanh(bJ) - 1 / bJ)
+    got = _chain_bond_corr("metropolis", 1.0)
+    assert abs(got - ref) < 0.02, (got, ref)
+
+
+def test_open_chain_bond_correlation_heatbath():
+    bJ = 2.0
+    ref = -(1 / math.tanh(bJ) - 1 / bJ)
+    got = _chain_bond_corr("heatbath", 0.5)
+    assert abs(got - ref) < 0.02, (got, ref)
+
+
+def test_frame_is_orthonormal_right_handed():
+    m = synth.random_unit(50, 4).astype(np.float64)
+    m[0] = [0, 0, 1]
+    m[1] = [0, 0, -1]
+    e1, e2 = dyn.frame_of(m)
+    np.testing.assert_allclose(np.cross(e1, e2), m, atol=1e-12)
+    np.testing.assert_allclose((e1 * m).sum(-1), 0, atol=1e-12)
