@@ -38,14 +38,21 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="split_bf16", choices=["split_bf16", "bf16", "tf32", "fp32"])
-    ap.add_argument("--small", action="store_true", help="tiny workload (smoke / profiling)")
+    ap.add_argument("--small", action="store_true", help="tiny workload (smoke)")
+    ap.add_argument("--medium", action="store_true", help="profiling workload (ncu)")
     ap.add_argument("--no-extras", action="store_true", help="skip form sweep, CPU baseline, e2e")
     ap.add_argument("--ncu", action="store_true", help="one step, nothing else (for ncu)")
     return ap.parse_args()
 
 
-def workload(small):
+def workload(small, medium=False):
     from paper_2308_07487_gb300 import synth
+    if medium:
+        # profiling case: same K and bin width as the throughput workload, 26^3 sites,
+        # 4 displacements (operands ~2 GB: larger than L2, small enough for ncu replay)
+        lat = synth.hypercubic(26, 3, True, J=1.0, seed=23082)
+        return dict(name="sc26_periodic_N17576", lat=lat, F=1003, T0=1000, n_t=4, w=0.5,
+                    n_bins=46, T=1.2, sweeps=200, dt=0.01)
     if small:
         lat = synth.hypercubic(16, 3, True, J=1.0, seed=23082)
         return dict(name="sc16_periodic_N4096", lat=lat, F=160, T0=128, n_t=32, w=0.5, n_bins=28,
@@ -362,7 +369,7 @@ def run_ours(args, W, ws, rank, local):
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
-    W = workload(args.small)
+    W = workload(args.small, args.medium)
     if args.impl == "reference":
         run_reference(args, W, ws, rank)
     else:

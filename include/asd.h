@@ -233,6 +233,39 @@ int asd_thermalize(const asd_system *sys, int n_samples, float *spins, float T, 
                    int proposal, const asd_mlp *net, float cone, int adapt, uint64_t seed,
                    uint64_t counter, const float *uniforms, asd_mc_stats *stats, void *stream);
 
+/* -------------------------------------------------------------------------------
+ * Training of the learned proposal network (no counterpart in the paper: an
+ * extension of the Monte Carlo sampler of Section 2.1).  Maximum likelihood of a
+ * site's spin given its neighbours' spins, on configurations from plain Monte Carlo.
+ *
+ * Parameter vector (device FP32, P = asd_mlp_param_count(n_in) entries):
+ *   [W1 H*n_in][b1 H][W2 H*H][b2 H][W3 4*H][b3 4]   (H = 64, row-major [out][in]).
+ * BF16 weight buffer (device, asd_mlp_param_count_bf16 entries): [W1][W2][W3].
+ * An asd_mlp view for inference points W1..W3 into the BF16 buffer and b1..b3 into
+ * the parameter vector.
+ * ------------------------------------------------------------------------------- */
+int64_t asd_mlp_param_count(int n_in);
+int64_t asd_mlp_param_count_bf16(int n_in);
+
+/* Training pairs: for sample s and site i (k = s*N + i), x[k] = the z neighbour spins
+ * (3z floats, zeros for empty slots) and y[k] = S_i.  spins device [S][N][3];
+ * x device [S*N][3z]; y device [S*N][3]. */
+int asd_mlp_gather(const asd_system *sys, int n_samples, const float *spins, float *x, float *y,
+                   void *stream);
+
+/* Negative log-likelihood of y under vMF(mu(x), kappa(x)) summed over the n pairs,
+ * added to *loss (device FP64 scalar), and its gradient with respect to the parameter
+ * vector (evaluated at the BF16-rounded weights of `net`) added to grad (device FP32 [P]).
+ * kappa = softplus(o_4) + 1e-4. */
+int asd_mlp_loss_grad(const asd_mlp *net, int64_t n, const float *x, const float *y, float *grad,
+                      double *loss, void *stream);
+
+/* One Adam step (bias-corrected, step >= 1) on params with gradient grad * grad_scale,
+ * moments m, v (device FP32 [P]); then writes the BF16 copy of the weights to w_bf16. */
+int asd_mlp_adam_step(float *params, const float *grad, float grad_scale, float *m, float *v,
+                      int n_in, float lr, float beta1, float beta2, float eps, int step,
+                      uint16_t *w_bf16, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,14 @@ _SIGS = {
                                       ctypes.c_int, ctypes.c_int, ctypes.POINTER(asd_mlp),
                                       ctypes.c_float, ctypes.c_int, ctypes.c_uint64,
                                       ctypes.c_uint64, _VP, ctypes.POINTER(asd_mc_stats), _VP]),
+    "asd_mlp_param_count": (ctypes.c_int64, [ctypes.c_int]),
+    "asd_mlp_param_count_bf16": (ctypes.c_int64, [ctypes.c_int]),
+    "asd_mlp_gather": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "asd_mlp_loss_grad": (ctypes.c_int, [ctypes.POINTER(asd_mlp), ctypes.c_int64, _VP, _VP, _VP, _VP,
+                                         _VP]),
+    "asd_mlp_adam_step": (ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, _VP, ctypes.c_int,
+                                         ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_int, _VP, _VP]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name, None)
@@ -223,6 +231,58 @@ def sync_status(stream=None):
     return lib.asd_sync_status(_stream(stream))
 
 
+class Mlp:
+    """Learned-proposal network: FP32 master parameters, BF16 weight copy, Adam moments
+    (device tensors) and the asd_mlp view the sampler reads."""
+
+    def __init__(self, n_in, params=None, device="cuda"):
+        import torch
+        self.n_in = n_in
+        P = lib.asd_mlp_param_count(n_in)
+        Pw = lib.asd_mlp_param_count_bf16(n_in)
+        self.P = P
+        p = np.zeros(P, np.float32) if params is None else np.asarray(params, np.float32)
+        assert p.shape == (P,)
+        self.params = torch.from_numpy(p.copy()).to(device)
+        self.grad = torch.zeros(P, dtype=torch.float32, device=device)
+        self.m = torch.zeros(P, dtype=torch.float32, device=device)
+        self.v = torch.zeros(P, dtype=torch.float32, device=device)
+        self.wb = torch.zeros(Pw, dtype=torch.bfloat16, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+        self.step = 0
+        self._refresh_bf16()
+        H, es = 64, self.params.element_size()
+        c = asd_mlp()
+        c.n_in, c.n_hidden = n_in, H
+        wp, bs = self.wb.data_ptr(), self.wb.element_size()
+        c.W1, c.W2, c.W3 = wp, wp + H * n_in * bs, wp + (H * n_in + H * H) * bs
+        pp = self.params.data_ptr()
+        c.b1 = pp + H * n_in * es
+        c.b2 = pp + (H * n_in + H + H * H) * es
+        c.b3 = pp + (H * n_in + H + H * H + H + 4 * H) * es
+        self.c = c
+
+    def _refresh_bf16(self):
+        import torch
+        H, n = 64, self.n_in
+        p = self.params
+        w = torch.cat([p[:H * n], p[H * n + H:H * n + H + H * H],
+                       p[H * n + 2 * H + H * H:H * n + 2 * H + H * H + 4 * H]])
+        self.wb.copy_(w.to(torch.bfloat16))
+
+    def loss_grad(self, x, y, n=None, stream=None):
+        n = x.shape[0] if n is None else n
+        check(lib.asd_mlp_loss_grad(ctypes.byref(self.c), n, _ptr(x), _ptr(y), _ptr(self.grad),
+                                    _ptr(self.loss), _stream(stream)), "mlp_loss_grad")
+
+    def adam(self, lr=1e-3, scale=1.0, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+        self.step += 1
+        check(lib.asd_mlp_adam_step(_ptr(self.params), _ptr(self.grad), float(scale), _ptr(self.m),
+                                    _ptr(self.v), self.n_in, float(lr), float(b1), float(b2),
+                                    float(eps), self.step, _ptr(self.wb), _stream(stream)),
+              "mlp_adam_step")
+
+
 class System:
     """asd_system for a synth.Lattice: neighbour table, couplings and colouring are
     copied to the device (torch tensors kept alive by this object)."""
@@ -245,6 +305,11 @@ class System:
         s.color_sites = self.color_sites.data_ptr()
         s.color_offsets = self.offsets.ctypes.data_as(c_i64p)
         self.c = s
+
+    def gather(self, spins, x, y, stream=None):
+        S = spins.shape[0] if spins.dim() == 3 else 1
+        check(lib.asd_mlp_gather(ctypes.byref(self.c), S, _ptr(spins), _ptr(x), _ptr(y),
+                                 _stream(stream)), "mlp_gather")
 
     def ll_integrate(self, spins0, dt, n_frames, stride, traj, spins_out=None, stream=None):
         S = spins0.shape[0] if spins0.dim() == 3 else 1

@@ -1,0 +1,270 @@
+// Training of the learned von Mises-Fisher proposal (extension of the Monte Carlo of
+// Section 2.1; the paper has no learned component).
+//
+// Model: x (neighbour spins, 3z) -> tanh(W1 x + b1) -> tanh(W2 h1 + b2) -> o = W3 h2 + b3,
+// mu = o[0:3]/|o[0:3]|, kappa = softplus(o[3]) + 1e-4.  Loss: the negative log-likelihood
+// of the site spin y under vMF(mu, kappa):
+//   NLL = -log kappa + log(2 pi) + kappa + log(1 - e^{-2 kappa}) - kappa mu.y
+// (log of the normaliser 4 pi sinh(kappa) / kappa written to stay finite).
+// Gradients: dNLL/dkappa = coth(kappa) - 1/kappa - mu.y (the Langevin function, with a
+// series below kappa = 1e-2), dNLL/dv = -kappa (y - mu (mu.y)) / |v| for v = o[0:3],
+// then back through the two tanh layers.
+//
+// loss_grad: persistent blocks of 64 threads, one sample per thread per chunk.  The
+// activations and deltas of a chunk go to shared memory; each thread then owns a
+// strided set of parameter entries and sums their gradient over the chunk, so the
+// whole launch issues one global atomic per parameter per block.
+#include <cuda_bf16.h>
+
+#include "asd_internal.h"
+#include "mlp.cuh"
+
+namespace asd {
+namespace {
+
+constexpr int H = kMlpHidden;
+constexpr int kChunk = 64;
+
+__host__ __device__ inline int64_t n_params(int nin) { return (int64_t)H * nin + H + H * H + H + 4 * H + 4; }
+__host__ __device__ inline int64_t n_weights(int nin) { return (int64_t)H * nin + H * H + 4 * H; }
+
+__global__ void gather_kernel(int64_t N, int S, int z, const int *__restrict__ nbr,
+                              const float *__restrict__ spins, float *__restrict__ x,
+                              float *__restrict__ y)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N * S) return;
+    const int64_t s = k / N, i = k % N;
+    const float *Ys = spins + s * N * 3;
+    for (int a = 0; a < z; ++a) {
+        const int j = nbr[i * z + a];
+        for (int c = 0; c < 3; ++c) x[k * 3 * z + 3 * a + c] = j >= 0 ? Ys[3 * (int64_t)j + c] : 0.f;
+    }
+    for (int c = 0; c < 3; ++c) y[3 * k + c] = Ys[3 * i + c];
+}
+
+__device__ __forceinline__ float langevin(float k)
+{
+    if (k < 1e-2f) return k * (1.f / 3.f) - k * k * k * (1.f / 45.f);
+    return 1.f / tanhf(k) - 1.f / k;
+}
+
+__global__ void __launch_bounds__(kChunk) loss_grad_kernel(MlpView net, int64_t n,
+                                                            const float *__restrict__ x,
+                                                            const float *__restrict__ y,
+                                                            float *__restrict__ grad,
+                                                            double *__restrict__ loss)
+{
+    const int nin = net.n_in;
+    const int P = (int)n_params(nin);
+    extern __shared__ float sm[];
+    float *W1 = sm;                    // [H][nin]
+    float *W2 = W1 + H * nin;          // [H][H]
+    float *W3 = W2 + H * H;            // [4][H]
+    float *Xs = W3 + 4 * H;            // [chunk][nin]
+    float *H1 = Xs + kChunk * nin;     // [chunk][H]
+    float *H2 = H1 + kChunk * H;       // [chunk][H]
+    float *D1 = H2 + kChunk * H;       // [chunk][H]
+    float *D2 = D1 + kChunk * H;       // [chunk][H]
+    float *DO = D2 + kChunk * H;       // [chunk][4]
+    float *acc = DO + kChunk * 4;      // [P] gradient accumulator of this block
+    __shared__ double lsum[kChunk];
+
+    const int t = threadIdx.x;
+    for (int e = t; e < H * nin; e += kChunk) W1[e] = __bfloat162float(net.W1[e]);
+    for (int e = t; e < H * H; e += kChunk) W2[e] = __bfloat162float(net.W2[e]);
+    for (int e = t; e < 4 * H; e += kChunk) W3[e] = __bfloat162float(net.W3[e]);
+    for (int e = t; e < P; e += kChunk) acc[e] = 0.f;
+    double my_loss = 0.0;
+    __syncthreads();
+
+    for (int64_t base = (int64_t)blockIdx.x * kChunk; base < n; base += (int64_t)gridDim.x * kChunk) {
+        const int64_t s = base + t;
+        const bool ok = s < n;
+        float xv[kMlpMaxIn];
+        for (int c = 0; c < nin; ++c) {
+            xv[c] = ok ? x[s * nin + c] : 0.f;
+            Xs[t * nin + c] = xv[c];
+        }
+        float h1[H], h2[H], o[4];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            float a = __ldg(net.b1 + k);
+            for (int c = 0; c < nin; ++c) a = fmaf(W1[k * nin + c], xv[c], a);
+            h1[k] = tanhf(a);
+        }
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            float a = __ldg(net.b2 + k);
+#pragma unroll
+            for (int c = 0; c < H; ++c) a = fmaf(W2[k * H + c], h1[c], a);
+            h2[k] = tanhf(a);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float a = __ldg(net.b3 + k);
+#pragma unroll
+            for (int c = 0; c < H; ++c) a = fmaf(W3[k * H + c], h2[c], a);
+            o[k] = a;
+        }
+        float yv[3] = {0.f, 0.f, 0.f};
+        if (ok)
+            for (int c = 0; c < 3; ++c) yv[c] = y[s * 3 + c];
+        const float vn = sqrtf(fmaxf(o[0] * o[0] + o[1] * o[1] + o[2] * o[2], 1e-30f));
+        const float mu[3] = {o[0] / vn, o[1] / vn, o[2] / vn};
+        const float kap = softplus_f(o[3]) + 1e-4f;
+        const float muy = mu[0] * yv[0] + mu[1] * yv[1] + mu[2] * yv[2];
+        float dO[4];
+        if (ok) {
+            my_loss += (double)(-logf(kap) + 1.8378770664093453f + kap + log1pf(-expf(-2.f * kap)) -
+                                kap * muy);
+            const float dk = langevin(kap) - muy;
+            dO[3] = dk / (1.f + expf(-o[3]));  // d softplus / d o3 = sigmoid(o3)
+            for (int c = 0; c < 3; ++c) dO[c] = -kap * (yv[c] - mu[c] * muy) / vn;
+        } else {
+            dO[0] = dO[1] = dO[2] = dO[3] = 0.f;
+        }
+        float d2[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            float g = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) g = fmaf(W3[q * H + k], dO[q], g);
+            d2[k] = g * (1.f - h2[k] * h2[k]);
+        }
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+            float g = 0.f;
+#pragma unroll
+            for (int k = 0; k < H; ++k) g = fmaf(W2[k * H + c], d2[k], g);
+            D1[t * H + c] = g * (1.f - h1[c] * h1[c]);
+            H1[t * H + c] = h1[c];
+            H2[t * H + c] = h2[c];
+            D2[t * H + c] = d2[c];
+        }
+        for (int q = 0; q < 4; ++q) DO[t * 4 + q] = dO[q];
+        __syncthreads();
+        // parameter gradients summed over the chunk
+        for (int e = t; e < P; e += kChunk) {
+            float g = 0.f;
+            int r = e;
+            if (r < H * nin) {
+                const int k = r / nin, c = r % nin;
+                for (int m = 0; m < kChunk; ++m) g = fmaf(D1[m * H + k], Xs[m * nin + c], g);
+            } else if ((r -= H * nin) < H) {
+                for (int m = 0; m < kChunk; ++m) g += D1[m * H + r];
+            } else if ((r -= H) < H * H) {
+                const int k = r / H, c = r % H;
+                for (int m = 0; m < kChunk; ++m) g = fmaf(D2[m * H + k], H1[m * H + c], g);
+            } else if ((r -= H * H) < H) {
+                for (int m = 0; m < kChunk; ++m) g += D2[m * H + r];
+            } else if ((r -= H) < 4 * H) {
+                const int q = r / H, c = r % H;
+                for (int m = 0; m < kChunk; ++m) g = fmaf(DO[m * 4 + q], H2[m * H + c], g);
+            } else {
+                r -= 4 * H;
+                for (int m = 0; m < kChunk; ++m) g += DO[m * 4 + r];
+            }
+            acc[e] += g;
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < P; e += kChunk)
+        if (acc[e] != 0.f) atomicAdd(&grad[e], acc[e]);
+    lsum[t] = my_loss;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int k = 0; k < kChunk; ++k) s += lsum[k];
+        atomicAdd(loss, s);
+    }
+}
+
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float scale,
+                            float *__restrict__ m, float *__restrict__ v, int64_t P, int nin,
+                            float lr, float b1, float b2, float eps, float c1, float c2,
+                            __nv_bfloat16 *__restrict__ wb)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= P) return;
+    const float gr = g[e] * scale;
+    const float mm = b1 * m[e] + (1.f - b1) * gr;
+    const float vv = b2 * v[e] + (1.f - b2) * gr * gr;
+    m[e] = mm;
+    v[e] = vv;
+    const float np = p[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    p[e] = np;
+    // packed BF16 weights [W1][W2][W3]; biases are skipped
+    const int64_t oW1 = 0, ob1 = (int64_t)H * nin, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H,
+                  ob3 = oW3 + 4 * H;
+    int64_t w = -1;
+    if (e < ob1) w = e - oW1;
+    else if (e >= oW2 && e < ob2) w = (int64_t)H * nin + (e - oW2);
+    else if (e >= oW3 && e < ob3) w = (int64_t)H * nin + H * H + (e - oW3);
+    if (w >= 0) wb[w] = __float2bfloat16_rn(np);
+}
+
+}  // namespace
+}  // namespace asd
+
+using namespace asd;
+
+extern "C" {
+
+int64_t asd_mlp_param_count(int n_in) { return n_params(n_in); }
+int64_t asd_mlp_param_count_bf16(int n_in) { return n_weights(n_in); }
+
+int asd_mlp_gather(const asd_system *sys, int n_samples, const float *spins, float *x, float *y,
+                   void *stream)
+{
+    ASD_CHECK_ARG(sys && spins && x && y, "null argument");
+    ASD_CHECK_ARG(sys->n_sites >= 1 && sys->z >= 1 && sys->z <= kMlpMaxIn / 3 && sys->nbr,
+                  "bad system (z must be 1..8)");
+    ASD_CHECK_ARG(n_samples >= 1, "bad n_samples");
+    const int64_t n = sys->n_sites * n_samples;
+    gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        sys->n_sites, n_samples, sys->z, sys->nbr, spins, x, y);
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}
+
+int asd_mlp_loss_grad(const asd_mlp *net, int64_t n, const float *x, const float *y, float *grad,
+                      double *loss, void *stream)
+{
+    ASD_CHECK_ARG(net && x && y && grad && loss, "null argument");
+    ASD_CHECK_ARG(net->n_hidden == kMlpHidden && net->n_in >= 3 && net->n_in <= kMlpMaxIn,
+                  "network shape must be [n_in <= 24 -> 64 -> 64 -> 4]");
+    ASD_CHECK_ARG(net->W1 && net->W2 && net->W3 && net->b1 && net->b2 && net->b3, "null weights");
+    ASD_CHECK_ARG(n >= 0, "bad n");
+    if (n == 0) return ASD_OK;
+    const int nin = net->n_in;
+    const size_t smem = sizeof(float) * ((size_t)H * nin + H * H + 4 * H + kChunk * nin +
+                                         4 * kChunk * H + kChunk * 4 + n_params(nin));
+    auto k = loss_grad_kernel;
+    ASD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0;
+    ASD_CUDA_TRY(cudaGetDevice(&dev));
+    ASD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t chunks = (n + kChunk - 1) / kChunk;
+    int64_t blocks = chunks < (int64_t)sms * 2 ? chunks : (int64_t)sms * 2;
+    k<<<(unsigned)blocks, kChunk, smem, (cudaStream_t)stream>>>(mlp_view(*net), n, x, y, grad, loss);
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}
+
+int asd_mlp_adam_step(float *params, const float *grad, float grad_scale, float *m, float *v,
+                      int n_in, float lr, float beta1, float beta2, float eps, int step,
+                      uint16_t *w_bf16, void *stream)
+{
+    ASD_CHECK_ARG(params && grad && m && v && w_bf16, "null argument");
+    ASD_CHECK_ARG(n_in >= 3 && n_in <= kMlpMaxIn && step >= 1, "bad n_in or step");
+    const int64_t P = n_params(n_in);
+    const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    adam_kernel<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        params, grad, grad_scale, m, v, P, n_in, lr, beta1, beta2, eps, c1, c2,
+        reinterpret_cast<__nv_bfloat16 *>(w_bf16));
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}
+
+}  // extern "C"

@@ -69,7 +69,7 @@ __device__ __forceinline__ void mlp_vmf(const MlpView &n, const float *x, float 
     mu[0] = o[0] * inv;
     mu[1] = o[1] * inv;
     mu[2] = o[2] * inv;
-    *kappa = softplus_f(o[3]);
+    *kappa = softplus_f(o[3]) + 1e-4f;
 }
 
 }  // namespace asd
