@@ -91,7 +91,9 @@ typedef struct asd_corr_desc {
     int32_t n_q;            /* 0 .. 256                                                */
     const double *q;        /* host [n_q][3]                                           */
     int32_t tile_n;         /* 0 = chosen by the autotuner, else 128 or 256 (tensor forms) */
-    int32_t reserved[7];    /* must be zero                                            */
+    int32_t raster_m;       /* 0 = automatic, else row tiles per raster group (1..64)  */
+    int32_t stages;         /* 0 = automatic, else shared-memory pipeline stages (2..8) */
+    int32_t reserved[5];    /* must be zero                                            */
 } asd_corr_desc;
 
 typedef struct asd_corr_plan asd_corr_plan;

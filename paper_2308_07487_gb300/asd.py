@@ -38,7 +38,8 @@ class asd_corr_desc(ctypes.Structure):
                 ("periodic", ctypes.c_int32), ("coords", c_i32p), ("pos", c_f32p),
                 ("bin_width", ctypes.c_double), ("n_bins", ctypes.c_int32),
                 ("n_q", ctypes.c_int32), ("q", c_f64p), ("tile_n", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("raster_m", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class asd_system(ctypes.Structure):
@@ -132,7 +133,7 @@ class CorrPlan:
 
     def __init__(self, N, F, T0, n_t, precision="split_bf16", S=1, center=False, coords=None,
                  L=(1, 1, 1), periodic=False, pos=None, bin_width=1.0, n_bins=0, q=None,
-                 tile_n=0):
+                 tile_n=0, raster_m=0, stages=0):
         d = asd_corr_desc()
         d.n_sites, d.n_frames, d.n_samples, d.T0, d.n_t = N, F, S, T0, n_t
         d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -159,6 +160,8 @@ class CorrPlan:
             d.n_q = qq.shape[0]
             d.q = qq.ctypes.data_as(c_f64p)
         d.tile_n = int(tile_n)
+        d.raster_m = int(raster_m)
+        d.stages = int(stages)
         self.desc = d
         self.N, self.F, self.S, self.T0, self.n_t = N, F, S, T0, n_t
         self.n_bins, self.n_q = int(n_bins), int(d.n_q)
@@ -169,15 +172,15 @@ class CorrPlan:
 
     @classmethod
     def for_lattice(cls, lat, F, T0, n_t, w, n_bins, precision="split_bf16", S=1, center=False,
-                    q=None, positions=None, tile_n=0):
+                    q=None, positions=None, **tune):
         """Plan for a synth.Lattice: integer-lattice geometry unless its positions are
         jittered (then the FP32 position rule) or positions=True is forced."""
         jittered = not np.array_equal(lat.pos, lat.coords.astype(np.float32))
         if positions or (positions is None and jittered):
             return cls(lat.n_sites, F, T0, n_t, precision, S, center, pos=lat.pos,
-                       bin_width=w, n_bins=n_bins, q=q, tile_n=tile_n)
+                       bin_width=w, n_bins=n_bins, q=q, **tune)
         return cls(lat.n_sites, F, T0, n_t, precision, S, center, coords=lat.coords, L=lat.L,
-                   periodic=lat.periodic, bin_width=w, n_bins=n_bins, q=q, tile_n=tile_n)
+                   periodic=lat.periodic, bin_width=w, n_bins=n_bins, q=q, **tune)
 
     def counts(self):
         out = np.zeros(max(self.n_bins, 1), np.int64)

@@ -717,7 +717,9 @@ int tc_configure(asd_corr_plan *p)
     if (p->n_bins == 0) NW = 0;
     p->NW = NW;
     int st = (int)((cap - epi(NW)) / stage_bytes);
-    p->stages = st > 6 ? 6 : st;
+    if (st > 8) st = 8;
+    if (p->d.stages > 0 && p->d.stages < st) st = p->d.stages;
+    p->stages = st;
     p->smem_bytes = epi(NW) + (size_t)p->stages * stage_bytes + 2048;
     // more than half of the SM's shared memory: never two CTAs (and TMEM owners) per SM
     if (p->smem_bytes < kMinSmem) p->smem_bytes = kMinSmem;

@@ -167,7 +167,7 @@ static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int6
     tp->Kseg = (int)p->Kseg;
     tp->nkb = (int)(p->Kseg / p->BK);
     tp->n_copies = p->n_copies;
-    tp->group_m = 8;
+    tp->group_m = p->d.raster_m > 0 ? p->d.raster_m : 16;
     tp->n_tiles = (int64_t)p->n_t * tp->tiles_m * tp->tiles_n;
     tp->epi = epi_of(p);
     return ASD_OK;
@@ -254,7 +254,9 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
     ASD_CHECK_ARG(d->n_bins == 0 || d->bin_width > 0, "bin_width must be > 0");
     ASD_CHECK_ARG(d->n_q == 0 || d->q, "q required when n_q > 0");
     ASD_CHECK_ARG(d->tile_n == 0 || d->tile_n == 128 || d->tile_n == 256, "tile_n: 0, 128, 256");
-    for (int k = 0; k < 7; ++k) ASD_CHECK_ARG(d->reserved[k] == 0, "reserved fields must be 0");
+    ASD_CHECK_ARG(d->raster_m >= 0 && d->raster_m <= 64, "raster_m: 0..64");
+    ASD_CHECK_ARG(d->stages == 0 || (d->stages >= 2 && d->stages <= 8), "stages: 0 or 2..8");
+    for (int k = 0; k < 5; ++k) ASD_CHECK_ARG(d->reserved[k] == 0, "reserved fields must be 0");
     if (d->geometry == ASD_GEOM_LATTICE) {
         ASD_CHECK_ARG(d->coords, "coords required for lattice geometry");
         for (int a = 0; a < 3; ++a) ASD_CHECK_ARG(d->L[a] >= 1 && d->L[a] <= 1 << 20, "bad L");
