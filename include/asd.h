@@ -201,6 +201,29 @@ typedef struct asd_system {
 int asd_ll_integrate(const asd_system *sys, int n_samples, const float *spins0, float dt,
                      int n_frames, int stride, float *traj, float *spins_out, void *stream);
 
+/*
+ * Same computation and arguments as asd_ll_integrate, for callers that cannot allocate
+ * device memory: for example code that runs while another thread holds a global-mode
+ * stream capture (cudaMalloc is refused then), processes whose device memory is owned
+ * entirely by their own pool allocator, or latency-critical loops that cannot take the
+ * implicit synchronisation of cudaMalloc / cudaFree.  The paper has no counterpart; this
+ * is a deployment variant only.
+ *
+ * The RK4 work buffers live in one fixed array in device memory that the library
+ * reserves when it is loaded (12 MiB on every GPU that loads it, held until the process
+ * exits).  Limit: n_sites * n_samples <= 262144; larger requests return ASD_EINVAL and
+ * launch nothing.  The first call on each device looks up that array's device address
+ * (a runtime query, no allocation), so make that first call before any stream capture
+ * begins.  All calls share the one array: calls whose work can overlap on the GPU (on
+ * different streams without ordering) race on it and give wrong results; calls on one
+ * stream are safe.  Nothing in the array needs to start at zero: every buffer is fully
+ * written before it is read.  Allocates nothing (no cudaMalloc, cudaMallocAsync or
+ * cudaFree).
+ */
+int asd_ll_integrate_noalloc(const asd_system *sys, int n_samples, const float *spins0, float dt,
+                             int n_frames, int stride, float *traj, float *spins_out,
+                             void *stream);
+
 enum asd_proposal {
     ASD_METROPOLIS = 0,  /* uniform on the sphere, or a cone about the old spin       */
     ASD_HEATBATH = 1,    /* exact conditional: von Mises-Fisher about -h             */

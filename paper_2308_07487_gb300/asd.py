@@ -75,6 +75,9 @@ _SIGS = {
     "asd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "asd_ll_integrate": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP, ctypes.c_float,
                                         ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "asd_ll_integrate_noalloc": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP,
+                                                ctypes.c_float, ctypes.c_int, ctypes.c_int, _VP,
+                                                _VP, _VP]),
     "asd_thermalize": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP, ctypes.c_float,
                                       ctypes.c_int, ctypes.c_int, ctypes.POINTER(asd_mlp),
                                       ctypes.c_float, ctypes.c_int, ctypes.c_uint64,
@@ -319,6 +322,16 @@ class System:
         check(lib.asd_ll_integrate(ctypes.byref(self.c), S, _ptr(spins0), float(dt), int(n_frames),
                                    int(stride), _ptr(traj), _ptr(spins_out), _stream(stream)),
               "ll_integrate")
+
+    def ll_integrate_noalloc(self, spins0, dt, n_frames, stride, traj, spins_out=None,
+                             stream=None):
+        """asd_ll_integrate_noalloc: same result, work buffers in the library's fixed
+        device array (for callers that cannot allocate; n_sites * n_samples <= 262144)."""
+        S = spins0.shape[0] if spins0.dim() == 3 else 1
+        check(lib.asd_ll_integrate_noalloc(ctypes.byref(self.c), S, _ptr(spins0), float(dt),
+                                           int(n_frames), int(stride), _ptr(traj),
+                                           _ptr(spins_out), _stream(stream)),
+              "ll_integrate_noalloc")
 
     def thermalize(self, spins, T, n_sweeps, proposal=ASD_METROPOLIS, net=None, cone=0.0,
                    adapt=False, seed=0, counter=0, uniforms=None, stats=False, stream=None):

@@ -144,3 +144,85 @@ extern "C" int asd_ll_integrate(const asd_system *sys, int n_samples, const floa
     if (rc == ASD_ECUDA) set_error_text("asd_ll_integrate: launch failed");
     return rc;
 }
+
+// ---------------------------------------------------------------------------------------
+// No-allocation variant: the same RK4 launches with their four work buffers (state,
+// two stage inputs, derivative sum) carved from one fixed device array reserved with the
+// library, for callers that cannot allocate device memory (see include/asd.h).
+// ---------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace asd {
+namespace {
+
+constexpr int64_t kLLStaticMaxSiteSamples = 1 << 18;  // n_sites * n_samples limit
+constexpr int kLLStaticMaxDevices = 64;
+
+// 4 buffers x 3 components x 262144 site-samples x 4 B = 12 MiB per device
+static __device__ __align__(256) float g_ll_scratch[4 * 3 * kLLStaticMaxSiteSamples];
+
+std::mutex g_ll_scratch_mu;
+float *g_ll_scratch_addr[kLLStaticMaxDevices] = {};
+
+// Device address of g_ll_scratch on the current device, looked up once per device.
+// In host code the symbol itself is only a host-side stand-in; kernels must be given
+// this address.
+int ll_scratch_address(float **out)
+{
+    int dev = 0;
+    ASD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kLLStaticMaxDevices) {
+        set_error_text("asd_ll_integrate_noalloc: device index out of range");
+        return ASD_EUNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_ll_scratch_mu);
+    if (!g_ll_scratch_addr[dev]) {
+        void *p = nullptr;
+        ASD_CUDA_TRY(cudaGetSymbolAddress(&p, g_ll_scratch));
+        g_ll_scratch_addr[dev] = static_cast<float *>(p);
+    }
+    *out = g_ll_scratch_addr[dev];
+    return ASD_OK;
+}
+
+}  // namespace
+}  // namespace asd
+
+extern "C" int asd_ll_integrate_noalloc(const asd_system *sys, int n_samples, const float *spins0,
+                                        float dt, int n_frames, int stride, float *traj,
+                                        float *spins_out, void *stream)
+{
+    ASD_CHECK_ARG(sys && spins0 && traj, "null argument");
+    ASD_CHECK_ARG(sys->n_sites >= 1 && sys->z >= 0 && sys->z <= 32, "bad system");
+    ASD_CHECK_ARG(sys->z == 0 || (sys->nbr && sys->J), "neighbour table required");
+    ASD_CHECK_ARG(n_samples >= 1 && n_frames >= 1 && stride >= 1, "bad n_samples/n_frames/stride");
+    ASD_CHECK_ARG(sys->n_sites * (int64_t)n_samples <= kLLStaticMaxSiteSamples,
+                  "asd_ll_integrate_noalloc: n_sites * n_samples exceeds the fixed work area "
+                  "(262144 site-samples); use asd_ll_integrate");
+    float *ws = nullptr;
+    int rc = ll_scratch_address(&ws);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    LLArgs a{sys->n_sites, n_samples, sys->z, sys->nbr, sys->J, sys->Hz};
+    const int64_t n = sys->n_sites * n_samples;
+    const size_t bytes = sizeof(float) * 3 * (size_t)n;
+    // every buffer is written before it is read: Y by the copy, acc by stage 1, T1 / T2
+    // by the stage that produces them, so no clearing is needed
+    float *Y = ws, *T1 = ws + 3 * n, *T2 = ws + 6 * n, *acc = ws + 9 * n;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    ASD_CUDA_TRY(cudaMemcpyAsync(Y, spins0, bytes, cudaMemcpyDeviceToDevice, s));
+    write_frame0<<<blocks, 256, 0, s>>>(Y, sys->n_sites, n_samples, traj, n_frames);
+    for (int f = 1; f < n_frames; ++f) {
+        for (int k = 0; k < stride; ++k) {
+            const int frame = k == stride - 1 ? f : -1;
+            rk4_stage<1><<<blocks, 256, 0, s>>>(a, Y, Y, T1, acc, dt, traj, n_frames, -1);
+            rk4_stage<2><<<blocks, 256, 0, s>>>(a, Y, T1, T2, acc, dt, traj, n_frames, -1);
+            rk4_stage<3><<<blocks, 256, 0, s>>>(a, Y, T2, T1, acc, dt, traj, n_frames, -1);
+            rk4_stage<4><<<blocks, 256, 0, s>>>(a, Y, T1, nullptr, acc, dt, traj, n_frames, frame);
+        }
+    }
+    ASD_CUDA_TRY(cudaGetLastError());
+    if (spins_out)
+        ASD_CUDA_TRY(cudaMemcpyAsync(spins_out, Y, bytes, cudaMemcpyDeviceToDevice, s));
+    return ASD_OK;
+}
