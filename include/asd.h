@@ -93,7 +93,12 @@ typedef struct asd_corr_desc {
     int32_t tile_n;         /* 0 = chosen by the autotuner, else 128 or 256 (tensor forms) */
     int32_t raster_m;       /* 0 = automatic, else row tiles per raster group (1..64)  */
     int32_t stages;         /* 0 = automatic, else shared-memory pipeline stages (2..8) */
-    int32_t reserved[5];    /* must be zero                                            */
+    int32_t k_chunks;       /* 0 = automatic, else partial accumulators per tile along K
+                               (1..16): each starts from zero, which bounds the tensor-core
+                               FP32 accumulation error; the epilogue adds them exactly   */
+    int32_t cluster;        /* 0 = automatic, 1, or 4: CTAs sharing one B tile via TMA
+                               multicast                                                 */
+    int32_t reserved[3];    /* must be zero                                            */
 } asd_corr_desc;
 
 typedef struct asd_corr_plan asd_corr_plan;
@@ -147,7 +152,7 @@ int asd_pair_corr_contract(asd_corr_plan *plan, int64_t row_begin, int64_t row_e
 /*
  * Several independent problems (each its own plan, trajectory and outputs) in ONE
  * persistent launch over a flattened (problem, t, tile) work list.  All plans must
- * use the same tensor-core precision and the same tile width.  Operand preparation
+ * use the same tensor-core precision, tile width and cluster size.  Operand preparation
  * for every problem is enqueued first on the same stream.  Capturable into a CUDA
  * graph (no host synchronisation, no allocation).
  */

@@ -39,7 +39,8 @@ class asd_corr_desc(ctypes.Structure):
                 ("bin_width", ctypes.c_double), ("n_bins", ctypes.c_int32),
                 ("n_q", ctypes.c_int32), ("q", c_f64p), ("tile_n", ctypes.c_int32),
                 ("raster_m", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("k_chunks", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class asd_system(ctypes.Structure):
@@ -136,7 +137,7 @@ class CorrPlan:
 
     def __init__(self, N, F, T0, n_t, precision="split_bf16", S=1, center=False, coords=None,
                  L=(1, 1, 1), periodic=False, pos=None, bin_width=1.0, n_bins=0, q=None,
-                 tile_n=0, raster_m=0, stages=0):
+                 tile_n=0, raster_m=0, stages=0, k_chunks=0, cluster=0):
         d = asd_corr_desc()
         d.n_sites, d.n_frames, d.n_samples, d.T0, d.n_t = N, F, S, T0, n_t
         d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -165,6 +166,8 @@ class CorrPlan:
         d.tile_n = int(tile_n)
         d.raster_m = int(raster_m)
         d.stages = int(stages)
+        d.k_chunks = int(k_chunks)
+        d.cluster = int(cluster)
         self.desc = d
         self.N, self.F, self.S, self.T0, self.n_t = N, F, S, T0, n_t
         self.n_bins, self.n_q = int(n_bins), int(d.n_q)

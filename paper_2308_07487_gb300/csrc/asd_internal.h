@@ -45,6 +45,7 @@ constexpr int kBM = 128;            // rows (sites i) per tile = TMEM lanes
 constexpr int kMaxCopies = 8;       // shifted operand copies (16-byte TMA start rule)
 constexpr int kMaxProblems = 4096;  // batched work list
 constexpr size_t kMinSmem = 120 * 1024;  // tensor-core kernel: one CTA per SM
+constexpr int kLutMax = 4096;            // largest d2 -> bin table kept in shared memory
 
 // Epilogue geometry + output parameters of one problem (device-visible POD).
 struct EpiParams {
@@ -59,10 +60,8 @@ struct EpiParams {
     const int4 *coords;     // [N] (x,y,z,0)
     const float4 *pos;      // [N] (x,y,z,0)
     const float *thr;       // [n_bins+2]: FP32 thresholds (k*w)^2 rounded up; thr[0]=0
-    const float4 *box_lo;   // [n_tiles_m_all] lower corner of each 128-row block (window mode)
-    const float4 *box_hi;
-    const float4 *cbox_lo;  // [n_tiles_n] column blocks
-    const float4 *cbox_hi;
+    const uint16_t *lut;    // lattices: bin of every integer d2 < n_lut (n_bins = dropped)
+    int n_lut;              // 0 when the table is not used
     const float2 *cs;       // [N][n_q] (cos, sin)(q.r_i)
     double *C_sum;          // [n_t][n_bins]
     double *Sq_sum;         // [n_t][n_q]
@@ -84,6 +83,7 @@ struct TcProblem {
     int nkb;                          // K blocks per sample
     int n_copies;                     // shifted copies (8 for BF16, 4 for TF32)
     int group_m;                      // raster group height (row tiles)
+    int k_chunks;                     // partial accumulators along K per tile
     EpiParams epi;
 };
 
@@ -128,7 +128,8 @@ struct asd_corr_plan {
     int4 *coords;
     float4 *pos;
     float *thr;
-    float4 *box;               // [2][tiles_m_all] row-block boxes, then [2][tiles_n] column boxes
+    uint16_t *lut;             // lattice d2 -> bin table (nullptr when d2 can reach kLutMax)
+    int n_lut;
     float2 *cs;
     int tiles_m_all, tiles_n;
     int use_window;
@@ -140,6 +141,8 @@ struct asd_corr_plan {
     asd::TcProblem *h_prob;
     int stages;
     size_t smem_bytes;
+    int CL;                    // cluster size (CTAs sharing a B tile)
+    int k_chunks;
     // last asd_pair_corr_prepare
     const float *prepared_traj;
     int64_t prepared_begin, prepared_end;
@@ -157,6 +160,11 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
 int tc_configure(asd_corr_plan *p);    // stages / smem for the plan's form
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
               int BN, int swizzle_bytes, int stages, size_t smem, int max_nw, int max_nb,
-              int max_nq, int sm_count, cudaStream_t s);
-size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN);
+              int max_nq, int max_nlut, int cl, int sm_count, cudaStream_t s);
+// work items of one problem: n_t * k_chunks * ceil(tiles_m / cl) * tiles_n
+inline int64_t tc_work_items(int n_t, int k_chunks, int tiles_m, int tiles_n, int cl)
+{
+    return (int64_t)n_t * k_chunks * ((tiles_m + cl - 1) / cl) * tiles_n;
+}
+size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut);
 }  // namespace asd

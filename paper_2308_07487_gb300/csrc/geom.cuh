@@ -10,8 +10,8 @@
 
 namespace asd {
 
-// Squared minimum-image distance of two lattice sites (exact integer, as float).
-__device__ __forceinline__ float lattice_d2(int4 a, int4 b, int Lx, int Ly, int Lz, int periodic)
+// Squared minimum-image distance of two lattice sites (exact integer).
+__device__ __forceinline__ int lattice_d2i(int4 a, int4 b, int Lx, int Ly, int Lz, int periodic)
 {
     int dx = abs(b.x - a.x), dy = abs(b.y - a.y), dz = abs(b.z - a.z);
     if (periodic) {
@@ -19,7 +19,13 @@ __device__ __forceinline__ float lattice_d2(int4 a, int4 b, int Lx, int Ly, int 
         dy = min(dy, Ly - dy);
         dz = min(dz, Lz - dz);
     }
-    return (float)(dx * dx + dy * dy + dz * dz);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// The same as a float (exact: lattice d2 stays far below 2^24).
+__device__ __forceinline__ float lattice_d2(int4 a, int4 b, int Lx, int Ly, int Lz, int periodic)
+{
+    return (float)lattice_d2i(a, b, Lx, Ly, Lz, periodic);
 }
 
 // FP32 positions rule: dx = x_j - x_i, d2 = fma(dz,dz, fma(dy,dy, dx*dx)), no contraction.

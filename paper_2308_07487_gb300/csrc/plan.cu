@@ -84,6 +84,8 @@ static EpiParams epi_of(const asd_corr_plan *p)
     e.coords = p->coords;
     e.pos = p->pos;
     e.thr = p->thr;
+    e.lut = p->lut;
+    e.n_lut = p->n_lut;
     e.cs = p->cs;
     return e;
 }
@@ -145,7 +147,7 @@ static int encode_2d(CUtensorMap *m, void *base, int elem_bytes, uint64_t inner,
 static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int64_t row_end)
 {
     memset(tp, 0, sizeof(*tp));
-    const int box_rows_b = p->BN;
+    const int box_rows_b = p->BN / p->CL;  // each CTA of a cluster loads a slice of B
     for (int pl = 0; pl < p->n_planes; ++pl) {
         for (int c = 0; c < p->n_copies; ++c) {
             int rc = encode_2d(&tp->mapA[pl][c], p->A[pl][c], p->elem_bytes, (uint64_t)p->Rpad,
@@ -168,7 +170,8 @@ static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int6
     tp->nkb = (int)(p->Kseg / p->BK);
     tp->n_copies = p->n_copies;
     tp->group_m = p->d.raster_m > 0 ? p->d.raster_m : 16;
-    tp->n_tiles = (int64_t)p->n_t * tp->tiles_m * tp->tiles_n;
+    tp->k_chunks = p->k_chunks;
+    tp->n_tiles = tc_work_items(p->n_t, p->k_chunks, tp->tiles_m, tp->tiles_n, p->CL);
     tp->epi = epi_of(p);
     return ASD_OK;
 }
@@ -220,6 +223,7 @@ void asd_pair_corr_plan_destroy(asd_corr_plan *p)
     cudaFree(p->coords);
     cudaFree(p->pos);
     cudaFree(p->thr);
+    cudaFree(p->lut);
     cudaFree(p->cs);
     cudaFree(p->inv_counts);
     cudaFree(p->d_prob);
@@ -256,7 +260,9 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
     ASD_CHECK_ARG(d->tile_n == 0 || d->tile_n == 128 || d->tile_n == 256, "tile_n: 0, 128, 256");
     ASD_CHECK_ARG(d->raster_m >= 0 && d->raster_m <= 64, "raster_m: 0..64");
     ASD_CHECK_ARG(d->stages == 0 || (d->stages >= 2 && d->stages <= 8), "stages: 0 or 2..8");
-    for (int k = 0; k < 5; ++k) ASD_CHECK_ARG(d->reserved[k] == 0, "reserved fields must be 0");
+    ASD_CHECK_ARG(d->k_chunks >= 0 && d->k_chunks <= 16, "k_chunks: 0..16");
+    ASD_CHECK_ARG(d->cluster == 0 || d->cluster == 1 || d->cluster == 4, "cluster: 0, 1 or 4");
+    for (int k = 0; k < 3; ++k) ASD_CHECK_ARG(d->reserved[k] == 0, "reserved fields must be 0");
     if (d->geometry == ASD_GEOM_LATTICE) {
         ASD_CHECK_ARG(d->coords, "coords required for lattice geometry");
         for (int a = 0; a < 3; ++a) ASD_CHECK_ARG(d->L[a] >= 1 && d->L[a] <= 1 << 20, "bad L");
@@ -321,12 +327,38 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         p->BN = d->tile_n ? d->tile_n : (p->N <= 4096 ? 128 : 256);
         p->Rpad = (R + 7) / 8 * 8;
         p->Kseg = ((int64_t)3 * d->T0 + p->BK - 1) / p->BK * p->BK;
+        // clusters of 4 row tiles share each B tile once there are enough row tiles
+        const int64_t tiles_m_all = (p->N + kBM - 1) / kBM;
+        // (measured: sharing B by multicast does not pay here, so clusters are opt-in)
+        p->CL = d->cluster ? d->cluster : 1;
+        (void)tiles_m_all;
+        // K chunks: split-BF16 is the FP32-accurate form; each chunk's accumulator starts
+        // from zero, bounding the FP32 accumulation error of the tensor core to ~1024
+        // terms per partial sum (the other forms are limited by their operand rounding)
+        const int64_t nk = (int64_t)p->S * (p->Kseg / p->BK);
+        int kc = d->k_chunks;
+        if (kc == 0)
+            kc = d->precision == ASD_SPLIT_BF16 ? (int)((p->S * p->Kseg + 1023) / 1024) : 1;
+        if (kc > 16) kc = 16;
+        if (kc > nk) kc = (int)nk;
+        p->k_chunks = kc < 1 ? 1 : kc;
     } else {
         p->Rpad = 0;
         p->Kseg = ((int64_t)3 * d->T0 + 15) / 16 * 16;
         p->BN = 128;
     }
     p->Kb = p->S * p->Kseg;
+
+    // lattice d2 -> bin table size (largest minimum-image d2 + 1), built with the tables
+    p->n_lut = 0;
+    if (d->geometry == ASD_GEOM_LATTICE && p->n_bins > 0) {
+        int64_t max_d2 = 0;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t m = d->periodic ? d->L[a] / 2 : d->L[a] - 1;
+            max_d2 += m * m;
+        }
+        if (max_d2 < kLutMax) p->n_lut = (int)(max_d2 + 1);
+    }
 
     // ---- bins: private window per epilogue thread ----
     if (tc) {
@@ -402,6 +434,29 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         }
         if (cudaMemcpy(p->thr, thr.data(), sizeof(float) * (nb + 2), cudaMemcpyHostToDevice))
             return fail(ASD_ECUDA);
+        // lattices: d2 is an integer below max_d2 + 1, so the bin of every possible d2 can
+        // be tabulated (same rule: largest k with (k w)^2 <= d2, n_bins when dropped)
+        if (p->n_lut > 0) {
+            const int64_t max_d2 = p->n_lut - 1;
+            {
+                std::vector<uint16_t> lut((size_t)max_d2 + 1);
+                for (int64_t d2 = 0; d2 <= max_d2; ++d2) {
+                    int k = 0;
+                    while (k < nb && ((double)(k + 1) * d->bin_width) * ((double)(k + 1) * d->bin_width) <=
+                                         (double)d2)
+                        ++k;
+                    lut[d2] = (uint16_t)k;  // k == nb only when (nb w)^2 <= d2: dropped
+                }
+                // (size fixed before the shared-memory configuration)
+                if (cudaMalloc(&p->lut, sizeof(uint16_t) * lut.size()) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(ASD_ENOMEM);
+                }
+                if (cudaMemcpy(p->lut, lut.data(), sizeof(uint16_t) * lut.size(),
+                               cudaMemcpyHostToDevice))
+                    return fail(ASD_ECUDA);
+            }
+        }
         if (p->n_q > 0) {
             std::vector<float2> cs((size_t)p->N * p->n_q);
             for (int64_t i = 0; i < p->N; ++i) {
@@ -517,11 +572,11 @@ int asd_pair_corr_contract(asd_corr_plan *p, int64_t row_begin, int64_t row_end,
     ov.row_begin = (int)row_begin;
     ov.row_end = (int)row_end;
     ov.tiles_m = (int)((row_end - row_begin + kBM - 1) / kBM);
-    ov.n_tiles = (int64_t)p->n_t * ov.tiles_m * p->h_prob->tiles_n;
+    ov.n_tiles = tc_work_items(p->n_t, p->k_chunks, ov.tiles_m, p->h_prob->tiles_n, p->CL);
     ov.C_sum = C_sum;
     ov.Sq_sum = Sq_sum;
     return launch_tc(p->d_prob, 1, ov.n_tiles, ov, p->prec, p->BN, p->swizzle_bytes, p->stages,
-                     p->smem_bytes, p->NW, p->n_bins, p->n_q, p->sm_count, s);
+                     p->smem_bytes, p->NW, p->n_bins, p->n_q, p->n_lut, p->CL, p->sm_count, s);
 }
 
 int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs, int n,
@@ -530,12 +585,12 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     ASD_CHECK_ARG(plans && trajs && n >= 1 && n <= kMaxProblems, "bad batch");
     const asd_corr_plan *p0 = plans[0];
     ASD_CHECK_ARG(p0 && p0->tc, "batched launch needs tensor-core plans");
-    int max_nw = 0, max_nb = 0, max_nq = 0, stages = 1 << 30;
+    int max_nw = 0, max_nb = 0, max_nq = 0, max_nlut = 0, stages = 1 << 30;
     size_t smem = 0;
     for (int k = 0; k < n; ++k) {
         const asd_corr_plan *p = plans[k];
         ASD_CHECK_ARG(p && trajs[k], "null plan or trajectory");
-        ASD_CHECK_ARG(p->tc && p->prec == p0->prec && p->BN == p0->BN,
+        ASD_CHECK_ARG(p->tc && p->prec == p0->prec && p->BN == p0->BN && p->CL == p0->CL,
                       "batched plans must share precision and tile width");
         ASD_CHECK_ARG(p->device == p0->device, "plans on different devices");
         ASD_CHECK_ARG(p->n_bins == 0 || (C_sum && C_sum[k]), "C_sum required");
@@ -544,6 +599,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
         max_nw = p->NW > max_nw ? p->NW : max_nw;
         max_nq = p->n_q > max_nq ? p->n_q : max_nq;
         max_nb = p->n_bins > max_nb ? p->n_bins : max_nb;
+        max_nlut = p->n_lut > max_nlut ? p->n_lut : max_nlut;
     }
     // one smem configuration for the whole batch
     {
@@ -552,7 +608,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
         for (int k = 0; k < n; ++k) {
             (void)k;
         }
-        epi = tc_epilogue_smem(max_nw, max_nb, max_nq, p0->BN);
+        epi = tc_epilogue_smem(max_nw, max_nb, max_nq, p0->BN, max_nlut);
         const size_t cap = 232448 - 2048;
         if (epi + 2 * stage_bytes > cap) {
             set_error_text("batched epilogue does not fit shared memory");
@@ -578,7 +634,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
         h[k].row_begin = 0;
         h[k].row_end = (int)p->N;
         h[k].tiles_m = (int)((p->N + kBM - 1) / kBM);
-        h[k].n_tiles = (int64_t)p->n_t * h[k].tiles_m * h[k].tiles_n;
+        h[k].n_tiles = tc_work_items(p->n_t, p->k_chunks, h[k].tiles_m, h[k].tiles_n, p->CL);
         h[k].tile_begin = total;
         h[k].epi.C_sum = C_sum ? C_sum[k] : nullptr;
         h[k].epi.Sq_sum = Sq_sum ? Sq_sum[k] : nullptr;
@@ -607,7 +663,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     }
     TcOverride ov{};
     return launch_tc(dbuf, n, total, ov, p0->prec, p0->BN, p0->swizzle_bytes, stages, smem, max_nw,
-                     max_nb, max_nq, p0->sm_count, s);
+                     max_nb, max_nq, max_nlut, p0->CL, p0->sm_count, s);
 }
 
 int asd_pair_corr_normalize(const asd_corr_plan *p, const double *C_sum, const double *Sq_sum,

@@ -149,3 +149,25 @@ def test_tile_widths_static_fm(asd, form, tile_n):
     C = got["C_sum"][:, full] / (8 * n[full])
     # identical products do not average: the worst-case per-product bound applies
     np.testing.assert_allclose(C, 1.0, rtol=0, atol=elem_bound(form, 24))
+
+
+@pytest.mark.parametrize("form", ["split_bf16", "bf16", "tf32"])
+@pytest.mark.parametrize("cluster,k_chunks", [(1, 1), (1, 3), (4, 1), (4, 4)])
+def test_cluster_and_k_chunks(asd, form, cluster, k_chunks):
+    """4-CTA clusters sharing B by multicast (9^3 = 729 sites: 6 row tiles, so the second
+    cluster has two surplus CTAs) and K split into partial accumulators; a row range
+    that starts mid-tile as well."""
+    lat = synth.hypercubic(9, 3, True)
+    tr = synth.traj_precess(lat.n_sites, 70, seed=21, S=2)
+    for rows in (None, (100, 700)):
+        tr2 = np.ascontiguousarray(tr)
+        N, S, F, _ = tr2.shape
+        plan = asd.CorrPlan.for_lattice(lat, F, 40, 6, 0.5, 14, precision=form, S=S,
+                                        cluster=cluster, k_chunks=k_chunks)
+        d_tr = torch.from_numpy(tr2).cuda()
+        C = torch.zeros((6, 14), dtype=torch.float64, device="cuda")
+        plan.run(d_tr, C, rows=rows)
+        assert asd.sync_status() == 0
+        ref = oracle_ref(lat, tr, 40, 6, 0.5, 14, rows=rows)
+        assert_parity({"C_sum": C.cpu().numpy()}, ref, form)
+        plan.close()
