@@ -98,7 +98,8 @@ typedef struct asd_corr_desc {
                                FP32 accumulation error; the epilogue adds them exactly   */
     int32_t cluster;        /* 0 = automatic, 1, or 4: CTAs sharing one B tile via TMA
                                multicast                                                 */
-    int32_t reserved[3];    /* must be zero                                            */
+    int32_t epi_warps;      /* 0 = automatic, 4 or 8 epilogue warps per CTA            */
+    int32_t reserved[2];    /* must be zero                                            */
 } asd_corr_desc;
 
 typedef struct asd_corr_plan asd_corr_plan;

@@ -1,908 +1,21 @@
-// Tensor-core forms (TF32, BF16, split-BF16): fused contraction + reduction epilogue.
-//
-// The method casts the pair sum of Eq. 4 / Eq. 5 for one time displacement as a GEMM
-// G_t = A_t B^T (Section 3.2) and fuses the element-wise reduction that follows it --
-// the bin sums or the phase-weighted inner product of Eq. 3 / Eq. 6 -- into the GEMM
-// epilogue so that G_t never reaches memory (Sections 3.3-3.4).  On sm_103a this is:
-//
-//   warp 0      TMA producer: streams 128-row A tiles (K-offset windows of the
-//               trajectory copies) and BN-row B tiles into a shared-memory ring;
-//   warp 1      allocates TMEM and, from one thread, issues tcgen05.mma into one of two
-//               128 x BN FP32 accumulators in tensor memory (double buffered), committing
-//               each stage back to the ring and each finished tile to the epilogue;
-//   warps 2-5   epilogue: tcgen05.ld one accumulator row per thread and reduce it --
-//               per-thread private FP32 bins in shared memory (conflict-free [bin][row]
-//               layout), phase weights from per-site cos/sin tables -- then FP64.
-//
-// The accumulator living in TMEM plays the role of the paper's OTF_SM shared-memory
-// staging of the C tile (Section 3.4): the epilogue never holds the tile in registers.
-// The per-pair phase factor uses cos(a - b) = cos a cos b + sin a sin b on tables made
-// once per plan, so no transcendental is evaluated per pair (the register-spill
-// problem of the paper's OTF_REG variant).
-//
-// Persistent: one CTA per SM walks a static round-robin list of
-// (problem, t, row tile, column tile) work items, grouped 8 row tiles at a time so
-// concurrently running CTAs share A and B panels in L2.  Several problems (a batched
-// ensemble) share the list.  Every wait is bounded: after kTimeoutNs a role records
-// an error in the device error word and stops; the CTA then drains its own in-flight
-// copies and MMAs, frees TMEM and exits.
-#include <cuda_bf16.h>
-
-#include "asd_internal.h"
-#include "geom.cuh"
+// Tensor-core forms: shared-memory configuration of a plan and launch dispatch.  The
+// kernel itself is in pc_tc_kernel.cuh, instantiated once per precision form in
+// pc_tc_bf16.cu, pc_tc_tf32.cu and pc_tc_split.cu (compiled in parallel).
+#include "pc_tc_kernel.cuh"
 
 namespace asd {
-namespace {
 
-constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter, half the columns each
-constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kThreads = 64 + kEpiThreads;   // + TMA warp + MMA warp
-constexpr int kQC = 16;                       // q-vectors per epilogue pass
-constexpr unsigned long long kTimeoutNs = 4000000000ull;
-// Private bins are a [bin][256] array: epilogue thread (row r, column half h) only ever
-// touches column r + 128 h, i.e. bank r mod 32, so the per-pair accumulation is free of
-// bank conflicts whatever the bins of the 32 lanes are (with an odd stride, bins that
-// fall as the row index rises put a whole warp on one bank).  The per-tile flush reads
-// whole bin rows warp-cooperatively.
-constexpr int kBinStride = 256;
+// instantiated in the per-form translation units
+extern template int tc_launch_form<ASD_BF16>(const TcLaunchArgs &, size_t, int, int, int, int,
+                                             cudaStream_t);
+extern template int tc_launch_form<ASD_TF32>(const TcLaunchArgs &, size_t, int, int, int, int,
+                                             cudaStream_t);
+extern template int tc_launch_form<ASD_SPLIT_BF16>(const TcLaunchArgs &, size_t, int, int, int,
+                                                   int, cudaStream_t);
 
-// ------------------------------------------------------------------------------------
-// PTX wrappers
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t saddr(const void *p)
+size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut, int ew)
 {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long gtimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity; false after kTimeoutNs (the error
-// word then holds `code`).
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code)
-{
-    if (mbar_test(bar, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if ((it & 1023u) == 0 && gtimer() - t0 > kTimeoutNs) {
-            atomicCAS(err, 0, code);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                            int x, int y)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
-        : "memory");
-}
-
-// Multicast variant: the box lands at the same shared-memory offset (and signals the
-// mbarrier at the same offset) in every CTA of `mask` within the cluster.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                               int x, int y, uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                     : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_slot, uint32_t ncols)
-{
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_slot),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// Arrive (when this thread's MMAs complete) on the mbarrier at offset `bar` in every CTA
-// of `mask`.
-__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar),
-        "h"(mask)
-        : "memory");
-}
-
-template <bool TF32>
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                       uint32_t acc)
-{
-    if (TF32)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-    else
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-// 32 lanes x 32 consecutive 32-bit columns; the wait is tied to the registers so no
-// use of them can be scheduled before it.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-        "%28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
-                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
-                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
-                   "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
-}
-
-__device__ __forceinline__ void epi_sync()
-{
-    __syncwarp();
-    asm volatile("bar.sync 1, 256;" ::: "memory");
-}
-
-// Epilogue barrier that also ANDs a flag over the 128 epilogue threads, so that every
-// thread takes the same branch after a bounded wait.
-__device__ __forceinline__ bool epi_sync_and(bool v)
-{
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"((uint32_t)v)
-        : "memory");
-    return r != 0;
-}
-
-// Shared-memory matrix descriptor, K-major, swizzled (128B: mode 2, 64B: mode 4).
-// SBO = 8 rows x swizzle span; LBO unused for swizzled K-major; version 1 (sm_100).
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, int swb)
-{
-    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)((8u * swb) >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)(swb == 128 ? 2 : 4) << 61;
-    return d;
-}
-
-// Instruction descriptor: FP32 accumulate, A/B = BF16 (1) or TF32 (2), both K-major.
-__host__ __device__ constexpr uint32_t idesc(bool tf32, int N)
-{
-    return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) |
-           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-}
-
-// ------------------------------------------------------------------------------------
-// shared-memory layout of the epilogue region
-// ------------------------------------------------------------------------------------
-struct EpiLayout {
-    uint32_t cacc, qacc, qred, bins, fb, colgeo, colcs, boxred, thr, total;
-};
-
-__host__ __device__ inline uint32_t take(uint32_t &o, uint32_t bytes)
-{
-    o = (o + 15u) & ~15u;
-    uint32_t r = o;
-    o += bytes;
-    return r;
-}
-
-__host__ __device__ inline EpiLayout epi_layout(int NW, int nb, int nq, int BN, int nlut)
-{
-    EpiLayout L;
-    uint32_t o = 0;
-    L.cacc = take(o, 8u * (nb > 0 ? nb : 1));
-    L.qacc = take(o, 8u * (nq > 0 ? nq : 1));
-    L.qred = take(o, 8u * kEpiWarps * kQC);
-    L.bins = take(o, 4u * (NW + 1) * kBinStride);
-    L.fb = take(o, 4u * (nb > 0 ? nb : 1));
-    L.colgeo = take(o, 16u * BN);
-    L.colcs = nq > 0 ? take(o, 8u * BN * kQC) : 0u;
-    L.boxred = take(o, 4u * kEpiWarps * 12);
-    // bin thresholds (FP32) or, for lattices, the d2 -> bin table (uint16), same region
-    const uint32_t tb = 4u * (nb + 2), lb = 2u * nlut;
-    L.thr = take(o, tb > lb ? tb : lb);
-    L.total = (o + 1023u) & ~1023u;
-    return L;
-}
-
-struct TileInfo {
-    int p, t, m0, n0, row_end;
-    int kg0, kg1;  // K blocks [kg0, kg1) of the S * nkb blocks of a full row
-};
-
-// Work item `tau` -> (problem, t, K chunk, row tile, column tile).  With clusters of CL
-// CTAs, a work item is a cluster tile: CL consecutive row tiles that share one column
-// tile; CTA `rank` of the cluster takes row tile mc * CL + rank.  K chunks split the
-// contraction so that each partial accumulator starts from zero (see kChunkK).
-template <int CL>
-__device__ __forceinline__ TileInfo decode(const TcProblem *__restrict__ probs, int n_probs,
-                                           const TcOverride &ov, int64_t tau, int BN, int rank)
-{
-    int p = 0;
-    if (n_probs > 1) {
-        int lo = 0, hi = n_probs - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (probs[mid].tile_begin <= tau) lo = mid;
-            else hi = mid - 1;
-        }
-        p = lo;
-    }
-    const TcProblem &P = probs[p];
-    const int tiles_m = ov.active ? ov.tiles_m : P.tiles_m;
-    const int row_begin = ov.active ? ov.row_begin : P.row_begin;
-    const int64_t l = tau - (ov.active ? 0 : P.tile_begin);
-    const int tiles_mc = (tiles_m + CL - 1) / CL;
-    const int64_t per_kc = (int64_t)tiles_mc * P.tiles_n;
-    const int kch = P.k_chunks;
-    TileInfo ti;
-    ti.p = p;
-    ti.t = (int)(l / (per_kc * kch));
-    const int64_t rem0 = l % (per_kc * kch);
-    const int kc = (int)(rem0 / per_kc);
-    const int64_t rem = rem0 % per_kc;
-    const int G = max(1, P.group_m / CL);
-    const int64_t gspan = (int64_t)G * P.tiles_n;
-    const int first_m = (int)(rem / gspan) * G;
-    const int gsz = min(G, tiles_mc - first_m);
-    const int64_t r2 = rem % gspan;
-    ti.m0 = row_begin + ((first_m + (int)(r2 % gsz)) * CL + rank) * kBM;
-    ti.n0 = (int)(r2 / gsz) * BN;
-    ti.row_end = ov.active ? ov.row_end : P.row_end;
-    const int nk = P.S * P.nkb;
-    ti.kg0 = (int)((int64_t)kc * nk / kch);
-    ti.kg1 = (int)((int64_t)(kc + 1) * nk / kch);
-    return ti;
-}
-
-// Per-tile constants of the binning epilogue, held in registers.
-struct BinArgs {
-    int Lx, Ly, Lz, periodic;
-    float inv_w;
-    int nb, blo, nwp, trash;
-};
-
-enum { GEO_PERIODIC = 0, GEO_OPEN = 1, GEO_POS = 2, GEO_LUT_PERIODIC = 3, GEO_LUT_OPEN = 4 };
-
-// Bin 32 consecutive columns of one accumulator row.  Phase 1 computes the exact bin
-// slot of every pair (loads of geometry and thresholds only, so the 32 independent
-// chains overlap); phase 2 adds the 32 values into this thread's private bins (its
-// column of a [bin][129] array) or, in window mode, into the shared fallback bins.
-template <int GEO, bool WINDOW>
-__device__ __forceinline__ void bin_chunk(const uint32_t (&g)[32], float scale, int4 ri, float4 rp,
-                                          const float4 *__restrict__ cgeo,
-                                          const float *__restrict__ thr,
-                                          float *__restrict__ myb, float *__restrict__ fb,
-                                          const BinArgs ba)
-{
-    int slot[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        const float4 cg = cgeo[k];
-        int b;
-        if (GEO == GEO_POS) {
-            b = bin_of_d2(position_d2(rp, cg), ba.inv_w, ba.nb, thr);
-        } else {
-            const int4 cj = make_int4(__float_as_int(cg.x), __float_as_int(cg.y),
-                                      __float_as_int(cg.z), 0);
-            const bool per = GEO == GEO_PERIODIC || GEO == GEO_LUT_PERIODIC;
-            const int d2 = lattice_d2i(ri, cj, ba.Lx, ba.Ly, ba.Lz, per);
-            if (GEO == GEO_LUT_PERIODIC || GEO == GEO_LUT_OPEN)
-                b = reinterpret_cast<const uint16_t *>(thr)[d2];
-            else
-                b = bin_of_d2((float)d2, ba.inv_w, ba.nb, thr);
-        }
-        if (WINDOW) {
-            const int lb = b - ba.blo;
-            slot[k] = (unsigned)lb < (unsigned)ba.nwp ? lb : (b < ba.nb ? -1 - b : ba.trash);
-        } else {
-            slot[k] = b < ba.nb ? b : ba.trash;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        const float val = scale * __uint_as_float(g[k]);
-        if (WINDOW && slot[k] < 0) atomicAdd(&fb[-1 - slot[k]], val);
-        else myb[slot[k] * kBinStride] += val;
-    }
-}
-
-struct LaunchArgs {
-    const TcProblem *probs;
-    int n_probs;
-    int64_t total_tiles;
-    TcOverride ov;
-    int stages;
-    int NW, NB, NQ, NLUT;  // epilogue layout maxima
-    int *err;
-};
-
-// ------------------------------------------------------------------------------------
-// the kernel
-// ------------------------------------------------------------------------------------
-template <int FORM, int BN, int SWB, int CL>
-__global__ void __launch_bounds__(kThreads, 1) pc_tc_kernel(const __grid_constant__ LaunchArgs args)
-{
-    constexpr bool kTF32 = FORM == ASD_TF32;
-    constexpr int kPlanes = FORM == ASD_SPLIT_BF16 ? 2 : 1;
-    constexpr uint32_t kABytes = kBM * SWB;
-    constexpr uint32_t kBBytes = BN * SWB;
-    // With a cluster of CL CTAs (consecutive row tiles, one column tile), each CTA loads
-    // BN/CL rows of the B tile and multicasts them to every CTA of the cluster.
-    constexpr int kBSlice = BN / CL;
-    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
-    constexpr uint32_t kStageBytes = kPlanes * (kABytes + kBBytes);
-    constexpr int kKSteps = SWB / 32;          // one MMA k-step covers 32 bytes of K
-    constexpr int kBK = SWB / (kTF32 ? 4 : 2); // K elements per stage
-    constexpr uint32_t kIdesc = idesc(kTF32, BN);
-    constexpr uint32_t kTmemCols = 2 * BN;
-
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    // 1024-byte aligned base for the swizzled tiles
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                ~(uintptr_t)1023);
-    const int stages = args.stages;
-    uint8_t *tiles = smem;
-    uint8_t *epi = tiles + (size_t)stages * kStageBytes;
-    const EpiLayout EL = epi_layout(args.NW, args.NB, args.NQ, BN, args.NLUT);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(epi + EL.total);
-    // bars: full[stages], empty[stages], tfull[2], tempty[2], drain
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 5);
-    const uint32_t full0 = saddr(bars), empty0 = saddr(bars + stages);
-    const uint32_t tfull0 = saddr(bars + 2 * stages), tempty0 = saddr(bars + 2 * stages + 2);
-    const uint32_t drain = saddr(bars + 2 * stages + 4);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < stages; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            // a stage is free again once the MMAs of every CTA of the cluster consumed it
-            mbar_init(empty0 + 8 * s, CL);
-        }
-        for (int a = 0; a < 2; ++a) {
-            mbar_init(tfull0 + 8 * a, 1);
-            mbar_init(tempty0 + 8 * a, kEpiWarps);
-        }
-        mbar_init(drain, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 1) tmem_alloc(saddr(tmem_slot), kTmemCols);
-    tc_before();
-    __syncthreads();
-    tc_after();
-    // every CTA's barriers are initialised before any CTA multicasts into them
-    if (CL > 1) cluster_sync();
-    const uint32_t tmem = *tmem_slot;
-    const TcProblem *__restrict__ probs = args.probs;
-    const int rank = CL > 1 ? (int)cluster_rank() : 0;
-    const int64_t cid = blockIdx.x / CL, n_clusters = gridDim.x / CL;
-
-    if (warp == 0) {
-        // ======================= TMA producer =======================
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            bool ok = true;
-            for (int64_t tau = cid; tau < args.total_tiles && ok; tau += n_clusters) {
-                const TileInfo ti = decode<CL>(probs, args.n_probs, args.ov, tau, BN, rank);
-                const TcProblem &P = probs[ti.p];
-                for (int kg = ti.kg0; kg < ti.kg1; ++kg) {
-                    const int s = kg / P.nkb, kb = kg % P.nkb;
-                    const int xw = s * P.F3 + 3 * ti.t;
-                    const int c = xw % P.n_copies;
-                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, args.err, DEV_TIMEOUT_TMA)) {
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t fb = full0 + 8 * stage;
-                    mbar_expect_tx(fb, kStageBytes);
-                    uint8_t *st = tiles + (size_t)stage * kStageBytes;
-#pragma unroll
-                    for (int pl = 0; pl < kPlanes; ++pl) {
-                        tma_load_2d(saddr(st + pl * kABytes), &P.mapA[pl][c], fb,
-                                    xw - c + kb * kBK, ti.m0);
-                        const uint32_t bdst = saddr(st + kPlanes * kABytes + pl * kBBytes);
-                        if (CL == 1)
-                            tma_load_2d(bdst, &P.mapB[pl], fb, s * P.Kseg + kb * kBK, ti.n0);
-                        else
-                            tma_load_2d_mc(bdst + rank * kBSlice * SWB, &P.mapB[pl], fb,
-                                           s * P.Kseg + kb * kBK, ti.n0 + rank * kBSlice, kMask);
-                    }
-                    if (++stage == stages) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
-                }
-            }
-            // drain: wait until the last fill of every stage has landed
-            for (int k = 0; k < stages; ++k) {
-                if (--stage < 0) {
-                    stage = stages - 1;
-                    phase ^= 1;
-                }
-                // the most recent fill of `stage` used parity `phase`; if that stage was never
-                // filled, its barrier is still in phase 0 and parity 1 reads as complete
-                mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_TMA);
-            }
-        }
-    } else if (warp == 1) {
-        // ======================= MMA issuer =======================
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            uint32_t v = 0;
-            bool ok = true;
-            for (int64_t tau = cid; tau < args.total_tiles && ok; tau += n_clusters, ++v) {
-                const TileInfo ti = decode<CL>(probs, args.n_probs, args.ov, tau, BN, rank);
-                const uint32_t acc = v & 1, use = v >> 1;
-                if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, args.err, DEV_TIMEOUT_MMA)) {
-                    ok = false;
-                    break;
-                }
-                tc_after();
-                const uint32_t d = tmem + acc * BN;
-                for (int kg = ti.kg0; kg < ti.kg1; ++kg) {
-                    const int kb = kg - ti.kg0;  // 0 for the first block of this chunk
-                    if (!mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_MMA)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_after();
-                    uint8_t *st = tiles + (size_t)stage * kStageBytes;
-                    const uint64_t a0 = sdesc(saddr(st), SWB);
-                    const uint64_t b0 = sdesc(saddr(st + kPlanes * kABytes), SWB);
-#pragma unroll
-                    for (int ks = 0; ks < kKSteps; ++ks) {
-                        const uint64_t off = (uint64_t)(ks * 32) >> 4;
-                        const uint32_t first = (kb | ks) != 0;
-                        if (kPlanes == 1) {
-                            tc_mma<kTF32>(d, a0 + off, b0 + off, kIdesc, first);
-                        } else {
-                            const uint64_t a1 = sdesc(saddr(st + kABytes), SWB);
-                            const uint64_t b1 = sdesc(saddr(st + 2 * kABytes + kBBytes), SWB);
-                            tc_mma<false>(d, a0 + off, b0 + off, kIdesc, first);  // hi*hi
-                            tc_mma<false>(d, a0 + off, b1 + off, kIdesc, 1u);     // hi*lo
-                            tc_mma<false>(d, a1 + off, b0 + off, kIdesc, 1u);     // lo*hi
-                        }
-                    }
-                    if (CL == 1) tc_commit(empty0 + 8 * stage);
-                    else tc_commit_mc(empty0 + 8 * stage, kMask);
-                    if (++stage == stages) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
-                }
-                if (!ok) break;
-                tc_commit(tfull0 + 8 * acc);
-            }
-            // drain every MMA this thread issued before TMEM is released
-            tc_commit(drain);
-            mbar_wait(drain, 0, args.err, DEV_TIMEOUT_MMA);
-        }
-    } else {
-        // ======================= epilogue =======================
-        const int et = threadIdx.x - 64;          // 0..127
-        const int q4 = warp & 3;                  // TMEM lane quarter of this warp
-        const int r = q4 * 32 + lane;             // accumulator row = tile row
-        const int ew = warp - 2;                  // epilogue warp 0..7
-        const int half = ew >> 2;                 // which half of the columns
-        const int ch0 = half * (BN / 64), ch1 = ch0 + BN / 64;  // its 32-column chunks
-        float *bins = reinterpret_cast<float *>(epi + EL.bins);
-        float *fb = reinterpret_cast<float *>(epi + EL.fb);
-        double *cacc = reinterpret_cast<double *>(epi + EL.cacc);
-        double *qacc = reinterpret_cast<double *>(epi + EL.qacc);
-        double *qred = reinterpret_cast<double *>(epi + EL.qred);
-        float4 *colgeo = reinterpret_cast<float4 *>(epi + EL.colgeo);
-        float4 *colcs = reinterpret_cast<float4 *>(epi + EL.colcs);
-        float *boxred = reinterpret_cast<float *>(epi + EL.boxred);
-        float *thr_s = reinterpret_cast<float *>(epi + EL.thr);
-        for (int k = et; k < (args.NW + 1) * kBinStride; k += kEpiThreads) bins[k] = 0.f;
-        for (int k = et; k < args.NB; k += kEpiThreads) {
-            fb[k] = 0.f;
-            cacc[k] = 0.0;
-        }
-        for (int k = et; k < args.NQ; k += kEpiThreads) qacc[k] = 0.0;
-
-        int cur_p = -1, cur_t = -1, tab_p = -1;
-        uint32_t v = 0;
-        bool ok = true;
-        // per-CTA FP64 sums of the current (problem, t), added to the outputs when it changes
-        auto flush_acc = [&](int p, int t) {
-            const EpiParams &E = probs[p].epi;
-            double *Cs = args.ov.active ? args.ov.C_sum : E.C_sum;
-            double *Qs = args.ov.active ? args.ov.Sq_sum : E.Sq_sum;
-            for (int b = et; b < E.n_bins; b += kEpiThreads) {
-                if (cacc[b] != 0.0) atomicAdd(&Cs[(int64_t)t * E.n_bins + b], cacc[b]);
-                cacc[b] = 0.0;
-            }
-            for (int q = et; q < E.n_q; q += kEpiThreads) {
-                if (qacc[q] != 0.0) atomicAdd(&Qs[(int64_t)t * E.n_q + q], qacc[q]);
-                qacc[q] = 0.0;
-            }
-        };
-        for (int64_t tau = cid; tau < args.total_tiles; tau += n_clusters, ++v) {
-            const TileInfo ti = decode<CL>(probs, args.n_probs, args.ov, tau, BN, rank);
-            const TcProblem &P = probs[ti.p];
-            const EpiParams &E = P.epi;
-            const int i = ti.m0 + r;
-            const bool row_ok = i < ti.row_end;
-            // rows past the range (ragged tiles, or a cluster's surplus row tiles) read the
-            // geometry of a valid site and contribute zeros
-            const int ic = row_ok ? i : P.N - 1;
-            const bool lattice = E.geom == ASD_GEOM_LATTICE;
-            // bin thresholds of this problem, then the column geometry of this tile
-            if (E.n_bins > 0 && ti.p != tab_p) {
-                // thresholds, or the lattice d2 -> bin table, of this problem
-                if (E.n_lut > 0) {
-                    uint16_t *lut_s = reinterpret_cast<uint16_t *>(thr_s);
-                    for (int k = et; k < E.n_lut; k += kEpiThreads) lut_s[k] = E.lut[k];
-                } else {
-                    for (int k = et; k < E.n_bins + 2; k += kEpiThreads) thr_s[k] = E.thr[k];
-                }
-                tab_p = ti.p;
-            }
-            for (int c = et; c < BN; c += kEpiThreads) {
-                const int j = min(ti.n0 + c, P.N - 1);
-                if (lattice) {
-                    const int4 g = E.coords[j];
-                    colgeo[c] = make_float4(__int_as_float(g.x), __int_as_float(g.y),
-                                            __int_as_float(g.z), 0.f);
-                } else {
-                    colgeo[c] = E.pos[j];
-                }
-            }
-            const int4 ri = E.coords[ic];
-            const float4 rp = E.pos[ic];
-            // bounding boxes for the bin window (only when the bins do not all fit)
-            if (E.use_window) {
-                float v6[12];
-                v6[0] = v6[3] = rp.x;
-                v6[1] = v6[4] = rp.y;
-                v6[2] = v6[5] = rp.z;
-                float cl[3] = {3e38f, 3e38f, 3e38f}, ch[3] = {-3e38f, -3e38f, -3e38f};
-                for (int c = et; c < BN; c += kEpiThreads) {
-                    const int j = min(ti.n0 + c, P.N - 1);
-                    const float4 pj = E.pos[j];
-                    cl[0] = fminf(cl[0], pj.x); ch[0] = fmaxf(ch[0], pj.x);
-                    cl[1] = fminf(cl[1], pj.y); ch[1] = fmaxf(ch[1], pj.y);
-                    cl[2] = fminf(cl[2], pj.z); ch[2] = fmaxf(ch[2], pj.z);
-                }
-                for (int a = 0; a < 3; ++a) {
-                    v6[6 + a] = cl[a];
-                    v6[9 + a] = ch[a];
-                }
-                if (!row_ok) {
-                    for (int a = 0; a < 3; ++a) {
-                        v6[a] = 3e38f;
-                        v6[3 + a] = -3e38f;
-                    }
-                }
-                for (int o = 16; o > 0; o >>= 1)
-                    for (int k = 0; k < 12; ++k) {
-                        const float w = __shfl_xor_sync(0xffffffffu, v6[k], o);
-                        v6[k] = ((k % 6) < 3) ? fminf(v6[k], w) : fmaxf(v6[k], w);
-                    }
-                if (lane == 0)
-                    for (int k = 0; k < 12; ++k) boxred[ew * 12 + k] = v6[k];
-            }
-            epi_sync();  // colgeo / boxred ready; previous tile fully flushed
-            if (ti.p != cur_p || ti.t != cur_t) {
-                if (cur_p >= 0) flush_acc(cur_p, cur_t);
-                cur_p = ti.p;
-                cur_t = ti.t;
-            }
-            int blo = 0;
-            if (E.use_window) {
-                float d2min = 0.f;
-                for (int a = 0; a < 3; ++a) {
-                    float rl = 3e38f, rh = -3e38f, cl = 3e38f, ch = -3e38f;
-                    for (int w = 0; w < kEpiWarps; ++w) {
-                        rl = fminf(rl, boxred[w * 12 + a]);
-                        rh = fmaxf(rh, boxred[w * 12 + 3 + a]);
-                        cl = fminf(cl, boxred[w * 12 + 6 + a]);
-                        ch = fmaxf(ch, boxred[w * 12 + 9 + a]);
-                    }
-                    float gap = fmaxf(0.f, fmaxf(cl - rh, rl - ch));
-                    if (lattice && E.periodic) {
-                        const float L = a == 0 ? E.Lx : a == 1 ? E.Ly : E.Lz;
-                        gap = fminf(gap, fmaxf(0.f, fmaxf(cl + L - rh, rl - (ch + L))));
-                        gap = fminf(gap, fmaxf(0.f, fmaxf(cl - L - rh, rl - (ch - L))));
-                    }
-                    d2min += gap * gap;
-                }
-                blo = max(0, bin_of_d2(d2min * 0.999f, E.inv_w, E.n_bins, E.thr) - 1);
-            }
-
-            const uint32_t acc = v & 1, use = v >> 1;
-            const bool got = mbar_wait(tfull0 + 8 * acc, use & 1, args.err, DEV_TIMEOUT_EPI);
-            ok = epi_sync_and(got);
-            if (!ok) break;
-            tc_after();
-            const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + acc * BN;
-
-            if (E.n_bins > 0) {
-                BinArgs ba;
-                ba.Lx = E.Lx;
-                ba.Ly = E.Ly;
-                ba.Lz = E.Lz;
-                ba.periodic = E.periodic;
-                ba.inv_w = E.inv_w;
-                ba.nb = E.n_bins;
-                ba.blo = blo;
-                ba.nwp = E.use_window ? args.NW : E.n_bins;
-                ba.trash = args.NW;
-                const float scale = row_ok ? 1.f : 0.f;
-                const int geo = !lattice ? GEO_POS
-                                : E.n_lut > 0 ? (E.periodic ? GEO_LUT_PERIODIC : GEO_LUT_OPEN)
-                                              : (E.periodic ? GEO_PERIODIC : GEO_OPEN);
-                const bool win = E.use_window != 0;
-                for (int ch = ch0; ch < ch1; ++ch) {
-                    uint32_t g[32];
-                    tmem_ld32(tbase + ch * 32, g);
-                    const float4 *cg = colgeo + ch * 32;
-                    float *mb = bins + r + kBM * half;
-                    if (geo == GEO_LUT_PERIODIC && !win) {
-                        bin_chunk<GEO_LUT_PERIODIC, false>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
-                    } else if (geo == GEO_LUT_OPEN && !win) {
-                        bin_chunk<GEO_LUT_OPEN, false>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
-                    } else if (geo == GEO_LUT_PERIODIC) {
-                        bin_chunk<GEO_LUT_PERIODIC, true>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
-                    } else if (geo == GEO_LUT_OPEN) {
-                        bin_chunk<GEO_LUT_OPEN, true>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
-                    } else if (win) {
-                        if (geo == GEO_PERIODIC)
-                            bin_chunk<GEO_PERIODIC, true>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
-                        else if (geo == GEO_OPEN)
-                            bin_chunk<GEO_OPEN, true>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
-                        else
-                            bin_chunk<GEO_POS, true>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
-                    } else {
-                        if (geo == GEO_PERIODIC)
-                            bin_chunk<GEO_PERIODIC, false>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
-                        else if (geo == GEO_OPEN)
-                            bin_chunk<GEO_OPEN, false>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
-                        else
-                            bin_chunk<GEO_POS, false>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
-                    }
-                }
-            }
-            if (E.n_q > 0) {
-                for (int qc = 0; qc < E.n_q; qc += kQC) {
-                    const int nqc = min(kQC, E.n_q - qc);
-                    epi_sync();  // previous users of colcs / qred are done
-                    for (int k = et; k < BN * kQC / 2; k += kEpiThreads) {
-                        const int c = k / (kQC / 2), q2 = (k % (kQC / 2)) * 2;
-                        const int j = min(ti.n0 + c, P.N - 1);
-                        float2 w0 = make_float2(0.f, 0.f), w1 = w0;
-                        if (q2 < nqc) w0 = E.cs[(int64_t)j * E.n_q + qc + q2];
-                        if (q2 + 1 < nqc) w1 = E.cs[(int64_t)j * E.n_q + qc + q2 + 1];
-                        colcs[k] = make_float4(w0.x, w0.y, w1.x, w1.y);
-                    }
-                    float cr[kQC], sr[kQC], u[kQC], vv[kQC];
-#pragma unroll
-                    for (int q = 0; q < kQC; ++q) {
-                        const float2 w = q < nqc ? E.cs[(int64_t)ic * E.n_q + qc + q]
-                                                 : make_float2(0.f, 0.f);
-                        cr[q] = w.x;
-                        sr[q] = w.y;
-                        u[q] = 0.f;
-                        vv[q] = 0.f;
-                    }
-                    epi_sync();
-                    for (int ch = ch0; ch < ch1; ++ch) {
-                        uint32_t g[32];
-                        tmem_ld32(tbase + ch * 32, g);
-#pragma unroll
-                        for (int k = 0; k < 32; ++k) {
-                            const float val = row_ok ? __uint_as_float(g[k]) : 0.f;
-                            const float4 *w = colcs + (ch * 32 + k) * (kQC / 2);
-#pragma unroll
-                            for (int q2 = 0; q2 < kQC / 2; ++q2) {
-                                const float4 w4 = w[q2];
-                                u[2 * q2] = fmaf(w4.x, val, u[2 * q2]);
-                                vv[2 * q2] = fmaf(w4.y, val, vv[2 * q2]);
-                                u[2 * q2 + 1] = fmaf(w4.z, val, u[2 * q2 + 1]);
-                                vv[2 * q2 + 1] = fmaf(w4.w, val, vv[2 * q2 + 1]);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < kQC; ++q) {
-                        double c = (double)fmaf(cr[q], u[q], sr[q] * vv[q]);
-                        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-                        if (lane == 0) qred[ew * kQC + q] = c;
-                    }
-                    epi_sync();
-                    if (et < nqc) {
-                        double sq = 0.0;
-                        for (int w = 0; w < kEpiWarps; ++w) sq += qred[w * kQC + et];
-                        qacc[qc + et] += sq;
-                    }
-                }
-            }
-            // accumulator buffer free for the MMA warp
-            tc_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
-            epi_sync();  // all private bins written
-            if (E.n_bins > 0) {
-                const int NWp = E.use_window ? args.NW : E.n_bins;
-                // epilogue warp ew reduces bins b = ew (mod 8): 8 conflict-free loads per
-                // lane, an FP32 tree over the 256 entries, one FP64 add per bin (the FP64
-                // pipe is narrow on this part, so FP64 work is kept per bin, not per row)
-                for (int b = ew; b < NWp; b += kEpiWarps) {
-                    float *row = bins + b * kBinStride;
-                    float v = 0.f;
-#pragma unroll
-                    for (int m = 0; m < kBinStride / 32; ++m) {
-                        v += row[lane + 32 * m];
-                        row[lane + 32 * m] = 0.f;
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0 && blo + b < E.n_bins) cacc[blo + b] += (double)v;
-                }
-                if (E.use_window) {
-                    epi_sync();  // the fallback bins update the same accumulators
-                    for (int b = et; b < E.n_bins; b += kEpiThreads) {
-                        if (fb[b] != 0.f) {
-                            cacc[b] += (double)fb[b];
-                            fb[b] = 0.f;
-                        }
-                    }
-                }
-            }
-        }
-        epi_sync();
-        if (ok && cur_p >= 0) flush_acc(cur_p, cur_t);
-    }
-    __syncwarp();
-    __syncthreads();
-    if (warp == 1) {
-        tc_after();
-        tmem_dealloc(tmem, kTmemCols);
-    }
-    // no CTA leaves while a peer may still multicast into its shared memory or arrive on
-    // its barriers (each CTA drained its own copies and MMAs above)
-    if (CL > 1) {
-        __syncwarp();
-        cluster_sync();
-    }
-}
-
-template <int FORM, int BN, int SWB, int CL>
-int launch_cl(const LaunchArgs &a, size_t smem, int sm_count, cudaStream_t s)
-{
-    auto k = pc_tc_kernel<FORM, BN, SWB, CL>;
-    ASD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (CL == 1) {
-        const int grid = (int)(a.total_tiles < sm_count ? a.total_tiles : sm_count);
-        k<<<grid, kThreads, smem, s>>>(a);
-        ASD_CUDA_TRY(cudaGetLastError());
-        return ASD_OK;
-    }
-    ASD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
-    cudaLaunchConfig_t cfg{};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    // as many clusters as can be resident at once (one CTA per SM), no more than needed
-    cfg.gridDim = dim3((unsigned)(sm_count / CL * CL), 1, 1);
-    int max_clusters = 0;
-    ASD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&max_clusters, (void *)k, &cfg));
-    if (max_clusters < 1) {
-        set_error_text("no cluster of the tensor-core kernel fits on the device");
-        return ASD_EUNSUPPORTED;
-    }
-    const int64_t nc = a.total_tiles < max_clusters ? a.total_tiles : max_clusters;
-    cfg.gridDim = dim3((unsigned)(nc * CL), 1, 1);
-    ASD_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, a));
-    return ASD_OK;
-}
-
-template <int FORM, int BN, int SWB>
-int launch_one(const LaunchArgs &a, size_t smem, int cl, int sm_count, cudaStream_t s)
-{
-    return cl == 4 ? launch_cl<FORM, BN, SWB, 4>(a, smem, sm_count, s)
-                   : launch_cl<FORM, BN, SWB, 1>(a, smem, sm_count, s);
-}
-
-}  // namespace
-
-size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut)
-{
-    return epi_layout(NW, n_bins, n_q, BN, n_lut).total;
+    return epi_layout(NW, n_bins, n_q, BN, n_lut, ew).total;
 }
 
 int tc_configure(asd_corr_plan *p)
@@ -912,7 +25,7 @@ int tc_configure(asd_corr_plan *p)
     // private bins: as many as fit with at least 3 stages (2 when tight)
     int NW = p->n_bins;
     p->use_window = 0;
-    auto epi = [&](int nw) { return tc_epilogue_smem(nw, p->n_bins, p->n_q, p->BN, p->n_lut); };
+    auto epi = [&](int nw) { return tc_epilogue_smem(nw, p->n_bins, p->n_q, p->BN, p->n_lut, p->EW); };
     for (int min_st = 3; min_st >= 2; --min_st) {
         NW = p->n_bins;
         while (NW > 8 && epi(NW) + min_st * stage_bytes > cap) NW = (NW * 3) / 4;
@@ -937,7 +50,7 @@ int tc_configure(asd_corr_plan *p)
 
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
               int BN, int swizzle_bytes, int stages, size_t smem, int max_nw, int max_nb,
-              int max_nq, int max_nlut, int cl, int sm_count, cudaStream_t s)
+              int max_nq, int max_nlut, int cl, int ew, int sm_count, cudaStream_t s)
 {
     if (total_tiles <= 0) return ASD_OK;
     LaunchArgs a{};
@@ -954,17 +67,10 @@ int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOver
     if (!a.err) return ASD_ECUDA;
     (void)swizzle_bytes;
     switch (prec) {
-    case ASD_BF16:
-        return BN == 256 ? launch_one<ASD_BF16, 256, 128>(a, smem, cl, sm_count, s)
-                         : launch_one<ASD_BF16, 128, 128>(a, smem, cl, sm_count, s);
-    case ASD_TF32:
-        return BN == 256 ? launch_one<ASD_TF32, 256, 128>(a, smem, cl, sm_count, s)
-                         : launch_one<ASD_TF32, 128, 128>(a, smem, cl, sm_count, s);
-    case ASD_SPLIT_BF16:
-        return BN == 256 ? launch_one<ASD_SPLIT_BF16, 256, 64>(a, smem, cl, sm_count, s)
-                         : launch_one<ASD_SPLIT_BF16, 128, 64>(a, smem, cl, sm_count, s);
-    default:
-        return ASD_EINVAL;
+    case ASD_BF16: return tc_launch_form<ASD_BF16>(a, smem, BN, cl, ew, sm_count, s);
+    case ASD_TF32: return tc_launch_form<ASD_TF32>(a, smem, BN, cl, ew, sm_count, s);
+    case ASD_SPLIT_BF16: return tc_launch_form<ASD_SPLIT_BF16>(a, smem, BN, cl, ew, sm_count, s);
+    default: return ASD_EINVAL;
     }
 }
 

@@ -1,0 +1,6 @@
+// Instantiation of the fused tensor-core kernel for the split form (see pc_tc_kernel.cuh).
+#include "pc_tc_kernel.cuh"
+
+namespace asd {
+template int tc_launch_form<ASD_SPLIT_BF16>(const TcLaunchArgs &, size_t, int, int, int, int, cudaStream_t);
+}  // namespace asd

@@ -1,0 +1,6 @@
+// Instantiation of the fused tensor-core kernel for the tf32 form (see pc_tc_kernel.cuh).
+#include "pc_tc_kernel.cuh"
+
+namespace asd {
+template int tc_launch_form<ASD_TF32>(const TcLaunchArgs &, size_t, int, int, int, int, cudaStream_t);
+}  // namespace asd

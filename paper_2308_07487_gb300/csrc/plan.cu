@@ -262,7 +262,18 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
     ASD_CHECK_ARG(d->stages == 0 || (d->stages >= 2 && d->stages <= 8), "stages: 0 or 2..8");
     ASD_CHECK_ARG(d->k_chunks >= 0 && d->k_chunks <= 16, "k_chunks: 0..16");
     ASD_CHECK_ARG(d->cluster == 0 || d->cluster == 1 || d->cluster == 4, "cluster: 0, 1 or 4");
-    for (int k = 0; k < 3; ++k) ASD_CHECK_ARG(d->reserved[k] == 0, "reserved fields must be 0");
+    ASD_CHECK_ARG(d->epi_warps == 0 || d->epi_warps == 4 || d->epi_warps == 8, "epi_warps: 0, 4 or 8");
+    {
+        // instantiated tensor-core kernels: 256-wide tiles with either warp count (cluster 4
+        // with the form's default); 128-wide tiles with cluster 1 and the default warps
+        const int ew_default = d->precision == ASD_BF16 ? 8 : 4;
+        const int ew = d->epi_warps ? d->epi_warps : ew_default;
+        ASD_CHECK_ARG(!(d->cluster == 4 && ew != ew_default),
+                      "cluster 4 runs with the form's default epi_warps");
+        ASD_CHECK_ARG(!(d->tile_n == 128 && (d->cluster == 4 || ew != ew_default)),
+                      "tile_n = 128 needs cluster 1 and the default epi_warps");
+    }
+    for (int k = 0; k < 2; ++k) ASD_CHECK_ARG(d->reserved[k] == 0, "reserved fields must be 0");
     if (d->geometry == ASD_GEOM_LATTICE) {
         ASD_CHECK_ARG(d->coords, "coords required for lattice geometry");
         for (int a = 0; a < 3; ++a) ASD_CHECK_ARG(d->L[a] >= 1 && d->L[a] <= 1 << 20, "bad L");
@@ -331,14 +342,21 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         const int64_t tiles_m_all = (p->N + kBM - 1) / kBM;
         // (measured: sharing B by multicast does not pay here, so clusters are opt-in)
         p->CL = d->cluster ? d->cluster : 1;
+        // epilogue warps (measured): split-BF16 and TF32 are MMA-bound and keep more
+        // pipeline stages with 4; single-product BF16 is epilogue-bound and gains from 8
+        p->EW = d->epi_warps ? d->epi_warps : (d->precision == ASD_BF16 ? 8 : 4);
+        // instantiated kernels: 256-wide tiles with any cluster / warp choice of the form;
+        // 128-wide tiles with one CTA per cluster and the form's default warps
+        const int ew_default = d->precision == ASD_BF16 ? 8 : 4;
+        if (p->CL == 4 || p->EW != ew_default) p->BN = 256;  // combination checked up front
         (void)tiles_m_all;
         // K chunks: split-BF16 is the FP32-accurate form; each chunk's accumulator starts
-        // from zero, bounding the FP32 accumulation error of the tensor core to ~1024
+        // from zero, bounding the FP32 accumulation error of the tensor core to ~1536
         // terms per partial sum (the other forms are limited by their operand rounding)
         const int64_t nk = (int64_t)p->S * (p->Kseg / p->BK);
         int kc = d->k_chunks;
         if (kc == 0)
-            kc = d->precision == ASD_SPLIT_BF16 ? (int)((p->S * p->Kseg + 1023) / 1024) : 1;
+            kc = d->precision == ASD_SPLIT_BF16 ? (int)((p->S * p->Kseg + 1535) / 1536) : 1;
         if (kc > 16) kc = 16;
         if (kc > nk) kc = (int)nk;
         p->k_chunks = kc < 1 ? 1 : kc;
@@ -576,7 +594,8 @@ int asd_pair_corr_contract(asd_corr_plan *p, int64_t row_begin, int64_t row_end,
     ov.C_sum = C_sum;
     ov.Sq_sum = Sq_sum;
     return launch_tc(p->d_prob, 1, ov.n_tiles, ov, p->prec, p->BN, p->swizzle_bytes, p->stages,
-                     p->smem_bytes, p->NW, p->n_bins, p->n_q, p->n_lut, p->CL, p->sm_count, s);
+                     p->smem_bytes, p->NW, p->n_bins, p->n_q, p->n_lut, p->CL, p->EW,
+                     p->sm_count, s);
 }
 
 int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs, int n,
@@ -590,7 +609,8 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     for (int k = 0; k < n; ++k) {
         const asd_corr_plan *p = plans[k];
         ASD_CHECK_ARG(p && trajs[k], "null plan or trajectory");
-        ASD_CHECK_ARG(p->tc && p->prec == p0->prec && p->BN == p0->BN && p->CL == p0->CL,
+        ASD_CHECK_ARG(p->tc && p->prec == p0->prec && p->BN == p0->BN && p->CL == p0->CL &&
+                          p->EW == p0->EW,
                       "batched plans must share precision and tile width");
         ASD_CHECK_ARG(p->device == p0->device, "plans on different devices");
         ASD_CHECK_ARG(p->n_bins == 0 || (C_sum && C_sum[k]), "C_sum required");
@@ -608,7 +628,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
         for (int k = 0; k < n; ++k) {
             (void)k;
         }
-        epi = tc_epilogue_smem(max_nw, max_nb, max_nq, p0->BN, max_nlut);
+        epi = tc_epilogue_smem(max_nw, max_nb, max_nq, p0->BN, max_nlut, p0->EW);
         const size_t cap = 232448 - 2048;
         if (epi + 2 * stage_bytes > cap) {
             set_error_text("batched epilogue does not fit shared memory");
@@ -663,7 +683,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     }
     TcOverride ov{};
     return launch_tc(dbuf, n, total, ov, p0->prec, p0->BN, p0->swizzle_bytes, stages, smem, max_nw,
-                     max_nb, max_nq, max_nlut, p0->CL, p0->sm_count, s);
+                     max_nb, max_nq, max_nlut, p0->CL, p0->EW, p0->sm_count, s);
 }
 
 int asd_pair_corr_normalize(const asd_corr_plan *p, const double *C_sum, const double *Sq_sum,
