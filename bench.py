@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--medium", action="store_true", help="profiling workload (ncu)")
     ap.add_argument("--no-extras", action="store_true", help="skip form sweep, CPU baseline, e2e")
     ap.add_argument("--ncu", action="store_true", help="one step, nothing else (for ncu)")
+    ap.add_argument("--workload", default="cubic40",
+                    choices=["cubic40", "glass", "ensemble", "learned"],
+                    help="cubic40: the headline line; the others print their own lines")
     return ap.parse_args()
 
 
@@ -365,10 +368,236 @@ def run_ours(args, W, ws, rank, local):
         print(json.dumps(out))
     plan.close()
 
+# -------------------------------------------------------------------------------------
+# other workloads (one JSON line each; the headline line is the cubic40 workload)
+# -------------------------------------------------------------------------------------
+def _timed(fn, reps=1):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def run_glass(args):
+    """64^3 jittered +-J glass (262144 sites, open): 256 bins of width 0.5 and S(q,t) for
+    64 q-vectors, 8 of the 128 displacements (every displacement costs the same), all
+    tensor forms; per-form error on a 16-row slice against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2308_07487_gb300 import asd, synth
+    cfg = synth.cfg_glass64()
+    lat = cfg.lattice
+    N = lat.n_sites
+    tr = synth.traj_precess(N, cfg.F, seed=23083)
+    d_tr = torch.from_numpy(tr).cuda()
+    nt = 8
+    fl = 2.0 * N * N * 3 * cfg.T0 * nt
+    rows, t_sel = (70000, 70016), [0, nt - 1]
+    ref = oracle.pair_corr(tr, cfg.T0, t_sel, oracle.Geometry.of_lattice(lat), cfg.w, cfg.n_bins,
+                           q=cfg.q, rows=rows)
+    out = {"workload": cfg.name, "metric": "fused pair-corr TFLOP/s (bins; bins + 64 q)",
+           "unit": "TFLOP/s", "displacements_timed": nt, "forms": {}}
+    for form in ("split_bf16", "bf16", "tf32", "fp32"):
+        res = {}
+        for with_q in (False, True):
+            q = cfg.q if with_q else None
+            plan = asd.CorrPlan.for_lattice(lat, cfg.F, cfg.T0, nt, cfg.w, cfg.n_bins,
+                                            precision=form, q=q)
+            C = torch.zeros((nt, cfg.n_bins), dtype=torch.float64, device="cuda")
+            Sq = torch.zeros((nt, len(cfg.q)), dtype=torch.float64, device="cuda") if with_q else None
+            plan.prepare(d_tr)
+            if form == "fp32":
+                dt = _timed(lambda: plan.contract(C, Sq, rows=(0, N // 8))) * 8
+            else:
+                dt = _timed(lambda: plan.contract(C, Sq))
+            asd.check(asd.sync_status(), "glass")
+            C.zero_()
+            if Sq is not None:
+                Sq.zero_()
+            plan.contract(C, Sq, rows=rows)
+            torch.cuda.synchronize()
+            err = float(oracle.bin_error(C.cpu().numpy()[t_sel], ref).max())
+            key = "bins_and_phase" if with_q else "bins"
+            res[key] = {"TFLOP/s": fl / dt / 1e12, "ms": dt * 1e3, "max_bin_err": err}
+            if with_q:
+                d = np.abs(Sq.cpu().numpy()[t_sel] - ref["Sq_sum"]).max() / np.abs(ref["Sq_sum"]).max()
+                res[key]["phase_rel_err"] = float(d)
+            plan.close()
+        out["forms"][form] = res
+    out["note"] = ("fp32 timed on rows 0..N/8 and scaled (the SIMT form is ~30x slower); "
+                   "errors on rows 70000..70016, displacements 0 and 7")
+    print(json.dumps(out))
+
+
+def run_ensemble(args):
+    """96 independent 2D/3D periodic samples, N_s log-uniform in [1024, 40000], each with
+    its own lattice, bins and plan; F = 320, T0 = 256, 64 displacements, split-BF16.
+    One persistent launch over all problems (asd_pair_corr_batched), the same captured
+    in a CUDA graph and replayed, and 96 separate launches."""
+    import torch
+
+    from paper_2308_07487_gb300 import asd, synth
+    F, T0, n_t = 320, 256, 64
+    sizes = synth.ensemble_sizes(96)
+    plans, trajs, Cs, fl = [], [], [], 0.0
+    for k, (d, L) in enumerate(sizes):
+        lat = synth.hypercubic(L, d, True, J=1.0)
+        w = 1.0 if d == 2 else 0.5
+        rmax = (d * (L // 2) ** 2) ** 0.5
+        nb = int(rmax / w) + 1
+        sysm = asd.System(lat)
+        sp = torch.from_numpy(synth.random_unit(lat.n_sites, 23084 + k)[None]).cuda()
+        sysm.thermalize(sp, 0.5 if d == 2 else 1.2, 200, asd.ASD_METROPOLIS, adapt=True,
+                        seed=23084 + k)
+        tr = torch.empty((lat.n_sites, 1, F, 3), dtype=torch.float32, device="cuda")
+        sysm.ll_integrate(sp, 0.01, F, 1, tr)
+        plans.append(asd.CorrPlan.for_lattice(lat, F, T0, n_t, w, nb, precision="split_bf16",
+                                              tile_n=256))
+        trajs.append(tr)
+        Cs.append(torch.zeros((n_t, nb), dtype=torch.float64, device="cuda"))
+        fl += 2.0 * lat.n_sites ** 2 * 3 * T0 * n_t
+    torch.cuda.synchronize()
+    t_sep = _timed(lambda: [p.run(t, c) for p, t, c in zip(plans, trajs, Cs)])
+    t_bat = _timed(lambda: asd.pair_corr_batched(plans, trajs, Cs))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        asd.pair_corr_batched(plans, trajs, Cs, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        asd.pair_corr_batched(plans, trajs, Cs, stream=s)
+    t_graph = _timed(lambda: g.replay())
+    asd.check(asd.sync_status(), "ensemble")
+    print(json.dumps({
+        "workload": "ensemble96_uneven", "metric": "fused pair-corr TFLOP/s (split-BF16)",
+        "unit": "TFLOP/s", "n_samples": len(plans),
+        "N_range": [min(p.N for p in plans), max(p.N for p in plans)],
+        "total_sites": int(sum(p.N for p in plans)),
+        "batched_one_launch": fl / t_bat / 1e12, "graph_replay": fl / t_graph / 1e12,
+        "separate_launches": fl / t_sep / 1e12,
+        "ms": {"batched": t_bat * 1e3, "graph": t_graph * 1e3, "separate": t_sep * 1e3}}))
+    for p in plans:
+        p.close()
+
+
+def run_learned(args):
+    """128^2 periodic lattice, J = +1, T = 0.7: train the vMF proposal network on plain
+    Metropolis configurations with the GPU kernels, sample 64 starts with the learned
+    proposal and with plain Metropolis, integrate LL (F = 576) and correlate the 64 starts
+    concatenated along K (T0 = 512, 64 displacements, K = 3 x 512 x 64)."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from oracle import mlp as omlp
+    from paper_2308_07487_gb300 import asd, synth
+    L, T, S = 128, 0.7, 64
+    lat = synth.hypercubic(L, 2, True, J=1.0)
+    N = lat.n_sites
+    sysm = asd.System(lat)
+    sp = torch.from_numpy(synth.random_unit(S * N, 23085).reshape(S, N, 3)).cuda()
+    sysm.thermalize(sp, T, 1000, asd.ASD_METROPOLIS, adapt=True, seed=23085)
+    xs, ys = [], []
+    nconf = 10000 // S + 1                       # ~10^4 training configurations
+    t0 = time.perf_counter()
+    for k in range(nconf):
+        sysm.thermalize(sp, T, 2, asd.ASD_METROPOLIS, adapt=True, seed=23085, counter=1000 + 2 * k)
+        if k % 8 == 0:
+            x = torch.empty((S * N, 12), device="cuda")
+            y = torch.empty((S * N, 3), device="cuda")
+            sysm.gather(sp, x, y)
+            xs.append(x)
+            ys.append(y)
+    X, Y = torch.cat(xs), torch.cat(ys)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = asd.Mlp(12, omlp.init(12, 5))
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    B, steps = 16384, 1500
+    t0 = time.perf_counter()
+    for it in range(steps):
+        idx = torch.randint(0, X.shape[0], (B,), device="cuda", generator=gen)
+        net.grad.zero_()
+        net.loss.zero_()
+        net.loss_grad(X[idx].contiguous(), Y[idx].contiguous())
+        net.adam(lr=3e-3 if it < 1000 else 1e-3, scale=1.0 / B)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    net.grad.zero_()
+    net.loss.zero_()
+    net.loss_grad(X[:262144].contiguous(), Y[:262144].contiguous())
+    nll = net.loss.item() / 262144
+
+    def chain(prop, kw):
+        s2 = sp.clone()
+        sysm.thermalize(s2, T, 200, prop, seed=7, **kw)
+        es, ms, acc, pr = [], [], 0, 0
+        for k in range(100):
+            st = sysm.thermalize(s2, T, 2, prop, seed=7, counter=200 + 2 * k, stats=True, **kw)
+            pr += st[0]
+            acc += st[1]
+            y = s2.double()
+            e = 0.0
+            for a in range(lat.nbr.shape[1]):
+                e += (y * y[:, torch.from_numpy(lat.nbr[:, a]).long().cuda()]).sum().item()
+            es.append(e / 2 / (S * N))
+            ms.append(float(y.mean(1).norm(dim=1).mean().item()))
+        es = np.array(es)
+        # integrated autocorrelation time of the energy (initial positive sequence)
+        x = es - es.mean()
+        c = np.correlate(x, x, "full")[len(x) - 1:] / (x.var() * len(x))
+        tau = 0.5 + sum(v for v in c[1:20] if v > 0)
+        return s2, {"acceptance": acc / pr, "energy_per_site": float(es.mean()),
+                    "energy_sem": float(es.std() / math.sqrt(len(es))), "tau_int_energy": tau,
+                    "magnetisation": float(np.mean(ms))}
+    s_learn, st_learn = chain(asd.ASD_LEARNED, {"net": net})
+    s_metro, st_metro = chain(asd.ASD_METROPOLIS, {"cone": 0.0})
+    _, st_heat = chain(asd.ASD_HEATBATH, {})
+    F, T0, n_t = 576, 512, 64
+    res = {}
+    for name, starts in (("learned", s_learn), ("metropolis", s_metro)):
+        tr = torch.empty((N, S, F, 3), dtype=torch.float32, device="cuda")
+        sysm.ll_integrate(starts, 0.01, F, 1, tr)
+        plan = asd.CorrPlan.for_lattice(lat, F, T0, n_t, 1.0, 91, precision="split_bf16", S=S)
+        C = torch.zeros((n_t, 91), dtype=torch.float64, device="cuda")
+        plan.prepare(tr)
+        dt = _timed(lambda: plan.contract(C))
+        C.zero_()
+        plan.contract(C)
+        Cn = torch.zeros_like(C)
+        plan.normalize(C, None, Cn, None)
+        torch.cuda.synchronize()
+        fl = 2.0 * N * N * 3 * T0 * S * n_t
+        res[name] = {"C": Cn.cpu().numpy(), "TFLOP/s": fl / dt / 1e12, "ms": dt * 1e3}
+        plan.close()
+    dC = np.abs(res["learned"]["C"] - res["metropolis"]["C"])[:, :40].max()
+    print(json.dumps({
+        "workload": "sq128_learned_proposal", "T": T, "starts": S,
+        "training": {"pairs": int(X.shape[0]), "steps": steps, "batch": B,
+                     "data_s": t_data, "train_s": t_train, "nll_per_site": nll,
+                     "nll_uniform": math.log(4 * math.pi)},
+        "chains": {"learned": st_learn, "metropolis": st_metro, "heatbath": st_heat},
+        "corr_TFLOP/s": {k: v["TFLOP/s"] for k, v in res.items()},
+        "corr_ms": {k: v["ms"] for k, v in res.items()},
+        "max_abs_C_diff_learned_vs_metropolis_r<40": float(dC)}))
+
 
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
+    if args.workload != "cubic40":
+        if rank == 0:
+            {"glass": run_glass, "ensemble": run_ensemble, "learned": run_learned}[args.workload](args)
+        return
     W = workload(args.small, args.medium)
     if args.impl == "reference":
         run_reference(args, W, ws, rank)

@@ -24,15 +24,6 @@ def bins_from_thresholds(d2, w, n_bins):
     return np.searchsorted(thr, np.asarray(d2, np.float64), side="right")
 
 
-def _grid(traj, coords, L):
-    """Scatter a [N][S][F][3] trajectory onto a dense [S][F][3][Lz][Ly][Lx] grid."""
-    N, S, F, _ = traj.shape
-    Lx, Ly, Lz = (int(v) for v in L)
-    g = np.zeros((S, F, 3, Lz, Ly, Lx), np.float64)
-    g[:, :, :, coords[:, 2], coords[:, 1], coords[:, 0]] = np.transpose(traj, (1, 2, 3, 0))
-    return g
-
-
 def lattice_fft_corr(traj, T0, t_list, coords, L, periodic, w, n_bins):
     """Binned C_sum[t][b] on a full lattice via FFT cross-correlation (FP64)."""
     tr = np.asarray(traj, np.float64)
@@ -42,25 +33,31 @@ def lattice_fft_corr(traj, T0, t_list, coords, L, periodic, w, n_bins):
     Lx, Ly, Lz = (int(v) for v in L)
     assert N == Lx * Ly * Lz, "FFT check needs every lattice point occupied"
     pad = (Lz, Ly, Lx) if periodic else tuple(2 * v if v > 1 else 1 for v in (Lz, Ly, Lx))
-    g = _grid(tr, coords, L)
-    # spatial transform of every frame
-    G = np.fft.fftn(g, s=pad, axes=(3, 4, 5))          # [S][F][3][pz][py][px]
     t_list = np.atleast_1d(t_list)
-    # temporal cross-correlation sum_{t0<T0} conj(G(t0+t)) G(t0) for each t, via FFT in f
     nf = 1
     while nf < F + T0:
         nf *= 2
-    A = np.fft.fft(G, n=nf, axis=1)
-    Bt = G.copy()
-    Bt[:, T0:] = 0.0
-    B = np.fft.fft(Bt, n=nf, axis=1)
-    # corr[t] = sum_t0 conj(G[t0+t]) G[t0]  ->  ifft(conj(A) * B) at lag -t ... use explicit form:
-    # sum_t0 conj(a[t0+t]) b[t0] = ifft(A * conj(B))[t]^*  (for lag t >= 0)
-    Xhat = np.fft.ifft(A * np.conj(B), axis=1)          # [S][nf][3][...]: sum_t0 a[t0+t] conj(b[t0])
-    Xhat = Xhat[:, t_list].sum(axis=(0, 2))               # [n_t][pz][py][px], a = G, b = G
-    # Xhat[t](k) = sum_{s,t0,a} G_k(t0+t) conj(G_k(t0)).  Spatially,
-    # X_d = sum_x a(x) b(x+d) = (1/V) sum_k conj(A_k) B_k e^{ikd}
-    X = np.fft.ifftn(np.conj(Xhat), axes=(1, 2, 3)).real  # [n_t][pz][py][px]
+    V = pad[0] * pad[1] * pad[2]
+    # Yhat[t](k) = sum_{s,t0,a} G_k(t0+t) conj(G_k(t0)), accumulated one (sample, component)
+    # and one chunk of wave vectors at a time (bounded memory at any lattice size)
+    Yhat = np.zeros((len(t_list), V), np.complex128)
+    chunk = max(1, (1 << 25) // (nf * 16))
+    for s in range(S):
+        for a in range(3):
+            g = np.zeros((F,) + tuple(int(v) for v in (Lz, Ly, Lx)), np.float64)
+            g[:, coords[:, 2], coords[:, 1], coords[:, 0]] = tr[:, s, :, a].T
+            # spatial transform of every frame, flattened over k
+            G = np.fft.fftn(g, s=pad, axes=(1, 2, 3)).reshape(F, V)
+            del g
+            for k0 in range(0, V, chunk):
+                Gc = G[:, k0:k0 + chunk]
+                # sum_{t0<T0} a[t0+t] conj(b[t0]) = ifft(fft(a) conj(fft(b)))[t], b = a cut at T0
+                A = np.fft.fft(Gc, n=nf, axis=0)
+                B = np.fft.fft(Gc[:T0], n=nf, axis=0)
+                Yhat[:, k0:k0 + chunk] += np.fft.ifft(A * np.conj(B), axis=0)[t_list]
+            del G
+    # X_d = sum_x a(x) b(x+d) = (1/V) sum_k conj(A_k) B_k e^{ikd}: conj of the above
+    X = np.fft.ifftn(np.conj(Yhat).reshape((len(t_list),) + pad), axes=(1, 2, 3)).real
     # displacement vectors of every grid offset and their squared distance
     dz, dy, dx = np.meshgrid(np.arange(pad[0]), np.arange(pad[1]), np.arange(pad[2]), indexing="ij")
     comps = []
