@@ -45,7 +45,12 @@ constexpr int kBM = 128;            // rows (sites i) per tile = TMEM lanes
 constexpr int kMaxCopies = 8;       // shifted operand copies (16-byte TMA start rule)
 constexpr int kMaxProblems = 4096;  // batched work list
 constexpr size_t kMinSmem = 120 * 1024;  // tensor-core kernel: one CTA per SM
-constexpr int kLutMax = 4096;            // largest d2 -> bin table kept in shared memory
+constexpr int kLutMax = 16384;           // largest d2 -> bin table kept in shared memory
+constexpr int kQChunk = 16;              // q-vectors per pass of the phase epilogue
+
+// Private-bin stride (floats) of the tensor-core epilogue with `ew` epilogue warps: one
+// column per accumulator row, so a warp's 32 lanes address 32 distinct banks.
+__host__ __device__ constexpr int bin_stride(int ew) { return 128 * (ew / 4); }
 
 // Epilogue geometry + output parameters of one problem (device-visible POD).
 struct EpiParams {
@@ -62,7 +67,11 @@ struct EpiParams {
     const float *thr;       // [n_bins+2]: FP32 thresholds (k*w)^2 rounded up; thr[0]=0
     const uint16_t *lut;    // lattices: bin of every integer d2 < n_lut (n_bins = dropped)
     int n_lut;              // 0 when the table is not used
-    const float2 *cs;       // [N][n_q] (cos, sin)(q.r_i)
+    int fast;               // lattice with byte-sized coordinates and every bin private:
+                            // packed-coordinate d2, table entries are private-bin offsets
+    uint32_t Lpk;           // fast: per-byte minimum-image modulus (x | y<<8 | z<<16)
+    int nq_pad;             // row length of cs (n_q rounded up to the q-chunk, zero padded)
+    const float2 *cs;       // [N][nq_pad] (cos, sin)(q.r_i)
     double *C_sum;          // [n_t][n_bins]
     double *Sq_sum;         // [n_t][n_q]
 };

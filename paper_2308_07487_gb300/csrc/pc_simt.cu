@@ -139,10 +139,10 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
             float2 wc[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-                wc[c] = cj[c] < P.N ? e.cs[(int64_t)cj[c] * e.n_q + q] : make_float2(0.f, 0.f);
+                wc[c] = cj[c] < P.N ? e.cs[(int64_t)cj[c] * e.nq_pad + q] : make_float2(0.f, 0.f);
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const float2 wr = ri[r] < P.row_end ? e.cs[(int64_t)ri[r] * e.n_q + q]
+                const float2 wr = ri[r] < P.row_end ? e.cs[(int64_t)ri[r] * e.nq_pad + q]
                                                     : make_float2(0.f, 0.f);
                 float u = 0.f, v = 0.f;
 #pragma unroll
@@ -192,6 +192,7 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
     e.coords = p->coords;
     e.pos = p->pos;
     e.thr = p->thr;
+    e.nq_pad = (p->n_q + kQChunk - 1) / kQChunk * kQChunk;
     e.cs = p->cs;
     e.C_sum = C_sum;
     e.Sq_sum = Sq_sum;

@@ -39,14 +39,15 @@ namespace {
 // Epilogue warps EW (template parameter): 4 (one per TMEM lane quarter, all columns) or
 // 8 (two per quarter, half the columns each).  Threads = TMA warp + MMA warp + EW warps.
 constexpr int kMaxEpiWarps = 8;
-constexpr int kQC = 16;                       // q-vectors per epilogue pass
+constexpr int kQC = kQChunk;                  // (cos, sin) rows are padded to whole kQC
+constexpr int kQP = 8;                        // q-vectors per pass of the phase loop
+static_assert(kQP == 8 && kQC % kQP == 0, "the phase reduction maps lane bits 4..2 to q");
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
 // Private bins are a [bin][128 * EW/4] array: epilogue thread (row r, column half h)
 // only ever touches column r + 128 h, i.e. bank r mod 32, so the per-pair accumulation
 // is free of bank conflicts whatever the bins of the 32 lanes are (with an odd stride,
 // bins that fall as the row index rises put a whole warp on one bank).  The per-tile
-// flush reads whole bin rows warp-cooperatively.
-__host__ __device__ constexpr int bin_stride(int ew) { return 128 * (ew / 4); }
+// flush reads whole bin rows warp-cooperatively (bin_stride, asd_internal.h).
 
 // ------------------------------------------------------------------------------------
 // PTX wrappers
@@ -192,6 +193,75 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// 16 lanes x 256 bits, 4 repetitions along the columns (32 columns): register 4m + e
+// holds (lane l/4, column 8m + 2(l%4) + e) and register 4m + 2 + e holds (lane l/4 + 8,
+// the same column), l = this thread's lane in the warp.  Valid after tmem_wait16x2.
+__device__ __forceinline__ void tmem_ld16x256b_x4(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+// Wait for two 16x256b.x4 loads, tied to their registers.
+__device__ __forceinline__ void tmem_wait16x2(uint32_t (&a)[16], uint32_t (&b)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
+                   "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]),
+                   "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(b[0]), "+r"(b[1]),
+                   "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+                   "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]),
+                   "+r"(b[14]), "+r"(b[15])
+                 :
+                 : "memory");
+}
+
+// Asynchronous 16-byte global -> shared copy (completion per thread by commit groups).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(smem_dst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Issue half of tmem_ld32: the registers are valid only after tmem_wait32 on them.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+
+// Wait for the TMEM loads of this thread; tied to the registers so no use of them can be
+// scheduled before it.
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                   "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
 // 32 lanes x 32 consecutive 32-bit columns; the wait is tied to the registers so no
 // use of them can be scheduled before it.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
@@ -261,7 +331,7 @@ __host__ __device__ constexpr uint32_t idesc(bool tf32, int N)
 // shared-memory layout of the epilogue region
 // ------------------------------------------------------------------------------------
 struct EpiLayout {
-    uint32_t cacc, qacc, qred, bins, fb, colgeo, colcs, boxred, thr, total;
+    uint32_t cacc, qacc, qred, bins, fb, colgeo, colpk, colcs, rowcs, boxred, thr, total;
 };
 
 __host__ __device__ inline uint32_t take(uint32_t &o, uint32_t bytes)
@@ -278,11 +348,15 @@ __host__ __device__ inline EpiLayout epi_layout(int NW, int nb, int nq, int BN, 
     uint32_t o = 0;
     L.cacc = take(o, 8u * (nb > 0 ? nb : 1));
     L.qacc = take(o, 8u * (nq > 0 ? nq : 1));
-    L.qred = take(o, 8u * ew * kQC);
+    // one slot per (pass, warp, q): the passes of a tile are reduced once at its end
+    L.qred = take(o, 8u * ew * (nq > 0 ? (nq + kQP - 1) / kQP * kQP : kQP));
     L.bins = take(o, 4u * (NW + 1) * bin_stride(ew));
     L.fb = take(o, 4u * (nb > 0 ? nb : 1));
     L.colgeo = take(o, 16u * BN);
-    L.colcs = nq > 0 ? take(o, 8u * BN * kQC) : 0u;
+    L.colpk = take(o, 4u * BN);
+    // phase weights of one pass, double buffered: columns (BN) and rows (128) of the tile
+    L.colcs = nq > 0 ? take(o, 2u * 8u * BN * kQP) : 0u;
+    L.rowcs = nq > 0 ? take(o, 2u * 8u * kBM * kQP) : 0u;
     L.boxred = take(o, 4u * ew * 12);
     // bin thresholds (FP32) or, for lattices, the d2 -> bin table (uint16), same region
     const uint32_t tb = 4u * (nb + 2), lb = 2u * nlut;
@@ -388,6 +462,36 @@ __device__ __forceinline__ void bin_chunk(const uint32_t (&g)[32], float scale, 
         const float val = scale * __uint_as_float(g[k]);
         if (slot[k] < 0) atomicAdd(&fb[-1 - slot[k]], val);
         else myb[slot[k] * STRIDE] += val;
+    }
+}
+
+// Fast lattice form of bin_chunk's first phase (EpiParams::fast): coordinates packed one per byte
+// (x | y<<8 | z<<16), the per-axis minimum image from byte-wise |a - b| and
+// min(d, L - d), d2 from a byte dot product, then the private-bin word offset from the
+// d2 table (LUT, entries pre-scaled by the bin stride) or from the thresholds (THR).
+// Dropped pairs land in the trash row, so no pair takes a branch.
+template <bool LUT, int STRIDE>
+__device__ __forceinline__ void pk_offsets(uint32_t (&off)[32], uint32_t rpk, uint32_t Lpk,
+                                           const uint4 *__restrict__ cpk,
+                                           const void *__restrict__ tab, float inv_w, int nb,
+                                           uint32_t trash_off)
+{
+#pragma unroll
+    for (int k4 = 0; k4 < 8; ++k4) {
+        const uint4 c4 = cpk[k4];
+        const uint32_t cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            uint32_t d = __vabsdiffu4(cc[u], rpk);
+            d = __vminu4(d, __vsub4(Lpk, d));
+            const uint32_t d2 = __dp4a(d, d, 0u);
+            if (LUT) {
+                off[4 * k4 + u] = reinterpret_cast<const uint16_t *>(tab)[d2];
+            } else {
+                const int b = bin_of_d2((float)d2, inv_w, nb, reinterpret_cast<const float *>(tab));
+                off[4 * k4 + u] = b < nb ? (uint32_t)(b * STRIDE) : trash_off;
+            }
+        }
     }
 }
 
@@ -573,7 +677,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         double *qacc = reinterpret_cast<double *>(epi + EL.qacc);
         double *qred = reinterpret_cast<double *>(epi + EL.qred);
         float4 *colgeo = reinterpret_cast<float4 *>(epi + EL.colgeo);
+        uint32_t *colpk = reinterpret_cast<uint32_t *>(epi + EL.colpk);
         float4 *colcs = reinterpret_cast<float4 *>(epi + EL.colcs);
+        float4 *rowcs = reinterpret_cast<float4 *>(epi + EL.rowcs);
         float *boxred = reinterpret_cast<float *>(epi + EL.boxred);
         float *thr_s = reinterpret_cast<float *>(epi + EL.thr);
         for (int k = et; k < (args.NW + 1) * kBinStride; k += kEpiThreads) bins[k] = 0.f;
@@ -584,6 +690,36 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         for (int k = et; k < args.NQ; k += kEpiThreads) qacc[k] = 0.0;
 
         int cur_p = -1, cur_t = -1, tab_p = -1;
+        // fast lattice binning also needs the private-bin offsets of this launch (the
+        // largest window of a batch, plus its trash row) to fit the 16-bit table entries
+        auto fast_ok = [&](const EpiParams &E) {
+            return E.fast && (args.NW + 1) * kBinStride <= 65536;
+        };
+        // phase weights of pass `pass` (q = pass*kQP ...) of a tile into buffer pass & 1:
+        // the tile's column and row (cos, sin) rows, as asynchronous copies (rows are zero
+        // padded to whole chunks, two q per float4; indices past the problem are clamped,
+        // their accumulator entries being zero or their rows weighed by 0)
+        auto stage_phase = [&](const TileInfo &tq, const TcProblem &Pq, int pass) {
+            const float4 *cs4 = reinterpret_cast<const float4 *>(Pq.epi.cs);
+            const int64_t qo = (int64_t)pass * kQP / 2;
+            const int64_t rl = Pq.epi.nq_pad / 2;
+            float4 *cb = colcs + (pass & 1) * (BN * kQP / 2);
+            float4 *rb = rowcs + (pass & 1) * (kBM * kQP / 2);
+            // shared layouts: columns [c/8][q2][c%8] (the 4 column pairs a warp reads at
+            // once are 32 bytes apart: distinct banks), rows [q2][row]
+            for (int k = et; k < BN * kQP / 2; k += kEpiThreads) {
+                const int c = k / (kQP / 2), q2 = k % (kQP / 2);
+                const int j = min(tq.n0 + c, Pq.N - 1);
+                cp_async16(cb + ((c >> 3) * (kQP / 2) + q2) * 8 + (c & 7),
+                           cs4 + (int64_t)j * rl + qo + q2);
+            }
+            for (int k = et; k < kBM * kQP / 2; k += kEpiThreads) {
+                const int r = k / (kQP / 2), q2 = k % (kQP / 2);
+                const int i = min(tq.m0 + r, Pq.N - 1);
+                cp_async16(rb + q2 * kBM + r, cs4 + (int64_t)i * rl + qo + q2);
+            }
+            cp_async_commit();
+        };
         uint32_t v = 0;
         bool ok = true;
         // per-CTA FP64 sums of the current (problem, t), added to the outputs when it changes
@@ -614,8 +750,15 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             if (E.n_bins > 0 && ti.p != tab_p) {
                 // thresholds, or the lattice d2 -> bin table, of this problem
                 if (E.n_lut > 0) {
+                    // fast form: entries become private-bin word offsets (the host checked
+                    // that (n_bins + 1) * stride fits 16 bits)
+                    // (dropped pairs: the trash row args.NW, which no flush reads)
                     uint16_t *lut_s = reinterpret_cast<uint16_t *>(thr_s);
-                    for (int k = et; k < E.n_lut; k += kEpiThreads) lut_s[k] = E.lut[k];
+                    for (int k = et; k < E.n_lut; k += kEpiThreads) {
+                        const int b = E.lut[k];
+                        lut_s[k] = (uint16_t)(fast_ok(E) ? (b < E.n_bins ? b : args.NW) * kBinStride
+                                                         : b);
+                    }
                 } else {
                     for (int k = et; k < E.n_bins + 2; k += kEpiThreads) thr_s[k] = E.thr[k];
                 }
@@ -627,6 +770,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     const int4 g = E.coords[j];
                     colgeo[c] = make_float4(__int_as_float(g.x), __int_as_float(g.y),
                                             __int_as_float(g.z), 0.f);
+                    colpk[c] = (uint32_t)g.x | ((uint32_t)g.y << 8) | ((uint32_t)g.z << 16);
                 } else {
                     colgeo[c] = E.pos[j];
                 }
@@ -693,6 +837,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 blo = max(0, bin_of_d2(d2min * 0.999f, E.inv_w, E.n_bins, E.thr) - 1);
             }
 
+            if (E.n_q > 0) stage_phase(ti, P, 0);  // lands while the MMAs finish
             const uint32_t acc = v & 1, use = v >> 1;
             const bool got = mbar_wait(tfull0 + 8 * acc, use & 1, args.err, DEV_TIMEOUT_EPI);
             ok = epi_sync_and(got, kEpiThreads);
@@ -713,6 +858,31 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 ba.trash = args.NW;
                 const float scale = row_ok ? 1.f : 0.f;
                 const int mode = !lattice ? BIN_POS : (E.n_lut > 0 ? BIN_LUT : BIN_THR);
+                if (fast_ok(E)) {
+                    // rows past the range skip the pairs (the TMEM loads stay warp-wide)
+                    const uint32_t rpk =
+                        (uint32_t)ri.x | ((uint32_t)ri.y << 8) | ((uint32_t)ri.z << 16);
+                    float *mb = bins + r + kBM * half;
+                    const bool lut = E.n_lut > 0;
+                    const uint32_t trash_off = (uint32_t)args.NW * kBinStride;
+                    for (int ch = ch0; ch < ch1; ++ch) {
+                        // the TMEM load runs while the bin offsets are computed
+                        uint32_t g[32], off[32];
+                        tmem_ld32_issue(tbase + ch * 32, g);
+                        const uint4 *cp = reinterpret_cast<const uint4 *>(colpk + ch * 32);
+                        if (lut)
+                            pk_offsets<true, kBinStride>(off, rpk, E.Lpk, cp, thr_s, E.inv_w,
+                                                         E.n_bins, trash_off);
+                        else
+                            pk_offsets<false, kBinStride>(off, rpk, E.Lpk, cp, thr_s, E.inv_w,
+                                                          E.n_bins, trash_off);
+                        tmem_wait32(g);
+                        if (row_ok) {
+#pragma unroll
+                            for (int k = 0; k < 32; ++k) mb[off[k]] += __uint_as_float(g[k]);
+                        }
+                    }
+                } else
                 for (int ch = ch0; ch < ch1; ++ch) {
                     uint32_t g[32];
                     tmem_ld32(tbase + ch * 32, g);
@@ -727,57 +897,103 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 }
             }
             if (E.n_q > 0) {
-                for (int qc = 0; qc < E.n_q; qc += kQC) {
-                    const int nqc = min(kQC, E.n_q - qc);
-                    epi_sync(kEpiThreads);  // previous users of colcs / qred are done
-                    for (int k = et; k < BN * kQC / 2; k += kEpiThreads) {
-                        const int c = k / (kQC / 2), q2 = (k % (kQC / 2)) * 2;
-                        const int j = min(ti.n0 + c, P.N - 1);
-                        float2 w0 = make_float2(0.f, 0.f), w1 = w0;
-                        if (q2 < nqc) w0 = E.cs[(int64_t)j * E.n_q + qc + q2];
-                        if (q2 + 1 < nqc) w1 = E.cs[(int64_t)j * E.n_q + qc + q2 + 1];
-                        colcs[k] = make_float4(w0.x, w0.y, w1.x, w1.y);
-                    }
-                    float cr[kQC], sr[kQC], u[kQC], vv[kQC];
-#pragma unroll
-                    for (int q = 0; q < kQC; ++q) {
-                        const float2 w = q < nqc ? E.cs[(int64_t)ic * E.n_q + qc + q]
-                                                 : make_float2(0.f, 0.f);
-                        cr[q] = w.x;
-                        sr[q] = w.y;
-                        u[q] = 0.f;
-                        vv[q] = 0.f;
-                    }
+                // Phase weights, kQP q per pass.  The accumulator is read in the 16x256b
+                // shape: a thread holds rows {l/4, l/4+8} (+16 for the second half-quarter)
+                // and columns {2(l%4), 2(l%4)+1} of every 8-column block, so each (cos, sin)
+                // column weight loaded from shared memory serves 4 rows:
+                //   u_r(q) = sum_j c_j(q) G_rj,  v_r(q) = sum_j s_j(q) G_rj  (partial over the
+                // thread's columns), then sum_r c_r(q) u_r(q) + s_r(q) v_r(q) over the warp.
+                // The weights of pass p+1 are copied while pass p computes.
+                const int npass = (E.n_q + kQP - 1) / kQP;
+                const int cq = 2 * (lane & 3);  // this thread's column pair in a block
+                for (int pass = 0; pass < npass; ++pass) {
+                    cp_async_wait_all();
+                    // everyone's copies of this pass are visible; everyone is done with the
+                    // buffer that the next pass's copies overwrite
                     epi_sync(kEpiThreads);
-                    for (int ch = ch0; ch < ch1; ++ch) {
-                        uint32_t g[32];
-                        tmem_ld32(tbase + ch * 32, g);
+                    if (pass + 1 < npass) stage_phase(ti, P, pass + 1);
+                    const float4 *cb = colcs + (pass & 1) * (BN * kQP / 2);
+                    const float4 *rb = rowcs + (pass & 1) * (kBM * kQP / 2);
+                    float u[4][kQP], vv[4][kQP];
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) {
-                            const float val = row_ok ? __uint_as_float(g[k]) : 0.f;
-                            const float4 *w = colcs + (ch * 32 + k) * (kQC / 2);
+                    for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-                            for (int q2 = 0; q2 < kQC / 2; ++q2) {
-                                const float4 w4 = w[q2];
-                                u[2 * q2] = fmaf(w4.x, val, u[2 * q2]);
-                                vv[2 * q2] = fmaf(w4.y, val, vv[2 * q2]);
-                                u[2 * q2 + 1] = fmaf(w4.z, val, u[2 * q2 + 1]);
-                                vv[2 * q2 + 1] = fmaf(w4.w, val, vv[2 * q2 + 1]);
+                        for (int q = 0; q < kQP; ++q) {
+                            u[rr][q] = 0.f;
+                            vv[rr][q] = 0.f;
+                        }
+                    auto chunk = [&](const uint32_t (&g)[2][16], int ch) {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const float4 *w = cb + (ch * 4 + m) * (kQP / 2) * 8 + cq + e;
+#pragma unroll
+                                for (int q2 = 0; q2 < kQP / 2; ++q2) {
+                                    const float4 w4 = w[q2 * 8];
+#pragma unroll
+                                    for (int rr = 0; rr < 4; ++rr) {
+                                        const float gv = __uint_as_float(g[rr >> 1][4 * m + 2 * (rr & 1) + e]);
+                                        u[rr][2 * q2] = fmaf(w4.x, gv, u[rr][2 * q2]);
+                                        vv[rr][2 * q2] = fmaf(w4.y, gv, vv[rr][2 * q2]);
+                                        u[rr][2 * q2 + 1] = fmaf(w4.z, gv, u[rr][2 * q2 + 1]);
+                                        vv[rr][2 * q2 + 1] = fmaf(w4.w, gv, vv[rr][2 * q2 + 1]);
+                                    }
+                                }
                             }
                         }
+                    };
+                    for (int ch = ch0; ch < ch1; ++ch) {
+                        uint32_t g[2][16];
+                        tmem_ld16x256b_x4(tbase + ch * 32, g[0]);
+                        tmem_ld16x256b_x4(tbase + (16u << 16) + ch * 32, g[1]);
+                        tmem_wait16x2(g[0], g[1]);
+                        chunk(g, ch);
                     }
+                    // row weights of the thread's 4 rows (rows past the range weigh 0)
+                    float x[kQP];
 #pragma unroll
-                    for (int q = 0; q < kQC; ++q) {
-                        double c = (double)fmaf(cr[q], u[q], sr[q] * vv[q]);
-                        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-                        if (lane == 0) qred[ew * kQC + q] = c;
+                    for (int q = 0; q < kQP; ++q) x[q] = 0.f;
+#pragma unroll
+                    for (int rr = 0; rr < 4; ++rr) {
+                        const int rrow = q4 * 32 + 16 * (rr >> 1) + 8 * (rr & 1) + (lane >> 2);
+                        const bool ok_r = ti.m0 + rrow < ti.row_end;
+#pragma unroll
+                        for (int q2 = 0; q2 < kQP / 2; ++q2) {
+                            float4 w = rb[q2 * kBM + rrow];
+                            if (!ok_r) w = make_float4(0.f, 0.f, 0.f, 0.f);
+                            x[2 * q2] = fmaf(w.x, u[rr][2 * q2], fmaf(w.y, vv[rr][2 * q2], x[2 * q2]));
+                            x[2 * q2 + 1] = fmaf(w.z, u[rr][2 * q2 + 1],
+                                                 fmaf(w.w, vv[rr][2 * q2 + 1], x[2 * q2 + 1]));
+                        }
                     }
-                    epi_sync(kEpiThreads);
-                    if (et < nqc) {
-                        double sq = 0.0;
-                        for (int w = 0; w < kEpiWarps; ++w) sq += qred[w * kQC + et];
-                        qacc[qc + et] += sq;
+                    // sum over the warp's 32 lanes by recursive halving: each exchange sends
+                    // the half of the q-values this lane does not keep; after three steps a
+                    // lane holds one q (set by lane bits 4..2), the last two add the rest
+#pragma unroll
+                    for (int hh = kQP / 2, o = 16; hh >= 1; hh >>= 1, o >>= 1) {
+                        const bool up = (lane & o) != 0;
+#pragma unroll
+                        for (int k = 0; k < hh; ++k) {
+                            const float send = up ? x[k] : x[k + hh];
+                            const float keep = up ? x[k + hh] : x[k];
+                            x[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                        }
                     }
+                    x[0] += __shfl_xor_sync(0xffffffffu, x[0], 2);
+                    x[0] += __shfl_xor_sync(0xffffffffu, x[0], 1);
+                    if ((lane & 3) == 0) {
+                        const int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 +
+                                      ((lane >> 2) & 1);
+                        qred[(pass * kEpiWarps + ew) * kQP + q] = (double)x[0];
+                    }
+                }
+                epi_sync(kEpiThreads);
+                for (int q = et; q < E.n_q; q += kEpiThreads) {
+                    double sq = 0.0;
+                    for (int w = 0; w < kEpiWarps; ++w)
+                        sq += qred[((q / kQP) * kEpiWarps + w) * kQP + q % kQP];
+                    qacc[q] += sq;
                 }
             }
             // accumulator buffer free for the MMA warp
@@ -813,6 +1029,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 }
             }
         }
+        cp_async_wait_all();  // no copy into this CTA's shared memory outlives it
         epi_sync(kEpiThreads);
         if (ok && cur_p >= 0) flush_acc(cur_p, cur_t);
     }
@@ -872,14 +1089,14 @@ int launch_cl(const LaunchArgs &a, size_t smem, int sm_count, cudaStream_t s)
 }  // namespace
 
 // Launch one precision form.  Instantiated combinations (the rest are rejected):
-//   BN = 256: cluster 1 with 4 or 8 epilogue warps; cluster 4 with the form's default;
-//   BN = 128: cluster 1 with the form's default warps.
+//   BN = 256: cluster 1 with 4 or 8 epilogue warps; cluster 4 with 4 warps;
+//   BN = 128: cluster 1 with 4 warps.
 template <int FORM>
 int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int cl, int ew, int sm_count,
                    cudaStream_t s)
 {
     constexpr int SWB = FORM == ASD_SPLIT_BF16 ? 64 : 128;
-    constexpr int EWD = FORM == ASD_BF16 ? 8 : 4;
+    constexpr int EWD = 4;
     if (BN == 256 && cl == 1 && ew == 4) return launch_cl<FORM, 256, SWB, 1, 4>(a, smem, sm_count, s);
     if (BN == 256 && cl == 1 && ew == 8) return launch_cl<FORM, 256, SWB, 1, 8>(a, smem, sm_count, s);
     if (BN == 256 && cl == 4 && ew == EWD)

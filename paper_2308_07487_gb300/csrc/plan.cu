@@ -86,6 +86,23 @@ static EpiParams epi_of(const asd_corr_plan *p)
     e.thr = p->thr;
     e.lut = p->lut;
     e.n_lut = p->n_lut;
+    // fast lattice binning: coordinates fit a byte (the minimum image |d| <= L/2 and, for
+    // open lattices, |d| <= 127 so that min(d, 255 - d) = d), every bin is private, and
+    // table entries scaled to private-bin offsets fit 16 bits
+    e.fast = 0;
+    e.Lpk = 0;
+    if (p->tc && p->d.geometry == ASD_GEOM_LATTICE && p->n_bins > 0 && !p->use_window) {
+        const int lim = p->d.periodic ? 255 : 128;
+        bool ok = p->d.L[0] <= lim && p->d.L[1] <= lim && p->d.L[2] <= lim;
+        if (p->n_lut > 0) ok = ok && (int64_t)(p->n_bins + 1) * bin_stride(p->EW) <= 65536;
+        if (ok) {
+            e.fast = 1;
+            e.Lpk = p->d.periodic ? ((uint32_t)p->d.L[0] | ((uint32_t)p->d.L[1] << 8) |
+                                     ((uint32_t)p->d.L[2] << 16))
+                                  : 0x00ffffffu;
+        }
+    }
+    e.nq_pad = (p->n_q + kQChunk - 1) / kQChunk * kQChunk;
     e.cs = p->cs;
     return e;
 }
@@ -265,13 +282,11 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
     ASD_CHECK_ARG(d->epi_warps == 0 || d->epi_warps == 4 || d->epi_warps == 8, "epi_warps: 0, 4 or 8");
     {
         // instantiated tensor-core kernels: 256-wide tiles with either warp count (cluster 4
-        // with the form's default); 128-wide tiles with cluster 1 and the default warps
-        const int ew_default = d->precision == ASD_BF16 ? 8 : 4;
-        const int ew = d->epi_warps ? d->epi_warps : ew_default;
-        ASD_CHECK_ARG(!(d->cluster == 4 && ew != ew_default),
-                      "cluster 4 runs with the form's default epi_warps");
-        ASD_CHECK_ARG(!(d->tile_n == 128 && (d->cluster == 4 || ew != ew_default)),
-                      "tile_n = 128 needs cluster 1 and the default epi_warps");
+        // with 4 warps); 128-wide tiles with cluster 1 and 4 warps
+        const int ew = d->epi_warps ? d->epi_warps : 4;
+        ASD_CHECK_ARG(!(d->cluster == 4 && ew != 4), "cluster 4 runs with 4 epilogue warps");
+        ASD_CHECK_ARG(!(d->tile_n == 128 && (d->cluster == 4 || ew != 4)),
+                      "tile_n = 128 needs cluster 1 and 4 epilogue warps");
     }
     for (int k = 0; k < 2; ++k) ASD_CHECK_ARG(d->reserved[k] == 0, "reserved fields must be 0");
     if (d->geometry == ASD_GEOM_LATTICE) {
@@ -342,13 +357,13 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         const int64_t tiles_m_all = (p->N + kBM - 1) / kBM;
         // (measured: sharing B by multicast does not pay here, so clusters are opt-in)
         p->CL = d->cluster ? d->cluster : 1;
-        // epilogue warps (measured): split-BF16 and TF32 are MMA-bound and keep more
-        // pipeline stages with 4; single-product BF16 is epilogue-bound and gains from 8
-        p->EW = d->epi_warps ? d->epi_warps : (d->precision == ASD_BF16 ? 8 : 4);
-        // instantiated kernels: 256-wide tiles with any cluster / warp choice of the form;
-        // 128-wide tiles with one CTA per cluster and the form's default warps
-        const int ew_default = d->precision == ASD_BF16 ? 8 : 4;
-        if (p->CL == 4 || p->EW != ew_default) p->BN = 256;  // combination checked up front
+        // epilogue warps: 4 by default (one launch of a batch needs one count).  8 warps
+        // (opt-in) cap the registers at 168: they help single-product BF16 binning with a
+        // short K on one large problem and lose with phase weights (measured)
+        p->EW = d->epi_warps ? d->epi_warps : 4;
+        // instantiated kernels: 256-wide tiles with either warp count; 128-wide tiles with
+        // one CTA per cluster and 4 warps; clusters of 4 with 4 warps
+        if (p->CL == 4 || p->EW != 4) p->BN = 256;  // combination checked up front
         (void)tiles_m_all;
         // K chunks: split-BF16 is the FP32-accurate form; each chunk's accumulator starts
         // from zero, bounding the FP32 accumulation error of the tensor core to ~1536
@@ -476,7 +491,9 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
             }
         }
         if (p->n_q > 0) {
-            std::vector<float2> cs((size_t)p->N * p->n_q);
+            // rows padded with zeros to whole q-chunks (aligned float4 loads, no tail)
+            const int nqp = (p->n_q + kQChunk - 1) / kQChunk * kQChunk;
+            std::vector<float2> cs((size_t)p->N * nqp, make_float2(0.f, 0.f));
             for (int64_t i = 0; i < p->N; ++i) {
                 double r[3];
                 for (int a = 0; a < 3; ++a)
@@ -484,7 +501,7 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
                                                            : (double)d->pos[3 * i + a];
                 for (int q = 0; q < p->n_q; ++q) {
                     double ph = d->q[3 * q] * r[0] + d->q[3 * q + 1] * r[1] + d->q[3 * q + 2] * r[2];
-                    cs[(size_t)i * p->n_q + q] = make_float2((float)cos(ph), (float)sin(ph));
+                    cs[(size_t)i * nqp + q] = make_float2((float)cos(ph), (float)sin(ph));
                 }
             }
             if (cudaMalloc(&p->cs, sizeof(float2) * cs.size()) != cudaSuccess) {

@@ -194,7 +194,7 @@ def q_path_square(L: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------------
-# Workload configurations (sizes of the paper-style runs)
+# Workload configurations (the sizes of the paper-style runs)
 # ---------------------------------------------------------------------------------
 
 @dataclass

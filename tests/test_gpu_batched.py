@@ -16,7 +16,7 @@ def asd():
     return m
 
 
-def _ensemble(n=6, F=30, T0=16, n_t=10, seed=5):
+def _ensemble(n=6, F=30, T0=16, n_t=10, seed=5, drop=False):
     g = np.random.default_rng(seed)
     out = []
     for k in range(n):
@@ -26,14 +26,17 @@ def _ensemble(n=6, F=30, T0=16, n_t=10, seed=5):
         lat = synth.hypercubic(L, d, True)
         rmax2 = d * (L // 2) ** 2
         n_bins = int(np.floor(np.sqrt(rmax2) / w)) + 1
+        if drop and k % 2 == 0:
+            n_bins = max(2, n_bins // 2)   # the far pairs of this problem are dropped
         tr = synth.traj_precess(lat.n_sites, F, seed=100 + k)
         out.append((lat, tr, w, n_bins))
     return out, F, T0, n_t
 
 
-@pytest.mark.parametrize("form", ["split_bf16", "bf16"])
-def test_batched_matches_oracle_and_single_launches(asd, form):
-    ens, F, T0, n_t = _ensemble()
+@pytest.mark.parametrize("form,drop", [("split_bf16", False), ("bf16", False),
+                                       ("split_bf16", True)])
+def test_batched_matches_oracle_and_single_launches(asd, form, drop):
+    ens, F, T0, n_t = _ensemble(drop=drop)
     plans, trajs, Cs, Cs1 = [], [], [], []
     for lat, tr, w, nb in ens:
         p = asd.CorrPlan.for_lattice(lat, F, T0, n_t, w, nb, precision=form, tile_n=128)

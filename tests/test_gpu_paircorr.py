@@ -171,3 +171,41 @@ def test_cluster_and_k_chunks(asd, form, cluster, k_chunks):
         ref = oracle_ref(lat, tr, 40, 6, 0.5, 14, rows=rows)
         assert_parity({"C_sum": C.cpu().numpy()}, ref, form)
         plan.close()
+
+
+# lattice binning variants: packed-coordinate d2 with the d2 -> bin table (periodic and
+# open), packed d2 with thresholds (table too large), the general path (coordinates past
+# one byte), and too few bins (dropped pairs go to the trash row)
+LATTICE_CASES = {
+    "periodic_table_dropped": (lambda: synth.hypercubic(12, 3, True), 0.5, 9, None),
+    "open_table": (lambda: synth.hypercubic(11, 3, False), 1.0, 12, None),
+    "periodic_thresholds": (lambda: synth.hypercubic(190, 2, True), 1.0, 60, (1000, 1100)),
+    "open_wide_general": (lambda: synth.hypercubic(130, 2, False), 2.0, 50, (16000, 16100)),
+    "periodic_256_general": (lambda: synth.hypercubic(256, 2, True), 1.5, 70, (30000, 30100)),
+}
+
+
+@pytest.mark.parametrize("form", ["split_bf16", "bf16"])
+@pytest.mark.parametrize("case", sorted(LATTICE_CASES))
+def test_lattice_binning_paths(asd, form, case):
+    make, w, nb, rows = LATTICE_CASES[case]
+    lat = make()
+    tr = synth.traj_precess(lat.n_sites, 14, seed=31)
+    got = run_gpu(asd, lat, tr, 8, 5, w, nb, form, rows=rows)
+    ref = oracle_ref(lat, tr, 8, 5, w, nb, rows=rows)
+    if rows is None:
+        np.testing.assert_array_equal(got["counts"], ref["counts"])
+    assert_parity(got, ref, form)
+
+
+@pytest.mark.parametrize("form", ["split_bf16", "bf16", "tf32"])
+def test_phase_on_lattice_row_range(asd, form):
+    """Phase weights on integer lattice coordinates (square-lattice q path, 21 q: a
+    partial last pass), bins at the same time, rows starting and ending mid-tile."""
+    lat = synth.hypercubic(20, 2, True)
+    q = synth.q_path_square(20)[:21]
+    tr = synth.traj_precess(lat.n_sites, 30, seed=12)
+    rows = (37, 301)
+    got = run_gpu(asd, lat, tr, 16, 6, 1.0, 15, form, q=q, rows=rows)
+    ref = oracle_ref(lat, tr, 16, 6, 1.0, 15, q=q, rows=rows)
+    assert_parity(got, ref, form, q=True)
