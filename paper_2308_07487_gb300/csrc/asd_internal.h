@@ -113,7 +113,8 @@ struct TcLaunchArgs {
     int64_t total_tiles;
     TcOverride ov;
     int stages;
-    int NW, NB, NQ, NLUT;  // epilogue shared-memory layout maxima
+    uint32_t VB;           // bytes of the per-problem epilogue region (largest problem)
+    int NB, NQ;            // epilogue shared-memory layout maxima
     int *err;
 };
 
@@ -184,12 +185,16 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
 // pc_tc.cu
 int tc_configure(asd_corr_plan *p);    // stages / smem for the plan's form
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
-              int BN, int swizzle_bytes, int stages, size_t smem, int max_nw, int max_nb,
-              int max_nq, int max_nlut, int cl, int ew, int sm_count, cudaStream_t s);
+              int BN, int swizzle_bytes, int stages, size_t smem, uint32_t var_bytes,
+              int max_nb, int max_nq, int cl, int ew, int sm_count, cudaStream_t s);
 // work items of one problem: n_t * k_chunks * ceil(tiles_m / cl) * tiles_n
 inline int64_t tc_work_items(int n_t, int k_chunks, int tiles_m, int tiles_n, int cl)
 {
     return (int64_t)n_t * k_chunks * ((tiles_m + cl - 1) / cl) * tiles_n;
 }
 size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut, int ew);
+// bytes of the per-problem epilogue region (private bins + bin table)
+uint32_t tc_var_bytes(int NW, int n_bins, int n_lut, int ew);
+// epilogue bytes with the per-problem region given separately
+size_t tc_epilogue_smem_vb(uint32_t var_bytes, int n_bins, int n_q, int BN, int ew);
 }  // namespace asd

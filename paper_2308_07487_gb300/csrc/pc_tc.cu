@@ -13,15 +13,22 @@ extern template int tc_launch_form<ASD_TF32>(const TcLaunchArgs &, size_t, int, 
 extern template int tc_launch_form<ASD_SPLIT_BF16>(const TcLaunchArgs &, size_t, int, int, int,
                                                    int, cudaStream_t);
 
-size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut, int ew)
+uint32_t tc_var_bytes(int NW, int n_bins, int n_lut, int ew) { return var_bytes(NW, n_bins, n_lut, ew); }
+
+size_t tc_epilogue_smem_vb(uint32_t vb, int n_bins, int n_q, int BN, int ew)
 {
-    return epi_layout(NW, n_bins, n_q, BN, n_lut, ew).total;
+    return epi_layout(vb, n_bins, n_q, BN, ew).total;
 }
 
-int tc_configure(asd_corr_plan *p)
+size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut, int ew)
 {
-    const size_t cap = 232448 - 1024 /*alignment slack*/ - 1024 /*barriers*/;
-    const size_t stage_bytes = (size_t)p->n_planes * (kBM + p->BN) * p->swizzle_bytes;
+    return epi_layout(var_bytes(NW, n_bins, n_lut, ew), n_bins, n_q, BN, ew).total;
+}
+
+// Bins window and stage count for the plan's current table choice; returns the number of
+// stages that fit (before any user cap), 0 when the epilogue does not fit at all.
+static int configure_once(asd_corr_plan *p, size_t cap, size_t stage_bytes)
+{
     // private bins: as many as fit with at least 3 stages (2 when tight)
     int NW = p->n_bins;
     p->use_window = 0;
@@ -31,26 +38,49 @@ int tc_configure(asd_corr_plan *p)
         while (NW > 8 && epi(NW) + min_st * stage_bytes > cap) NW = (NW * 3) / 4;
         if (epi(NW) + min_st * stage_bytes <= cap) break;
     }
-    if (epi(NW) + 2 * stage_bytes > cap) {
-        set_error_text("epilogue does not fit shared memory");
-        return ASD_EUNSUPPORTED;
-    }
+    if (epi(NW) + 2 * stage_bytes > cap) return 0;
     if (NW < p->n_bins) p->use_window = 1;
     if (p->n_bins == 0) NW = 0;
     p->NW = NW;
-    int st = (int)((cap - epi(NW)) / stage_bytes);
+    return (int)((cap - epi(NW)) / stage_bytes);
+}
+
+int tc_configure(asd_corr_plan *p)
+{
+    const size_t cap = 232448 - 1024 /*alignment slack*/ - 1024 /*barriers*/;
+    const size_t stage_bytes = (size_t)p->n_planes * (kBM + p->BN) * p->swizzle_bytes;
+    int st = configure_once(p, cap, stage_bytes);
+    // a d2 -> bin table that costs the third pipeline stage (or the whole bin set) is
+    // dropped: the threshold rule bins the same pairs with a few more instructions, and
+    // the third stage is worth more (measured)
+    if (p->n_lut > 0 && (st < 3 || p->use_window)) {
+        const int keep = p->n_lut;
+        p->n_lut = 0;
+        const int st2 = configure_once(p, cap, stage_bytes);
+        if (st2 >= 3 && !p->use_window) {
+            st = st2;
+        } else {
+            p->n_lut = keep;
+            st = configure_once(p, cap, stage_bytes);
+        }
+    }
+    if (st == 0) {
+        set_error_text("epilogue does not fit shared memory");
+        return ASD_EUNSUPPORTED;
+    }
     if (st > 8) st = 8;
     if (p->d.stages > 0 && p->d.stages < st) st = p->d.stages;
     p->stages = st;
-    p->smem_bytes = epi(NW) + (size_t)p->stages * stage_bytes + 2048;
+    p->smem_bytes = tc_epilogue_smem(p->NW, p->n_bins, p->n_q, p->BN, p->n_lut, p->EW) +
+                    (size_t)p->stages * stage_bytes + 2048;
     // more than half of the SM's shared memory: never two CTAs (and TMEM owners) per SM
     if (p->smem_bytes < kMinSmem) p->smem_bytes = kMinSmem;
     return ASD_OK;
 }
 
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
-              int BN, int swizzle_bytes, int stages, size_t smem, int max_nw, int max_nb,
-              int max_nq, int max_nlut, int cl, int ew, int sm_count, cudaStream_t s)
+              int BN, int swizzle_bytes, int stages, size_t smem, uint32_t var_bytes_,
+              int max_nb, int max_nq, int cl, int ew, int sm_count, cudaStream_t s)
 {
     if (total_tiles <= 0) return ASD_OK;
     LaunchArgs a{};
@@ -59,10 +89,9 @@ int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOver
     a.total_tiles = total_tiles;
     a.ov = ov;
     a.stages = stages;
-    a.NW = max_nw;
+    a.VB = var_bytes_;
     a.NB = max_nb;
     a.NQ = max_nq;
-    a.NLUT = max_nlut;
     a.err = device_error_word();
     if (!a.err) return ASD_ECUDA;
     (void)swizzle_bytes;

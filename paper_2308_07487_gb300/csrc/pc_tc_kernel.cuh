@@ -331,7 +331,7 @@ __host__ __device__ constexpr uint32_t idesc(bool tf32, int N)
 // shared-memory layout of the epilogue region
 // ------------------------------------------------------------------------------------
 struct EpiLayout {
-    uint32_t cacc, qacc, qred, bins, fb, colgeo, colpk, colcs, rowcs, boxred, thr, total;
+    uint32_t cacc, qacc, qred, fb, colgeo, colpk, colcs, rowcs, boxred, var, total;
 };
 
 __host__ __device__ inline uint32_t take(uint32_t &o, uint32_t bytes)
@@ -342,7 +342,23 @@ __host__ __device__ inline uint32_t take(uint32_t &o, uint32_t bytes)
     return r;
 }
 
-__host__ __device__ inline EpiLayout epi_layout(int NW, int nb, int nq, int BN, int nlut, int ew)
+// The per-problem part of the epilogue's shared memory: the private bins (NW + 1 rows,
+// the last one the trash row of dropped pairs) followed by the bin threshold pairs (FP32)
+// or, for lattices, the d2 -> bin table (uint16).  A batched launch sizes it for the
+// largest problem and lays it out again whenever the problem changes.
+__host__ __device__ inline uint32_t var_bins_bytes(int NW, int ew)
+{
+    return (4u * (NW + 1) * bin_stride(ew) + 15u) & ~15u;
+}
+__host__ __device__ inline uint32_t var_bytes(int NW, int nb, int nlut, int ew)
+{
+    const uint32_t tb = 8u * (nb + 1), lb = 2u * nlut;
+    return var_bins_bytes(NW, ew) + (((tb > lb ? tb : lb) + 15u) & ~15u);
+}
+
+// Epilogue shared memory: the fixed arrays (sized for the largest n_bins / n_q of the
+// launch) and the per-problem region of `vb` bytes.
+__host__ __device__ inline EpiLayout epi_layout(uint32_t vb, int nb, int nq, int BN, int ew)
 {
     EpiLayout L;
     uint32_t o = 0;
@@ -350,7 +366,6 @@ __host__ __device__ inline EpiLayout epi_layout(int NW, int nb, int nq, int BN, 
     L.qacc = take(o, 8u * (nq > 0 ? nq : 1));
     // one slot per (pass, warp, q): the passes of a tile are reduced once at its end
     L.qred = take(o, 8u * ew * (nq > 0 ? (nq + kQP - 1) / kQP * kQP : kQP));
-    L.bins = take(o, 4u * (NW + 1) * bin_stride(ew));
     L.fb = take(o, 4u * (nb > 0 ? nb : 1));
     L.colgeo = take(o, 16u * BN);
     L.colpk = take(o, 4u * BN);
@@ -358,9 +373,7 @@ __host__ __device__ inline EpiLayout epi_layout(int NW, int nb, int nq, int BN, 
     L.colcs = nq > 0 ? take(o, 2u * 8u * BN * kQP) : 0u;
     L.rowcs = nq > 0 ? take(o, 2u * 8u * kBM * kQP) : 0u;
     L.boxred = take(o, 4u * ew * 12);
-    // bin thresholds (FP32) or, for lattices, the d2 -> bin table (uint16), same region
-    const uint32_t tb = 4u * (nb + 2), lb = 2u * nlut;
-    L.thr = take(o, tb > lb ? tb : lb);
+    L.var = take(o, vb);
     L.total = (o + 1023u) & ~1023u;
     return L;
 }
@@ -374,45 +387,81 @@ struct TileInfo {
 // CTAs, a work item is a cluster tile: CL consecutive row tiles that share one column
 // tile; CTA `rank` of the cluster takes row tile mc * CL + rank.  K chunks split the
 // contraction so that each partial accumulator starts from zero (see kChunkK).
+// Per-role walk over the work list.  A role visits its work items in increasing order,
+// so the problem of the next item is found by stepping forward from the current one, and
+// the fields that decoding needs stay in registers until the problem changes (a batched
+// launch would otherwise repeat a search over the descriptors in global memory per item).
+struct WorkCursor {
+    int p = -1;
+    int64_t begin = 0, end = 0;  // flattened items [begin, end) belong to problem p
+    int tiles_mc, tiles_n, kch, G, nk, row_begin, row_end;
+    int64_t per_kc;
+};
+
 template <int CL>
-__device__ __forceinline__ TileInfo decode(const TcProblem *__restrict__ probs, int n_probs,
-                                           const TcOverride &ov, int64_t tau, int BN, int rank)
+__device__ __forceinline__ TileInfo decode(WorkCursor &cu, const TcProblem *__restrict__ probs,
+                                           int n_probs, const TcOverride &ov, int64_t tau,
+                                           int BN, int rank)
 {
-    int p = 0;
-    if (n_probs > 1) {
-        int lo = 0, hi = n_probs - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (probs[mid].tile_begin <= tau) lo = mid;
-            else hi = mid - 1;
+    if (cu.p < 0 || tau >= cu.end) {
+        int p = cu.p < 0 ? 0 : cu.p;
+        if (n_probs > 1) {
+            if (cu.p < 0) {
+                int lo = 0, hi = n_probs - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (probs[mid].tile_begin <= tau) lo = mid;
+                    else hi = mid - 1;
+                }
+                p = lo;
+            } else {
+                while (p + 1 < n_probs && probs[p + 1].tile_begin <= tau) ++p;
+            }
         }
-        p = lo;
+        const TcProblem &P = probs[p];
+        cu.p = p;
+        const int tiles_m = ov.active ? ov.tiles_m : P.tiles_m;
+        cu.begin = ov.active ? 0 : P.tile_begin;
+        cu.end = cu.begin + (ov.active ? ov.n_tiles : P.n_tiles);
+        cu.tiles_mc = (tiles_m + CL - 1) / CL;
+        cu.tiles_n = P.tiles_n;
+        cu.kch = P.k_chunks;
+        cu.G = max(1, P.group_m / CL);
+        cu.nk = P.S * P.nkb;
+        cu.row_begin = ov.active ? ov.row_begin : P.row_begin;
+        cu.row_end = ov.active ? ov.row_end : P.row_end;
+        cu.per_kc = (int64_t)cu.tiles_mc * cu.tiles_n;
     }
-    const TcProblem &P = probs[p];
-    const int tiles_m = ov.active ? ov.tiles_m : P.tiles_m;
-    const int row_begin = ov.active ? ov.row_begin : P.row_begin;
-    const int64_t l = tau - (ov.active ? 0 : P.tile_begin);
-    const int tiles_mc = (tiles_m + CL - 1) / CL;
-    const int64_t per_kc = (int64_t)tiles_mc * P.tiles_n;
-    const int kch = P.k_chunks;
+    const int64_t l = tau - cu.begin;
     TileInfo ti;
-    ti.p = p;
-    ti.t = (int)(l / (per_kc * kch));
-    const int64_t rem0 = l % (per_kc * kch);
-    const int kc = (int)(rem0 / per_kc);
-    const int64_t rem = rem0 % per_kc;
-    const int G = max(1, P.group_m / CL);
-    const int64_t gspan = (int64_t)G * P.tiles_n;
-    const int first_m = (int)(rem / gspan) * G;
-    const int gsz = min(G, tiles_mc - first_m);
+    ti.p = cu.p;
+    ti.t = (int)(l / (cu.per_kc * cu.kch));
+    const int64_t rem0 = l % (cu.per_kc * cu.kch);
+    const int kc = (int)(rem0 / cu.per_kc);
+    const int64_t rem = rem0 % cu.per_kc;
+    const int64_t gspan = (int64_t)cu.G * cu.tiles_n;
+    const int first_m = (int)(rem / gspan) * cu.G;
+    const int gsz = min(cu.G, cu.tiles_mc - first_m);
     const int64_t r2 = rem % gspan;
-    ti.m0 = row_begin + ((first_m + (int)(r2 % gsz)) * CL + rank) * kBM;
+    ti.m0 = cu.row_begin + ((first_m + (int)(r2 % gsz)) * CL + rank) * kBM;
     ti.n0 = (int)(r2 / gsz) * BN;
-    ti.row_end = ov.active ? ov.row_end : P.row_end;
-    const int nk = P.S * P.nkb;
-    ti.kg0 = (int)((int64_t)kc * nk / kch);
-    ti.kg1 = (int)((int64_t)(kc + 1) * nk / kch);
+    ti.row_end = cu.row_end;
+    ti.kg0 = (int)((int64_t)kc * cu.nk / cu.kch);
+    ti.kg1 = (int)((int64_t)(kc + 1) * cu.nk / cu.kch);
     return ti;
+}
+
+// Exact bin of an FP32 d2 from a table of threshold pairs thr2[k] = (thr[k], thr[k+1]),
+// thr[k] = (k w)^2 rounded up to FP32: a first guess from the square root, then one
+// 8-byte load corrects it by one either way (the same result as two dependent fix-ups,
+// since the guess is within one bin).  Returns 0 .. n_bins + 1 (>= n_bins: dropped).
+__device__ __forceinline__ int bin_of_d2_pair(float d2, float inv_w, int nb,
+                                              const float2 *__restrict__ thr2)
+{
+    const float r = d2 * rsqrtf(fmaxf(d2, 1e-30f));
+    const int k = min((int)(r * inv_w), nb);
+    const float2 t = thr2[k];
+    return k + (d2 >= t.y ? 1 : 0) - (d2 < t.x ? 1 : 0);
 }
 
 // Per-tile constants of the binning epilogue, held in registers.
@@ -444,7 +493,8 @@ __device__ __forceinline__ void bin_chunk(const uint32_t (&g)[32], float scale, 
         const float4 cg = cgeo[k];
         int b;
         if (MODE == BIN_POS) {
-            b = bin_of_d2(position_d2(rp, cg), ba.inv_w, ba.nb, thr);
+            b = bin_of_d2_pair(position_d2(rp, cg), ba.inv_w, ba.nb,
+                               reinterpret_cast<const float2 *>(thr));
         } else {
             const int4 cj = make_int4(__float_as_int(cg.x), __float_as_int(cg.y),
                                       __float_as_int(cg.z), 0);
@@ -452,7 +502,8 @@ __device__ __forceinline__ void bin_chunk(const uint32_t (&g)[32], float scale, 
             if (MODE == BIN_LUT)
                 b = reinterpret_cast<const uint16_t *>(thr)[d2];
             else
-                b = bin_of_d2((float)d2, ba.inv_w, ba.nb, thr);
+                b = bin_of_d2_pair((float)d2, ba.inv_w, ba.nb,
+                                   reinterpret_cast<const float2 *>(thr));
         }
         const int lb = b - ba.blo;
         slot[k] = (unsigned)lb < (unsigned)ba.nwp ? lb : (b < ba.nb ? -1 - b : ba.trash);
@@ -488,7 +539,8 @@ __device__ __forceinline__ void pk_offsets(uint32_t (&off)[32], uint32_t rpk, ui
             if (LUT) {
                 off[4 * k4 + u] = reinterpret_cast<const uint16_t *>(tab)[d2];
             } else {
-                const int b = bin_of_d2((float)d2, inv_w, nb, reinterpret_cast<const float *>(tab));
+                const int b =
+                    bin_of_d2_pair((float)d2, inv_w, nb, reinterpret_cast<const float2 *>(tab));
                 off[4 * k4 + u] = b < nb ? (uint32_t)(b * STRIDE) : trash_off;
             }
         }
@@ -528,7 +580,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     const int stages = args.stages;
     uint8_t *tiles = smem;
     uint8_t *epi = tiles + (size_t)stages * kStageBytes;
-    const EpiLayout EL = epi_layout(args.NW, args.NB, args.NQ, BN, args.NLUT, EW);
+    const EpiLayout EL = epi_layout(args.VB, args.NB, args.NQ, BN, EW);
     uint64_t *bars = reinterpret_cast<uint64_t *>(epi + EL.total);
     // bars: full[stages], empty[stages], tfull[2], tempty[2], drain
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 5);
@@ -567,8 +619,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
+            WorkCursor cu;
             for (int64_t tau = cid; tau < args.total_tiles && ok; tau += n_clusters) {
-                const TileInfo ti = decode<CL>(probs, args.n_probs, args.ov, tau, BN, rank);
+                const TileInfo ti = decode<CL>(cu, probs, args.n_probs, args.ov, tau, BN, rank);
                 const TcProblem &P = probs[ti.p];
                 for (int kg = ti.kg0; kg < ti.kg1; ++kg) {
                     const int s = kg / P.nkb, kb = kg % P.nkb;
@@ -616,8 +669,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             uint32_t phase = 0;
             uint32_t v = 0;
             bool ok = true;
+            WorkCursor cu;
             for (int64_t tau = cid; tau < args.total_tiles && ok; tau += n_clusters, ++v) {
-                const TileInfo ti = decode<CL>(probs, args.n_probs, args.ov, tau, BN, rank);
+                const TileInfo ti = decode<CL>(cu, probs, args.n_probs, args.ov, tau, BN, rank);
                 const uint32_t acc = v & 1, use = v >> 1;
                 if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, args.err, DEV_TIMEOUT_MMA)) {
                     ok = false;
@@ -671,7 +725,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         const int ew = warp - 2;                  // epilogue warp 0..7
         const int half = ew >> 2;                 // which part of the columns (EW = 8)
         const int ch0 = half * (BN / 32 / kHalves), ch1 = ch0 + BN / 32 / kHalves;
-        float *bins = reinterpret_cast<float *>(epi + EL.bins);
+        // private bins and bin table of the current problem (set when the problem changes)
+        float *bins = reinterpret_cast<float *>(epi + EL.var);
         float *fb = reinterpret_cast<float *>(epi + EL.fb);
         double *cacc = reinterpret_cast<double *>(epi + EL.cacc);
         double *qacc = reinterpret_cast<double *>(epi + EL.qacc);
@@ -681,8 +736,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         float4 *colcs = reinterpret_cast<float4 *>(epi + EL.colcs);
         float4 *rowcs = reinterpret_cast<float4 *>(epi + EL.rowcs);
         float *boxred = reinterpret_cast<float *>(epi + EL.boxred);
-        float *thr_s = reinterpret_cast<float *>(epi + EL.thr);
-        for (int k = et; k < (args.NW + 1) * kBinStride; k += kEpiThreads) bins[k] = 0.f;
+        float *thr_s = bins;
         for (int k = et; k < args.NB; k += kEpiThreads) {
             fb[k] = 0.f;
             cacc[k] = 0.0;
@@ -690,10 +744,11 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         for (int k = et; k < args.NQ; k += kEpiThreads) qacc[k] = 0.0;
 
         int cur_p = -1, cur_t = -1, tab_p = -1;
+        WorkCursor cu;
         // fast lattice binning also needs the private-bin offsets of this launch (the
         // largest window of a batch, plus its trash row) to fit the 16-bit table entries
         auto fast_ok = [&](const EpiParams &E) {
-            return E.fast && (args.NW + 1) * kBinStride <= 65536;
+            return E.fast && (E.NW + 1) * kBinStride <= 65536;
         };
         // phase weights of pass `pass` (q = pass*kQP ...) of a tile into buffer pass & 1:
         // the tile's column and row (cos, sin) rows, as asynchronous copies (rows are zero
@@ -737,7 +792,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             }
         };
         for (int64_t tau = cid; tau < args.total_tiles; tau += n_clusters, ++v) {
-            const TileInfo ti = decode<CL>(probs, args.n_probs, args.ov, tau, BN, rank);
+            const TileInfo ti = decode<CL>(cu, probs, args.n_probs, args.ov, tau, BN, rank);
             const TcProblem &P = probs[ti.p];
             const EpiParams &E = P.epi;
             const int i = ti.m0 + r;
@@ -748,19 +803,28 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             const bool lattice = E.geom == ASD_GEOM_LATTICE;
             // bin thresholds of this problem, then the column geometry of this tile
             if (E.n_bins > 0 && ti.p != tab_p) {
+                // lay out the per-problem region for this problem: every thread is done
+                // with the previous problem's bins (flushed and zeroed at each tile's end)
+                // and table, then the new bins are zeroed and the new table loaded
+                epi_sync(kEpiThreads);
+                bins = reinterpret_cast<float *>(epi + EL.var);
+                thr_s = reinterpret_cast<float *>(epi + EL.var + var_bins_bytes(E.NW, EW));
+                for (int k = et; k < (E.NW + 1) * kBinStride; k += kEpiThreads) bins[k] = 0.f;
                 // thresholds, or the lattice d2 -> bin table, of this problem
                 if (E.n_lut > 0) {
                     // fast form: entries become private-bin word offsets (the host checked
                     // that (n_bins + 1) * stride fits 16 bits)
-                    // (dropped pairs: the trash row args.NW, which no flush reads)
+                    // (dropped pairs: the trash row E.NW, which no flush reads)
                     uint16_t *lut_s = reinterpret_cast<uint16_t *>(thr_s);
                     for (int k = et; k < E.n_lut; k += kEpiThreads) {
                         const int b = E.lut[k];
-                        lut_s[k] = (uint16_t)(fast_ok(E) ? (b < E.n_bins ? b : args.NW) * kBinStride
+                        lut_s[k] = (uint16_t)(fast_ok(E) ? (b < E.n_bins ? b : E.NW) * kBinStride
                                                          : b);
                     }
                 } else {
-                    for (int k = et; k < E.n_bins + 2; k += kEpiThreads) thr_s[k] = E.thr[k];
+                    float2 *thr2 = reinterpret_cast<float2 *>(thr_s);
+                    for (int k = et; k <= E.n_bins; k += kEpiThreads)
+                        thr2[k] = make_float2(E.thr[k], E.thr[k + 1]);
                 }
                 tab_p = ti.p;
             }
@@ -854,8 +918,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 ba.inv_w = E.inv_w;
                 ba.nb = E.n_bins;
                 ba.blo = E.use_window ? blo : 0;
-                ba.nwp = E.use_window ? args.NW : E.n_bins;
-                ba.trash = args.NW;
+                ba.nwp = E.use_window ? E.NW : E.n_bins;
+                ba.trash = E.NW;
                 const float scale = row_ok ? 1.f : 0.f;
                 const int mode = !lattice ? BIN_POS : (E.n_lut > 0 ? BIN_LUT : BIN_THR);
                 if (fast_ok(E)) {
@@ -864,7 +928,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         (uint32_t)ri.x | ((uint32_t)ri.y << 8) | ((uint32_t)ri.z << 16);
                     float *mb = bins + r + kBM * half;
                     const bool lut = E.n_lut > 0;
-                    const uint32_t trash_off = (uint32_t)args.NW * kBinStride;
+                    const uint32_t trash_off = (uint32_t)E.NW * kBinStride;
                     for (int ch = ch0; ch < ch1; ++ch) {
                         // the TMEM load runs while the bin offsets are computed
                         uint32_t g[32], off[32];
@@ -1002,7 +1066,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
             epi_sync(kEpiThreads);  // all private bins written
             if (E.n_bins > 0) {
-                const int NWp = E.use_window ? args.NW : E.n_bins;
+                const int NWp = E.use_window ? E.NW : E.n_bins;
                 // epilogue warp ew reduces bins b = ew (mod 8): 8 conflict-free loads per
                 // lane, an FP32 tree over the 256 entries, one FP64 add per bin (the FP64
                 // pipe is narrow on this part, so FP64 work is kept per bin, not per row)
