@@ -161,6 +161,24 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
                           double *const *C_sum, double *const *Sq_sum, void *stream);
 
 /*
+ * Separable evaluation of the phase-weighted sum: the same quantity as the Sq_sum of
+ * asd_pair_corr (the cosine part of Eq. 3 with the weights of Eq. 6, over all ordered
+ * pairs, B centred when the plan centres), through cos(a - b) = cos a cos b + sin a sin b:
+ * per-site transforms Fc(q; s,f,a) = sum_i cos(q.r_i) S_i(s,f,a) (and Fs with sin) of every
+ * frame (FP32 within slices of 4096 sites, FP64 across slices), then
+ *   Sq_sum[t][q] += sum_{s,a,t0<T0} Fc(s,t0+t,a) Fc_B(s,t0,a) + Fs(s,t0+t,a) Fs_B(s,t0,a)
+ * in FP64.  O(N S F n_q) work instead of O(N^2 S T0 n_t); the paper evaluates the pair
+ * form, which asd_pair_corr keeps.
+ *   plan    a plan with n_q > 0 (any precision form; the transform is FP32 SIMT)
+ *   traj    device [N][S][F][3] FP32, all sites (no row range)
+ *   Sq_sum  device [n_t][n_q] FP64, accumulated into
+ * Uses the plan's transform buffer (allocated at plan creation): calls on one plan must
+ * not overlap.  Enqueue-only (no synchronisation, no allocation).
+ */
+int asd_pair_corr_sq_separable(asd_corr_plan *plan, const float *traj, double *Sq_sum,
+                               void *stream);
+
+/*
  * Eq. 3 / Eq. 4 normalisation (device buffers, may alias their inputs):
  *   C[t][b]  = C_sum[t][b] / (S*T0*n_b)   (0 where n_b = 0)
  *   Sq[t][q] = Sq_sum[t][q] / (N*S*T0)
@@ -172,6 +190,16 @@ int asd_pair_corr_normalize(const asd_corr_plan *plan, const double *C_sum, cons
 /* Synchronise `stream` and report (then clear) the device error word:
  * ASD_OK, ASD_ETIMEOUT or ASD_ECUDA. */
 int asd_sync_status(void *stream);
+
+/*
+ * Self-test of the failure path (the paper has no counterpart).  Enqueues on `stream` one
+ * thread that waits, through the same bounded wait every mbarrier wait of the tensor-core
+ * kernel uses, on a barrier that nothing ever arrives on.  After limit_ns nanoseconds
+ * (1 .. 1e9) the wait gives up, records a timeout in the device error word and the kernel
+ * returns, so the context stays usable and the next asd_sync_status reports ASD_ETIMEOUT
+ * (and clears the word).  Returns ASD_EINVAL for a limit out of range; nothing is allocated.
+ */
+int asd_selftest_timeout(int64_t limit_ns, void *stream);
 
 /* Static text for a status code (ASD_ECUDA includes the last CUDA error). */
 const char *asd_strerror(int status);

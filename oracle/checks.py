@@ -77,7 +77,13 @@ def lattice_fft_corr(traj, T0, t_list, coords, L, periodic, w, n_bins):
 
 
 def separable_phase_sum(traj, T0, t_list, pos, q, center=False):
-    """Sq_sum[t][q] = sum_ij cos(q.(r_i-r_j)) G_ij(t) through the factorised transform."""
+    """Sq_sum[t][q] = sum_ij cos(q.(r_i-r_j)) G_ij(t) through the factorised transform.
+
+    F^c = C^T X and F^s = S^T X with C[i][q] = cos(q.r_i), S[i][q] = sin(q.r_i) and X the
+    trajectory flattened to [N][S*F*3] (FP64 matrix products), then per t the sum over
+    samples, origins and components of F(t0 + t) F(t0).  Centring (per site, over samples
+    and origins, of both operands as in Eq. 5) is linear, so it is applied to the
+    transforms: the transform of a centred operand is the transform minus its mean."""
     tr = np.asarray(traj, np.float64)
     if tr.ndim == 3:
         tr = tr[:, None]
@@ -85,20 +91,20 @@ def separable_phase_sum(traj, T0, t_list, pos, q, center=False):
     r = np.asarray(pos, np.float64)
     ph = r @ np.asarray(q, np.float64).T            # [N][n_q]
     c, s = np.cos(ph), np.sin(ph)
+    X = tr.reshape(N, S * F * 3)
+    Fc = (c.T @ X).reshape(-1, S, F, 3)             # [n_q][S][F][3]
+    Fs = (s.T @ X).reshape(-1, S, F, 3)
     t_list = np.atleast_1d(t_list)
     out = np.zeros((len(t_list), len(q)))
-    B = tr[:, :, :T0]                               # [N][S][T0][3]
-    if center:
-        B = B - B.mean(axis=(1, 2), keepdims=True)
-    Fc_B = np.einsum("iq,isfa->qsfa", c, B)
-    Fs_B = np.einsum("iq,isfa->qsfa", s, B)
-    for k, t in enumerate(t_list):
-        A = tr[:, :, t:t + T0]
+
+    def window(Fx, t):
+        w = Fx[:, :, t:t + T0]
         if center:
-            A = A - A.mean(axis=(1, 2), keepdims=True)
-        Fc_A = np.einsum("iq,isfa->qsfa", c, A)
-        Fs_A = np.einsum("iq,isfa->qsfa", s, A)
-        out[k] = (Fc_A * Fc_B).sum(axis=(1, 2, 3)) + (Fs_A * Fs_B).sum(axis=(1, 2, 3))
+            w = w - w.mean(axis=(1, 2), keepdims=True)
+        return w
+    Bc, Bs = window(Fc, 0), window(Fs, 0)
+    for k, t in enumerate(t_list):
+        out[k] = (window(Fc, t) * Bc).sum(axis=(1, 2, 3)) + (window(Fs, t) * Bs).sum(axis=(1, 2, 3))
     return out
 
 

@@ -73,6 +73,8 @@ _SIGS = {
                                              ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     "asd_pair_corr_normalize": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "asd_sync_status": (ctypes.c_int, [_VP]),
+    "asd_pair_corr_sq_separable": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "asd_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, _VP]),
     "asd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "asd_ll_integrate": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP, ctypes.c_float,
                                         ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
@@ -212,6 +214,11 @@ class CorrPlan:
         check(lib.asd_pair_corr_contract(self.handle, r0, r1, _ptr(C_sum), _ptr(Sq_sum),
                                          _stream(stream)), "pair_corr_contract")
 
+    def sq_separable(self, traj, Sq_sum, stream=None):
+        """asd_pair_corr_sq_separable: the phase-weighted sum through per-site transforms."""
+        check(lib.asd_pair_corr_sq_separable(self.handle, _ptr(traj), _ptr(Sq_sum),
+                                             _stream(stream)), "pair_corr_sq_separable")
+
     def normalize(self, C_sum=None, Sq_sum=None, C=None, Sq=None, stream=None):
         check(lib.asd_pair_corr_normalize(self.handle, _ptr(C_sum), _ptr(Sq_sum), _ptr(C), _ptr(Sq),
                                           _stream(stream)), "normalize")
@@ -239,6 +246,11 @@ def pair_corr_batched(plans, trajs, C_sums, Sq_sums=None, stream=None):
 
 def sync_status(stream=None):
     return lib.asd_sync_status(_stream(stream))
+
+
+def selftest_timeout(limit_ns, stream=None):
+    """asd_selftest_timeout: a bounded wait that runs out; read with sync_status."""
+    check(lib.asd_selftest_timeout(int(limit_ns), _stream(stream)), "selftest_timeout")
 
 
 class Mlp:

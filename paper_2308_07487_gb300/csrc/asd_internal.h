@@ -35,7 +35,13 @@ void set_error_text(const std::string &s);
     } while (0)
 
 // Device error word (one per device, module scope): bounded waits write a code here.
-enum DeviceError : int { DEV_OK = 0, DEV_TIMEOUT_TMA = 1, DEV_TIMEOUT_MMA = 2, DEV_TIMEOUT_EPI = 3 };
+enum DeviceError : int {
+    DEV_OK = 0,
+    DEV_TIMEOUT_TMA = 1,
+    DEV_TIMEOUT_MMA = 2,
+    DEV_TIMEOUT_EPI = 3,
+    DEV_TIMEOUT_SELFTEST = 4
+};
 int *device_error_word();          // device address of the word for the current device
 
 // ----------------------------------------------------------------------------------
@@ -156,6 +162,7 @@ struct asd_corr_plan {
     uint16_t *lut;             // lattice d2 -> bin table (nullptr when d2 can reach kLutMax)
     int n_lut;
     float2 *cs;
+    double *sqF;               // separable phase form: transforms [2 n_q][S*3F] (n_q > 0)
     int tiles_m_all, tiles_n;
     int use_window;
     int NW;

@@ -103,4 +103,28 @@ int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOver
     }
 }
 
+// One thread waits, through the bounded wait of the tensor-core kernel, on an mbarrier
+// that nothing arrives on: after limit_ns the wait records DEV_TIMEOUT_SELFTEST in the
+// device error word and the kernel returns.
+__global__ void wait_selftest_kernel(int *err, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(saddr(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        (void)mbar_wait_for(saddr(&bar), 0, err, DEV_TIMEOUT_SELFTEST, limit_ns);
+    }
+}
+
 }  // namespace asd
+
+int asd_selftest_timeout(int64_t limit_ns, void *stream)
+{
+    using namespace asd;
+    ASD_CHECK_ARG(limit_ns > 0 && limit_ns <= 1000000000, "limit_ns: 1 .. 1e9");
+    int *err = device_error_word();
+    if (!err) return ASD_ECUDA;
+    wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(err, (unsigned long long)limit_ns);
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}

@@ -95,17 +95,23 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
 
 // Bounded wait for the phase with the given parity; false after kTimeoutNs (the error
 // word then holds `code`).
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code)
+__device__ __noinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, int *err, int code,
+                                          unsigned long long limit_ns)
 {
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_test(bar, parity)) return true;
-        if ((it & 1023u) == 0 && gtimer() - t0 > kTimeoutNs) {
+        if ((it & 1023u) == 0 && gtimer() - t0 > limit_ns) {
             atomicCAS(err, 0, code);
             return false;
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code)
+{
+    return mbar_wait_for(bar, parity, err, code, kTimeoutNs);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,

@@ -242,6 +242,7 @@ void asd_pair_corr_plan_destroy(asd_corr_plan *p)
     cudaFree(p->thr);
     cudaFree(p->lut);
     cudaFree(p->cs);
+    cudaFree(p->sqF);
     cudaFree(p->inv_counts);
     cudaFree(p->d_prob);
     delete p->h_prob;
@@ -510,6 +511,12 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
             }
             if (cudaMemcpy(p->cs, cs.data(), sizeof(float2) * cs.size(), cudaMemcpyHostToDevice))
                 return fail(ASD_ECUDA);
+            // transforms of the separable phase form (asd_pair_corr_sq_separable)
+            const size_t fb = sizeof(double) * 2 * (size_t)p->n_q * p->S * 3 * p->F;
+            if (cudaMalloc(&p->sqF, fb) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ASD_ENOMEM);
+            }
         }
     }
 
