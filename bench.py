@@ -327,6 +327,44 @@ def run_ours(args, W, ws, rank, local):
         out["forms"] = forms
         out["speedup_split_bf16_vs_fp32"] = forms["split_bf16"]["TFLOP/s"] / forms["fp32"]["TFLOP/s"]
 
+        # Unfused comparison (context, library path): cuBLAS through torch.matmul forms the
+        # N x N matrix of one displacement in HBM; a separate binning pass must then read it
+        # back, which costs at least N^2 * 4 B at the measured copy bandwidth.
+        tv = traj.view(N, -1)
+        t_u = min(7, n_t - 1)
+        A_t, B_0 = tv[:, 3 * t_u:3 * t_u + K], tv[:, :K]
+        unf = {}
+        tf32_was = torch.backends.cuda.matmul.allow_tf32
+        for name in ("fp32", "tf32", "bf16"):
+            torch.backends.cuda.matmul.allow_tf32 = name == "tf32"
+            a_, b_ = (A_t.to(torch.bfloat16), B_0.to(torch.bfloat16)) if name == "bf16" else (A_t, B_0)
+            holder = {}
+
+            def gemm():
+                holder["G"] = None
+                holder["G"] = torch.matmul(a_, b_.t())
+            gemm()
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            gemm()
+            ev1.record()
+            torch.cuda.synchronize()
+            unf[name + "_gemm_ms"] = ev0.elapsed_time(ev1)
+            unf[name + "_gemm_output"] = str(holder["G"].dtype).replace("torch.", "")
+            holder.clear()
+            del a_, b_
+            torch.cuda.empty_cache()
+        torch.backends.cuda.matmul.allow_tf32 = tf32_was
+        pk0, _ = peaks()
+        unf["binning_read_lower_bound_ms"] = N * N * 4 / (pk0["hbm_gbs"] * 1e9) * 1e3
+        unf["fused_ms_per_displacement"] = {f: 2.0 * N * N * K / (forms[f]["TFLOP/s"] * 1e12) * 1e3
+                                            for f in forms}
+        unf["note"] = ("per displacement; cuBLAS fp32 is the accuracy peer of split_bf16, "
+                       "tf32 / bf16 of the fused tf32 / bf16 forms; N x N FP32 = "
+                       f"{N * N * 4 / 1e9:.1f} GB per displacement")
+        out["unfused_cublas"] = unf
+
         # CPU oracle on rows 0..R (about 10-15 s on 16 host cores), three displacements, and
         # the per-bin error of the timed form on the same rows
         rows = (0, 256)
@@ -477,7 +515,7 @@ def run_ensemble(args):
     from paper_2308_07487_gb300 import asd, synth
     F, T0, n_t = 320, 256, 64
     sizes = synth.ensemble_sizes(96)
-    plans, trajs, Cs, fl = [], [], [], 0.0
+    plans, trajs, Cs, fl, lat_list = [], [], [], 0.0, []
     for k, (d, L) in enumerate(sizes):
         lat = synth.hypercubic(L, d, True, J=1.0)
         w = 1.0 if d == 2 else 0.5
@@ -491,6 +529,7 @@ def run_ensemble(args):
         sysm.ll_integrate(sp, 0.01, F, 1, tr)
         plans.append(asd.CorrPlan.for_lattice(lat, F, T0, n_t, w, nb, precision="split_bf16",
                                               tile_n=256))
+        lat_list.append((lat, w, nb))
         trajs.append(tr)
         Cs.append(torch.zeros((n_t, nb), dtype=torch.float64, device="cuda"))
         fl += 2.0 * lat.n_sites ** 2 * 3 * T0 * n_t
@@ -506,6 +545,19 @@ def run_ensemble(args):
         asd.pair_corr_batched(plans, trajs, Cs, stream=s)
     t_graph = _timed(lambda: g.replay())
     asd.check(asd.sync_status(), "ensemble")
+    # autotuned shared launch knobs (timed on 4 displacements of the whole batch)
+    from paper_2308_07487_gb300 import tune
+    probs = [(pl_lat, pl_w, pl_nb) for pl_lat, pl_w, pl_nb in lat_list]
+    t0 = time.perf_counter()
+    best = tune.Tuner().tune_batch(asd, probs, F, T0, trajs, n_t_sample=4,
+                                   space={"tile_n": [128, 256], "epi_warps": [4, 8],
+                                          "raster_m": [16, 32]})
+    t_tune = time.perf_counter() - t0
+    tplans = [asd.CorrPlan.for_lattice(pl_lat, F, T0, n_t, pl_w, pl_nb, precision="split_bf16",
+                                       **best) for pl_lat, pl_w, pl_nb in lat_list]
+    t_tuned = _timed(lambda: asd.pair_corr_batched(tplans, trajs, Cs))
+    for p in tplans:
+        p.close()
     print(json.dumps({
         "workload": "ensemble96_uneven", "metric": "fused pair-corr TFLOP/s (split-BF16)",
         "unit": "TFLOP/s", "n_samples": len(plans),
@@ -513,7 +565,10 @@ def run_ensemble(args):
         "total_sites": int(sum(p.N for p in plans)),
         "batched_one_launch": fl / t_bat / 1e12, "graph_replay": fl / t_graph / 1e12,
         "separate_launches": fl / t_sep / 1e12,
-        "ms": {"batched": t_bat * 1e3, "graph": t_graph * 1e3, "separate": t_sep * 1e3}}))
+        "batched_autotuned": fl / t_tuned / 1e12, "autotuned_knobs": best,
+        "autotune_s": t_tune,
+        "ms": {"batched": t_bat * 1e3, "graph": t_graph * 1e3, "separate": t_sep * 1e3,
+               "batched_autotuned": t_tuned * 1e3}}))
     for p in plans:
         p.close()
 
@@ -571,16 +626,23 @@ def run_learned(args):
         s2 = sp.clone()
         sysm.thermalize(s2, T, 200, prop, seed=7, **kw)
         es, ms, acc, pr = [], [], 0, 0
+        e_smp, m_smp = [], []
         for k in range(100):
             st = sysm.thermalize(s2, T, 2, prop, seed=7, counter=200 + 2 * k, stats=True, **kw)
             pr += st[0]
             acc += st[1]
             y = s2.double()
-            e = 0.0
+            e = torch.zeros(S, dtype=torch.float64, device="cuda")
             for a in range(lat.nbr.shape[1]):
-                e += (y * y[:, torch.from_numpy(lat.nbr[:, a]).long().cuda()]).sum().item()
-            es.append(e / 2 / (S * N))
-            ms.append(float(y.mean(1).norm(dim=1).mean().item()))
+                e += (y * y[:, torch.from_numpy(lat.nbr[:, a]).long().cuda()]).sum(dim=(1, 2))
+            e = (e / 2 / N).cpu().numpy()              # per sample, energy per site (J = 1)
+            m = y.mean(1).norm(dim=1).cpu().numpy()    # per sample |M| / N
+            e_smp.append(e)
+            m_smp.append(m)
+            es.append(float(e.mean()))
+            ms.append(float(m.mean()))
+        hist_e[prop] = np.concatenate(e_smp)
+        hist_m[prop] = np.concatenate(m_smp)
         es = np.array(es)
         # integrated autocorrelation time of the energy (initial positive sequence)
         x = es - es.mean()
@@ -589,9 +651,35 @@ def run_learned(args):
         return s2, {"acceptance": acc / pr, "energy_per_site": float(es.mean()),
                     "energy_sem": float(es.std() / math.sqrt(len(es))), "tau_int_energy": tau,
                     "magnetisation": float(np.mean(ms))}
+    hist_e, hist_m = {}, {}
     s_learn, st_learn = chain(asd.ASD_LEARNED, {"net": net})
     s_metro, st_metro = chain(asd.ASD_METROPOLIS, {"cone": 0.0})
     _, st_heat = chain(asd.ASD_HEATBATH, {})
+
+    def ks(a, b):
+        """Two-sample Kolmogorov-Smirnov statistic (largest gap between the ECDFs)."""
+        z = np.sort(np.concatenate([a, b]))
+        return float(np.abs(np.searchsorted(np.sort(a), z, "right") / len(a)
+                            - np.searchsorted(np.sort(b), z, "right") / len(b)).max())
+
+    def hist(x, lo, hi):
+        h, _ = np.histogram(x, bins=20, range=(lo, hi))
+        return (h / len(x)).round(4).tolist()
+    elo = min(v.min() for v in hist_e.values())
+    ehi = max(v.max() for v in hist_e.values())
+    mhi = max(v.max() for v in hist_m.values())
+    L_, M_, H_ = asd.ASD_LEARNED, asd.ASD_METROPOLIS, asd.ASD_HEATBATH
+    histograms = {
+        "samples_per_method": int(len(hist_e[L_])),
+        "ks_energy": {"learned_vs_heatbath": ks(hist_e[L_], hist_e[H_]),
+                      "metropolis_vs_heatbath": ks(hist_e[M_], hist_e[H_])},
+        "ks_magnetisation": {"learned_vs_heatbath": ks(hist_m[L_], hist_m[H_]),
+                             "metropolis_vs_heatbath": ks(hist_m[M_], hist_m[H_])},
+        "energy_range": [float(elo), float(ehi)], "magnetisation_range": [0.0, float(mhi)],
+        "energy_hist": {k: hist(hist_e[v], elo, ehi) for k, v in
+                        (("learned", L_), ("metropolis", M_), ("heatbath", H_))},
+        "magnetisation_hist": {k: hist(hist_m[v], 0.0, mhi) for k, v in
+                               (("learned", L_), ("metropolis", M_), ("heatbath", H_))}}
     F, T0, n_t = 576, 512, 64
     res = {}
     for name, starts in (("learned", s_learn), ("metropolis", s_metro)):
@@ -616,6 +704,7 @@ def run_learned(args):
                      "data_s": t_data, "train_s": t_train, "nll_per_site": nll,
                      "nll_uniform": math.log(4 * math.pi)},
         "chains": {"learned": st_learn, "metropolis": st_metro, "heatbath": st_heat},
+        "histograms": histograms,
         "corr_TFLOP/s": {k: v["TFLOP/s"] for k, v in res.items()},
         "corr_ms": {k: v["ms"] for k, v in res.items()},
         "max_abs_C_diff_learned_vs_metropolis_r<40": float(dC)}))

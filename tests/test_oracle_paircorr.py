@@ -191,3 +191,27 @@ def test_position_rule_threshold_cases():
     dx, dy = np.float32(0.3), np.float32(0.4)
     d2 = np.float32(np.float64(dy) * np.float64(dy) + np.float64(np.float32(dx * dx)))
     assert oracle.pair_d2(geo, 0, 3) == float(d2)
+
+
+@pytest.mark.parametrize("periodic,jitter", [(True, 0.0), (False, 0.1)])
+def test_time_reversal_swaps_the_pair_roles(periodic, jitter):
+    """i <-> j symmetry: with F = T0 + n_t - 1 frames, reversing the trajectory in time
+    maps displacement t_max = n_t - 1 onto itself with S_i(t0 + t) . S_j(t0) turned into
+    S_j(u + t) . S_i(u) over the same origins; the bins and the phase weights are
+    symmetric in (i, j) (cos is even), so the binned and phase sums at t_max are unchanged,
+    while the other displacements move to other origin windows."""
+    lat = synth.hypercubic(4, 3, periodic, jitter=jitter, seed=7)
+    geo = oracle.Geometry.of_lattice(lat)
+    T0, n_t = 6, 5
+    F = T0 + n_t - 1
+    tr = synth.traj_precess(lat.n_sites, F, seed=13, S=2)
+    rev = np.ascontiguousarray(tr[:, :, ::-1])
+    q = synth.q_vectors_glass()[::9]
+    a = oracle.pair_corr(tr, T0, [n_t - 1], geo, 0.5, 8, q=q)
+    b = oracle.pair_corr(rev, T0, [n_t - 1], geo, 0.5, 8, q=q)
+    np.testing.assert_allclose(a["C_sum"], b["C_sum"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(a["Sq_sum"], b["Sq_sum"], rtol=1e-12, atol=1e-12)
+    # a planted swap of i and j in one term would break it: t = 1 is not invariant
+    c = oracle.pair_corr(tr, T0, [1], geo, 0.5, 8)
+    d = oracle.pair_corr(rev, T0, [1], geo, 0.5, 8)
+    assert np.abs(c["C_sum"] - d["C_sum"]).max() > 1e-3
