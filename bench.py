@@ -696,6 +696,17 @@ def run_learned(args):
         Cn = torch.zeros_like(C)
         plan.normalize(C, None, Cn, None)
         torch.cuda.synchronize()
+        if name == "learned":
+            # per-bin error against the FP64 oracle on 4 rows x all columns
+            import oracle
+            rows = (5000, 5004)
+            Cr = torch.zeros_like(C)
+            plan.contract(Cr, rows=rows)
+            tr_h = tr.cpu().numpy()
+            ref = oracle.pair_corr(tr_h, T0, [0, n_t - 1], oracle.Geometry.of_lattice(lat),
+                                   1.0, 91, rows=rows)
+            err_rows = float(oracle.bin_error(Cr.cpu().numpy()[[0, n_t - 1]], ref).max())
+            del tr_h
         fl = 2.0 * N * N * 3 * T0 * S * n_t
         res[name] = {"C": Cn.cpu().numpy(), "TFLOP/s": fl / dt / 1e12, "ms": dt * 1e3}
         plan.close()
@@ -709,7 +720,8 @@ def run_learned(args):
         "histograms": histograms,
         "corr_TFLOP/s": {k: v["TFLOP/s"] for k, v in res.items()},
         "corr_ms": {k: v["ms"] for k, v in res.items()},
-        "max_abs_C_diff_learned_vs_metropolis_r<40": float(dC)}))
+        "max_abs_C_diff_learned_vs_metropolis_r<40": float(dC),
+        "corr_max_bin_err_rows_5000_5004": err_rows}))
 
 
 def main():

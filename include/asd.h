@@ -93,9 +93,11 @@ typedef struct asd_corr_desc {
     int32_t tile_n;         /* 0 = chosen by the autotuner, else 128 or 256 (tensor forms) */
     int32_t raster_m;       /* 0 = automatic, else row tiles per raster group (1..64)  */
     int32_t stages;         /* 0 = automatic, else shared-memory pipeline stages (2..8) */
-    int32_t k_chunks;       /* 0 = automatic, else partial accumulators per tile along K
-                               (1..16): each starts from zero, which bounds the tensor-core
-                               FP32 accumulation error; the epilogue adds them exactly   */
+    int32_t k_chunks;       /* 0 = automatic (split-BF16: one per ~1536 K elements;
+                               other forms: 1), else partial accumulators per tile along K
+                               (1..256): each starts from zero, which bounds the
+                               tensor-core FP32 accumulation error; the epilogue bins each
+                               one (FP32 within a tile, FP64 across tiles)               */
     int32_t cluster;        /* 0 = automatic, 1, or 4: CTAs sharing one B tile via TMA
                                multicast                                                 */
     int32_t epi_warps;      /* 0 = automatic, 4 or 8 epilogue warps per CTA            */

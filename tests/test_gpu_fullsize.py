@@ -7,6 +7,10 @@
   oracle with the per-bin metric.
 * 64^3 jittered +-J glass (262144 sites, open, 256 bins, 64 q): row slices of the
   bins and of the phase sums against the loop oracle.
+* 96-sample uneven ensemble (N_s up to 40000, F = 320, T0 = 256, 64 displacements), one
+  batched split-BF16 launch as the bench runs it: every problem against the FFT route.
+* 128^2 lattice with 64 starts concatenated along K (K = 98304, F = 576, T0 = 512,
+  64 displacements): rows against the loop oracle, C(0,0) = 1 on the full launch.
 """
 import numpy as np
 import pytest
@@ -74,4 +78,55 @@ def test_glass_rows_bins_and_phase(asd):
     sq = Sq.cpu().numpy()[t_sel]
     scale = np.abs(r["Sq_sum"]).max()
     assert np.abs(sq - r["Sq_sum"]).max() <= 1e-4 * scale
+    plan.close()
+
+
+def test_ensemble96_batched_vs_fft(asd):
+    F, T0, n_t = 320, 256, 64
+    t_list = [0, 1, 31, 63]
+    probs = []
+    for k, (d, L) in enumerate(synth.ensemble_sizes(96)):
+        lat = synth.hypercubic(L, d, True, J=1.0)
+        w = 1.0 if d == 2 else 0.5
+        nb = int((d * (L // 2) ** 2) ** 0.5 / w) + 1
+        tr = synth.traj_precess(lat.n_sites, F, seed=23084 + k)
+        plan = asd.CorrPlan.for_lattice(lat, F, T0, n_t, w, nb, precision="split_bf16",
+                                        tile_n=256)
+        probs.append((lat, w, nb, tr, plan, torch.from_numpy(tr[:, None].copy()).cuda(),
+                      torch.zeros((n_t, nb), dtype=torch.float64, device="cuda")))
+    asd.pair_corr_batched([p[4] for p in probs], [p[5] for p in probs], [p[6] for p in probs])
+    assert asd.sync_status() == 0
+    worst = 0.0
+    for lat, w, nb, tr, plan, _, C in probs:
+        n = plan.counts().astype(np.float64)
+        ref = checks.lattice_fft_corr(tr, T0, t_list, lat.coords, lat.L, True, w, nb)
+        got = C.cpu().numpy()[t_list]
+        occ = n > 0
+        worst = max(worst, float((np.abs(got[:, occ] - ref[:, occ]) / (T0 * n[occ])).max()))
+        assert np.abs(got[:, ~occ]).max(initial=0.0) == 0.0
+        plan.close()
+    assert worst <= 1e-5, worst
+
+
+def test_learned_config_k98304(asd):
+    L, S, F, T0, n_t = 128, 64, 576, 512, 64
+    lat = synth.hypercubic(L, 2, True, J=1.0)
+    # [N][S][F][3], generated one start at a time (bounded host memory)
+    tr = np.empty((lat.n_sites, S, F, 3), np.float32)
+    for s in range(S):
+        tr[:, s] = synth.traj_precess(lat.n_sites, F, seed=23085 + s)[:, 0]
+    plan = asd.CorrPlan.for_lattice(lat, F, T0, n_t, 1.0, 91, precision="split_bf16", S=S)
+    d_tr = torch.from_numpy(tr).cuda()
+    C = torch.zeros((n_t, 91), dtype=torch.float64, device="cuda")
+    plan.run(d_tr, C)
+    Cr = torch.zeros_like(C)
+    rows = (5000, 5004)
+    plan.run(d_tr, Cr, rows=rows)
+    assert asd.sync_status() == 0
+    r = oracle.pair_corr(tr, T0, [0, 63], oracle.Geometry.of_lattice(lat), 1.0, 91, rows=rows)
+    assert oracle.bin_error(Cr.cpu().numpy()[[0, 63]], r).max() <= 1e-5
+    # the full launch at any size: C(0, 0) = 1 for unit spins (self pairs only in bin 0)
+    n = plan.counts().astype(np.float64)
+    c00 = C.cpu().numpy()[0, 0] / (S * T0 * n[0])
+    assert abs(c00 - 1.0) <= 1e-5, c00
     plan.close()
