@@ -181,6 +181,20 @@ int asd_pair_corr_sq_separable(asd_corr_plan *plan, const float *traj, double *S
                                void *stream);
 
 /*
+ * Dynamical structure factor (Section 4: S(q, omega) from the Fourier transform of S(q,t)
+ * in time).  With S(q, -t) = S(q, t) (the cosine form is symmetric under i <-> j):
+ *   Sqw[k][q] = dt * ( v_0 S[0][q] + 2 sum_{t=1}^{n_t-1} v_t S[t][q] cos(omega[k] t dt) )
+ *   window 0: v_t = 1;  1 (Hann): v_t = (1 + cos(pi t / n_t)) / 2;
+ *          2 (Gaussian): v_t = exp(-(t / (width n_t))^2 / 2).
+ *   S      device [n_t][n_q] FP64 (any normalisation; typically asd_pair_corr_normalize's)
+ *   omega  device [n_w] FP64 angular frequencies, in the inverse unit of dt
+ *   Sqw    device [n_w][n_q] FP64, overwritten
+ * n_t <= 6000, n_w <= 65535.  FP64 throughout.  Enqueue-only.
+ */
+int asd_sq_omega(const double *S, int n_t, int n_q, double dt, int window, double width,
+                 const double *omega, int n_w, double *Sqw, void *stream);
+
+/*
  * Eq. 3 / Eq. 4 normalisation (device buffers, may alias their inputs):
  *   C[t][b]  = C_sum[t][b] / (S*T0*n_b)   (0 where n_b = 0)
  *   Sq[t][q] = Sq_sum[t][q] / (N*S*T0)

@@ -74,6 +74,8 @@ _SIGS = {
     "asd_pair_corr_normalize": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "asd_sync_status": (ctypes.c_int, [_VP]),
     "asd_pair_corr_sq_separable": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "asd_sq_omega": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_double, _VP, ctypes.c_int, _VP, _VP]),
     "asd_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, _VP]),
     "asd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "asd_ll_integrate": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP, ctypes.c_float,
@@ -242,6 +244,17 @@ def pair_corr_batched(plans, trajs, C_sums, Sq_sums=None, stream=None):
     C = (_VP * n)(*[_ptr(c) for c in C_sums])
     Q = (_VP * n)(*[_ptr(q) for q in Sq_sums]) if Sq_sums is not None else None
     check(lib.asd_pair_corr_batched(P, T, n, C, Q, _stream(stream)), "pair_corr_batched")
+
+
+WINDOWS = {"none": 0, "hann": 1, "gauss": 2}
+
+
+def sq_omega(S, dt, omega, Sqw, window="hann", width=0.25, stream=None):
+    """asd_sq_omega: S(q, omega) [n_w][n_q] from S(q, t) [n_t][n_q] (device FP64 tensors)."""
+    n_t, n_q = S.shape
+    check(lib.asd_sq_omega(_ptr(S), int(n_t), int(n_q), float(dt), WINDOWS[window], float(width),
+                           _ptr(omega), int(omega.shape[0]), _ptr(Sqw), _stream(stream)),
+          "sq_omega")
 
 
 def sync_status(stream=None):
