@@ -239,7 +239,13 @@ typedef struct asd_system {
     int32_t n_colors;             /* independent-set colouring for parallel updates   */
     const int32_t *color_sites;   /* device: sites of colour 0, then colour 1, ...    */
     const int64_t *color_offsets; /* host [n_colors+1] offsets into color_sites       */
+    const float *D;               /* device [N][z][3] DM vector of the directed bond
+                                     (i, nbr[i][k]), D_ji = -D_ij; NULL = no DM term  */
+    float A;                      /* single-ion anisotropy: -A sum_i (S^z_i)^2        */
 } asd_system;
+/* H = sum_<ij> J_ij S_i.S_j - sum_<ij> D_ij.(S_i x S_j) - A sum_i (S^z_i)^2
+ *     - Hz sum_i S^z_i  (Eq. 1); the local field is
+ * h_i = dH/dS_i = sum_j J_ij S_j + sum_j D_ij x S_j - 2 A S^z_i z^ - Hz z^. */
 
 /*
  * Landau-Lifshitz dynamics dS_i/dt = (dH/dS_i) x S_i (Eq. 2), classic RK4 without

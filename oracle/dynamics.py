@@ -1,10 +1,13 @@
 """FP64 oracle of the trajectory producers (test infrastructure only).
 
-* ll_rk4           Eq. 2, dS_i/dt = (dH/dS_i) x S_i, with H of Eq. 1 restricted to exchange
-                   and field, integrated by classic RK4 without renormalisation (Section 3.1).
+* ll_rk4           Eq. 2, dS_i/dt = (dH/dS_i) x S_i, with H of Eq. 1 (exchange, DM,
+                   single-ion anisotropy, field), integrated by classic RK4 without
+                   renormalisation (Section 3.1).
 * mc_sweep         Section 2.1: single-spin Metropolis with trial spins uniform on the sphere
                    or in a cone about the current spin, accepted with min(1, e^{-beta dE});
-                   heat-bath: the exact conditional, a von Mises-Fisher law about -h.
+                   heat-bath: the exact conditional of the terms linear in S_i, a von
+                   Mises-Fisher law about -h, with a Metropolis-Hastings correction
+                   min(1, e^{beta A (Sz_new^2 - Sz_old^2)}) for the anisotropy.
                    Checkerboard order: all sites of one colour, then the next.  Random
                    numbers are passed in (4 uniforms per site per sweep).
 * energy, vmf_w    helpers with their closed forms pinned in tests/test_oracle_dynamics.py
@@ -14,23 +17,28 @@ from __future__ import annotations
 import numpy as np
 
 
-def local_field(Y, nbr, J, Hz):
-    """h_i = sum_j J_ij S_j - Hz z^ for Y [S][N][3] (dH/dS_i of Eq. 1, exchange + field)."""
+def local_field(Y, nbr, J, Hz, D=None, A=0.0):
+    """h_i = dH/dS_i of Eq. 1 for Y [S][N][3]:
+    sum_j J_ij S_j + sum_j D_ij x S_j - 2 A S^z_i z^ - Hz z^, where D_ij is the DM vector of
+    the directed bond (i, j) = slot k of site i (D_ji = -D_ij)."""
     Y = np.asarray(Y, np.float64)
     h = np.zeros_like(Y)
     for k in range(nbr.shape[1]):
         j = nbr[:, k]
         ok = j >= 0
         h[:, ok] += J[ok, k][None, :, None] * Y[:, j[ok]]
+        if D is not None:
+            h[:, ok] += np.cross(np.asarray(D, np.float64)[ok, k][None], Y[:, j[ok]])
+    h[..., 2] -= 2.0 * A * Y[..., 2]
     h[..., 2] -= Hz
     return h
 
 
-def ll_rhs(Y, nbr, J, Hz):
-    return np.cross(local_field(Y, nbr, J, Hz), Y)
+def ll_rhs(Y, nbr, J, Hz, D=None, A=0.0):
+    return np.cross(local_field(Y, nbr, J, Hz, D, A), Y)
 
 
-def ll_rk4(spins0, nbr, J, Hz, dt, n_frames, stride=1):
+def ll_rk4(spins0, nbr, J, Hz, dt, n_frames, stride=1, D=None, A=0.0):
     """spins0 [S][N][3] -> trajectory [N][S][F][3] (FP64); frame 0 is spins0."""
     Y = np.array(spins0, np.float64)
     S, N, _ = Y.shape
@@ -38,20 +46,31 @@ def ll_rk4(spins0, nbr, J, Hz, dt, n_frames, stride=1):
     out[:, :, 0] = np.transpose(Y, (1, 0, 2))
     for f in range(1, n_frames):
         for _ in range(stride):
-            k1 = ll_rhs(Y, nbr, J, Hz)
-            k2 = ll_rhs(Y + 0.5 * dt * k1, nbr, J, Hz)
-            k3 = ll_rhs(Y + 0.5 * dt * k2, nbr, J, Hz)
-            k4 = ll_rhs(Y + dt * k3, nbr, J, Hz)
+            k1 = ll_rhs(Y, nbr, J, Hz, D, A)
+            k2 = ll_rhs(Y + 0.5 * dt * k1, nbr, J, Hz, D, A)
+            k3 = ll_rhs(Y + 0.5 * dt * k2, nbr, J, Hz, D, A)
+            k4 = ll_rhs(Y + dt * k3, nbr, J, Hz, D, A)
             Y = Y + (dt / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
         out[:, :, f] = np.transpose(Y, (1, 0, 2))
     return out
 
 
-def energy(Y, nbr, J, Hz):
-    """H of Eq. 1 (exchange + field) per sample; every bond appears in both neighbour lists."""
+def energy(Y, nbr, J, Hz, D=None, A=0.0):
+    """H of Eq. 1 per sample, summed directly over the bonds (not through local_field):
+    every bond appears in both neighbour lists, so each orientation carries half of
+    J S_i.S_j - D_ij.(S_i x S_j) (the two orientations are equal since D_ji = -D_ij);
+    then -A sum (S^z)^2 - Hz sum S^z."""
     Y = np.asarray(Y, np.float64)
-    h_ex = local_field(Y, nbr, J, 0.0)
-    return 0.5 * (h_ex * Y).sum(axis=(1, 2)) - Hz * Y[..., 2].sum(axis=1)
+    E = np.zeros(Y.shape[0])
+    for k in range(nbr.shape[1]):
+        j = nbr[:, k]
+        ok = np.nonzero(j >= 0)[0]
+        Si, Sj = Y[:, ok], Y[:, j[ok]]
+        E += 0.5 * (J[ok, k][None, :] * (Si * Sj).sum(-1)).sum(-1)
+        if D is not None:
+            Dk = np.asarray(D, np.float64)[ok, k][None]
+            E -= 0.5 * (Dk * np.cross(Si, Sj)).sum(axis=(1, 2))
+    return E - A * (Y[..., 2] ** 2).sum(axis=1) - Hz * Y[..., 2].sum(axis=1)
 
 
 def frame_of(m):
@@ -86,27 +105,31 @@ def vmf_w(kappa, u):
     return np.where(small, 1.0 - 2.0 * u, np.maximum(-1.0, w))
 
 
-def mc_sweep(Y, nbr, J, Hz, T, uniforms, colors, proposal="metropolis", cone=0.0):
+def mc_sweep(Y, nbr, J, Hz, T, uniforms, colors, proposal="metropolis", cone=0.0, D=None,
+             A=0.0):
     """One checkerboard sweep.  Y [S][N][3] (updated copy returned), uniforms [S][N][4].
-    Returns (Y_new, accepted_count, proposed_count)."""
+    Returns (Y_new, accepted_count, proposed_count).  The energy change of moving S_i is
+    (S' - S).h_lin - A (S'z^2 - Sz^2), h_lin the field of the terms linear in S_i."""
     Y = np.array(Y, np.float64)
     beta = 1.0 / T
     acc_total = 0
     prop_total = 0
     for sites in colors:
         u = uniforms[:, sites]                       # [S][n][4]
-        h = local_field(Y, nbr, J, Hz)[:, sites]     # neighbours are of other colours
+        # neighbours are of other colours; the anisotropy term is kept apart
+        h = local_field(Y, nbr, J, Hz, D, 0.0)[:, sites]
         old = Y[:, sites]
         if proposal == "heatbath":
             hn = np.linalg.norm(h, axis=-1)
             m = np.where(hn[..., None] > 0, -h / np.where(hn > 0, hn, 1.0)[..., None],
                          np.array([0.0, 0.0, 1.0]))
             new = around(m, vmf_w(beta * hn, u[..., 0]), 2 * np.pi * u[..., 1])
-            accept = np.ones(hn.shape, bool)
+            la = beta * A * (new[..., 2] ** 2 - old[..., 2] ** 2)
+            accept = (la >= 0) | (u[..., 2] < np.exp(np.minimum(la, 0.0)))
         else:
             cmin = -1.0 if (cone <= 0 or cone >= np.pi) else np.cos(cone)
             new = around(old, 1.0 - u[..., 0] * (1.0 - cmin), 2 * np.pi * u[..., 1])
-            dE = ((new - old) * h).sum(-1)
+            dE = ((new - old) * h).sum(-1) - A * (new[..., 2] ** 2 - old[..., 2] ** 2)
             la = -beta * dE
             accept = (la >= 0) | (u[..., 2] < np.exp(np.minimum(la, 0.0)))
         Y[:, sites] = np.where(accept[..., None], new, old)

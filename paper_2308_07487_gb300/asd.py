@@ -46,7 +46,8 @@ class asd_corr_desc(ctypes.Structure):
 class asd_system(ctypes.Structure):
     _fields_ = [("n_sites", ctypes.c_int64), ("z", ctypes.c_int32), ("nbr", ctypes.c_void_p),
                 ("J", ctypes.c_void_p), ("Hz", ctypes.c_float), ("n_colors", ctypes.c_int32),
-                ("color_sites", ctypes.c_void_p), ("color_offsets", c_i64p)]
+                ("color_sites", ctypes.c_void_p), ("color_offsets", c_i64p),
+                ("D", ctypes.c_void_p), ("A", ctypes.c_float)]
 
 
 class asd_mlp(ctypes.Structure):
@@ -339,6 +340,12 @@ class System:
         s.n_colors = len(lat.colors)
         s.color_sites = self.color_sites.data_ptr()
         s.color_offsets = self.offsets.ctypes.data_as(c_i64p)
+        # Eq. 1's DM vectors per directed bond and single-ion anisotropy (optional)
+        D = getattr(lat, "D", None)
+        self.D = None if D is None else torch.from_numpy(
+            np.ascontiguousarray(D, np.float32)).to(device)
+        s.D = self.D.data_ptr() if self.D is not None else None
+        s.A = float(getattr(lat, "A", 0.0))
         self.c = s
 
     def gather(self, spins, x, y, stream=None):

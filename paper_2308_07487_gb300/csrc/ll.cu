@@ -1,7 +1,9 @@
 // Landau-Lifshitz dynamics (Eq. 2): dS_i/dt = (dH/dS_i) x S_i, classic RK4.
 //
-// H = sum_<ij> J_ij S_i.S_j - Hz sum_i S^z_i (Eq. 1 without DM / anisotropy), so the
-// local field is h_i = sum_j J_ij S_j - Hz z^.  As in Algorithm 1, one thread handles
+// H of Eq. 1 (exchange, DM, single-ion anisotropy, field), so the local field is
+// h_i = sum_j J_ij S_j + sum_j D_ij x S_j - 2 A S^z_i z^ - Hz z^ (D_ij the DM vector of the
+// directed bond, D_ji = -D_ij: Algorithm 1's exchange, DMI, anisotropy and field
+// contributions).  As in Algorithm 1, one thread handles
 // one site and the S samples are processed by the same launch (the paper passes its
 // M configurations to one kernel, Section 3.1); the RK4 stages keep their derivative
 // in separate arrays so sites never race (Section 3.1).  No renormalisation: the paper
@@ -22,6 +24,8 @@ struct LLArgs {
     const int *nbr;
     const float *J;
     float Hz;
+    const float *D;  // [N][z][3] or null
+    float A;
 };
 
 __device__ __forceinline__ float3 field(const LLArgs &a, const float *__restrict__ Y, int s,
@@ -36,7 +40,17 @@ __device__ __forceinline__ float3 field(const LLArgs &a, const float *__restrict
         h.x = fmaf(Jij, Ys[3 * (int64_t)j + 0], h.x);
         h.y = fmaf(Jij, Ys[3 * (int64_t)j + 1], h.y);
         h.z = fmaf(Jij, Ys[3 * (int64_t)j + 2], h.z);
+        if (a.D) {  // D_ij x S_j
+            const float *d = a.D + (i * a.z + k) * 3;
+            const float dx = __ldg(d), dy = __ldg(d + 1), dz = __ldg(d + 2);
+            const float sx = Ys[3 * (int64_t)j], sy = Ys[3 * (int64_t)j + 1],
+                        sz = Ys[3 * (int64_t)j + 2];
+            h.x += dy * sz - dz * sy;
+            h.y += dz * sx - dx * sz;
+            h.z += dx * sy - dy * sx;
+        }
     }
+    h.z = fmaf(-2.f * a.A, Ys[3 * i + 2], h.z);
     return h;
 }
 
@@ -108,7 +122,7 @@ extern "C" int asd_ll_integrate(const asd_system *sys, int n_samples, const floa
     ASD_CHECK_ARG(sys->z == 0 || (sys->nbr && sys->J), "neighbour table required");
     ASD_CHECK_ARG(n_samples >= 1 && n_frames >= 1 && stride >= 1, "bad n_samples/n_frames/stride");
     cudaStream_t s = (cudaStream_t)stream;
-    LLArgs a{sys->n_sites, n_samples, sys->z, sys->nbr, sys->J, sys->Hz};
+    LLArgs a{sys->n_sites, n_samples, sys->z, sys->nbr, sys->J, sys->Hz, sys->D, sys->A};
     const int64_t n = sys->n_sites * n_samples;
     const size_t bytes = sizeof(float) * 3 * (size_t)n;
     float *ws = nullptr;
@@ -203,7 +217,7 @@ extern "C" int asd_ll_integrate_noalloc(const asd_system *sys, int n_samples, co
     int rc = ll_scratch_address(&ws);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    LLArgs a{sys->n_sites, n_samples, sys->z, sys->nbr, sys->J, sys->Hz};
+    LLArgs a{sys->n_sites, n_samples, sys->z, sys->nbr, sys->J, sys->Hz, sys->D, sys->A};
     const int64_t n = sys->n_sites * n_samples;
     const size_t bytes = sizeof(float) * 3 * (size_t)n;
     // every buffer is written before it is read: Y by the copy, acc by stage 1, T1 / T2

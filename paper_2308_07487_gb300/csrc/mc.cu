@@ -3,8 +3,12 @@
 // Metropolis: a trial spin is drawn uniformly on the sphere, or inside a cone about the
 // current spin whose half-angle adapts between sweeps (the paper keeps the acceptance
 // rate at least 20 %); it is accepted with probability min(1, exp(-beta dE)).
-// Heat-bath: the new spin is drawn from the exact conditional p(S) ~ exp(-beta S.h),
-// a von Mises-Fisher law with mean -h/|h| and concentration beta|h|.
+// Heat-bath: the new spin is drawn from the exact conditional of the terms linear in S,
+// p(S) ~ exp(-beta S.h), a von Mises-Fisher law with mean -h/|h| and concentration
+// beta|h|; with single-ion anisotropy the draw is a Metropolis-Hastings proposal accepted
+// with min(1, exp(beta A (Sz_new^2 - Sz_old^2))), which keeps the chain exact.
+// Energy change of a move: dE = (S' - S).h - A (S'z^2 - Sz^2), h = sum_j J_ij S_j +
+// sum_j D_ij x S_j - Hz z^ (Eq. 1).
 // Learned: a small MLP maps the neighbour spins to a vMF proposal; the
 // Metropolis-Hastings ratio exp(-beta dE) q(S_old)/q(S_new) keeps the chain exact.
 //
@@ -47,6 +51,8 @@ struct MCArgs {
     const int *nbr;
     const float *J;
     float Hz;
+    const float *D;     // [N][z][3] DM vectors or null
+    float A;            // single-ion anisotropy
     float beta;
     int proposal;
     const int *sites;   // this colour's sites
@@ -110,6 +116,12 @@ __global__ void mc_color_kernel(MCArgs a, float *__restrict__ spins)
             h.x = fmaf(Jij, sj.x, h.x);
             h.y = fmaf(Jij, sj.y, h.y);
             h.z = fmaf(Jij, sj.z, h.z);
+            if (a.D && j >= 0) {  // D_ij x S_j
+                const float *d = a.D + (i * a.z + k) * 3;
+                h.x += d[1] * sj.z - d[2] * sj.y;
+                h.y += d[2] * sj.x - d[0] * sj.z;
+                h.z += d[0] * sj.y - d[1] * sj.x;
+            }
             if (a.proposal == ASD_LEARNED && k < 32) {
                 nb[3 * k] = sj.x;
                 nb[3 * k + 1] = sj.y;
@@ -149,10 +161,13 @@ __global__ void mc_color_kernel(MCArgs a, float *__restrict__ spins)
             nw = around(old, 1.f - u[0] * (1.f - cmin), TWO_PI * u[1]);
         }
         prop = true;
+        const float daniso = a.A * (nw.z * nw.z - old.z * old.z);  // -(anisotropy change)
         if (a.proposal == ASD_HEATBATH) {
-            acc = true;
+            const float la = a.beta * daniso;
+            acc = la >= 0.f || u[2] < expf(la);
         } else {
-            const float dE = (nw.x - old.x) * h.x + (nw.y - old.y) * h.y + (nw.z - old.z) * h.z;
+            const float dE = (nw.x - old.x) * h.x + (nw.y - old.y) * h.y +
+                             (nw.z - old.z) * h.z - daniso;
             const float la = -a.beta * dE + logq_ratio;
             acc = la >= 0.f || u[2] < expf(la);
         }
@@ -237,6 +252,8 @@ extern "C" int asd_thermalize(const asd_system *sys, int n_samples, float *spins
         a.nbr = sys->nbr;
         a.J = sys->J;
         a.Hz = sys->Hz;
+        a.D = sys->D;
+        a.A = sys->A;
         a.beta = 1.f / T;
         a.proposal = proposal;
         a.seed = seed;

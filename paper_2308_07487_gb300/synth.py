@@ -34,6 +34,7 @@ class Lattice:
     J       f32   [N,z]  coupling per slot (0 where absent); J_ij == J_ji
     pos     f32   [N,3]  Cartesian positions (coords, or jittered coords)
     colors  list of int32 arrays: sites of each checkerboard colour
+    D, A    optional DM vectors per directed bond and single-ion anisotropy (Eq. 1 terms)
     """
     dim: int
     L: tuple
@@ -44,6 +45,8 @@ class Lattice:
     pos: np.ndarray
     colors: list = field(default_factory=list)
     Hz: float = 0.0
+    D: np.ndarray | None = None   # f32 [N,z,3] DM vector per directed bond (D_ji = -D_ij)
+    A: float = 0.0                # single-ion anisotropy
 
     @property
     def n_sites(self) -> int:
@@ -250,3 +253,21 @@ def ensemble_sizes(n: int = 96, seed: int = SEED_BASE * 10 + 4, lo: int = 1024, 
         L = max(2, int(round(Ns ** (1.0 / d))))
         out.append((d, L))
     return out
+
+
+def with_dm_anisotropy(lat: Lattice, D: float = 0.0, A: float = 0.0) -> Lattice:
+    """A copy of `lat` with bulk-type DM vectors D_ij = D * (unit bond vector from i to j,
+    minimum image when periodic; antisymmetric by construction) and anisotropy A."""
+    import dataclasses
+    N, z = lat.nbr.shape
+    Dv = np.zeros((N, z, 3), np.float32)
+    Ls = np.array(lat.L, np.float64)
+    for k in range(z):
+        j = lat.nbr[:, k]
+        ok = j >= 0
+        d = lat.coords[j[ok]].astype(np.float64) - lat.coords[ok].astype(np.float64)
+        if lat.periodic:
+            d -= Ls * np.round(d / Ls)
+        n = np.linalg.norm(d, axis=1, keepdims=True)
+        Dv[ok, k] = (D * d / np.where(n > 0, n, 1.0)).astype(np.float32)
+    return dataclasses.replace(lat, D=Dv, A=float(A))

@@ -108,3 +108,36 @@ def test_adaptive_cone_keeps_acceptance(asd):
     prop, acc, cone = sysm.thermalize(sp, 0.05, 50, asd.ASD_METROPOLIS, cone=0.3, adapt=True,
                                       seed=11, counter=200, stats=True)
     assert acc / prop >= 0.2 and 0 < cone < 1.0
+
+
+def test_ll_with_dm_and_anisotropy_matches_fp64_rk4(asd):
+    """All terms of Eq. 1 (exchange, bulk DM, single-ion anisotropy, field)."""
+    lat = synth.with_dm_anisotropy(synth.hypercubic(8, 3, True, J=-1.0, Hz=0.3), D=0.4, A=0.7)
+    S, F, stride = 2, 31, 2
+    s0 = synth.random_unit(S * lat.n_sites, 13).reshape(S, lat.n_sites, 3)
+    ref = dyn.ll_rk4(s0.astype(np.float64), lat.nbr, lat.J, lat.Hz, 0.01, F, stride,
+                     D=lat.D, A=lat.A)
+    traj = torch.zeros((lat.n_sites, S, F, 3), dtype=torch.float32, device="cuda")
+    asd.System(lat).ll_integrate(torch.from_numpy(s0).cuda(), 0.01, F, stride, traj)
+    assert asd.sync_status() == 0
+    assert np.abs(traj.cpu().numpy() - ref).max() < 2e-5
+
+
+@pytest.mark.parametrize("proposal", ["metropolis", "heatbath"])
+def test_mc_with_dm_and_anisotropy_matches_oracle(asd, proposal):
+    lat = synth.with_dm_anisotropy(synth.hypercubic(10, 2, True, J=1.0, Hz=0.2), D=0.5, A=0.8)
+    S, sweeps, T = 2, 3, 0.7
+    g = np.random.default_rng(6)
+    u = g.random((sweeps, S, lat.n_sites, 4)).astype(np.float32)
+    u[..., :2] = 1.0 - u[..., :2]
+    s0 = synth.random_unit(S * lat.n_sites, 10).reshape(S, lat.n_sites, 3)
+    Y = s0.astype(np.float64)
+    for k in range(sweeps):
+        Y, _, _ = dyn.mc_sweep(Y, lat.nbr, lat.J, lat.Hz, T, u[k].astype(np.float64), lat.colors,
+                               proposal, D=lat.D, A=lat.A)
+    sp = torch.from_numpy(s0.copy()).cuda()
+    pid = asd.ASD_HEATBATH if proposal == "heatbath" else asd.ASD_METROPOLIS
+    asd.System(lat).thermalize(sp, T, sweeps, pid, uniforms=torch.from_numpy(u).cuda())
+    assert asd.sync_status() == 0
+    d = np.abs(sp.cpu().numpy() - Y).max(-1)
+    assert (d > 1e-4).mean() == 0.0, f"{(d > 1e-4).sum()} sites differ"

@@ -112,3 +112,85 @@ def test_frame_is_orthonormal_right_handed():
     e1, e2 = dyn.frame_of(m)
     np.testing.assert_allclose(np.cross(e1, e2), m, atol=1e-12)
     np.testing.assert_allclose((e1 * m).sum(-1), 0, atol=1e-12)
+
+
+# ---- the DM and single-ion anisotropy terms of Eq. 1 ----
+
+def _dm_z_lattice(L=6, D=0.7, A=0.4, Hz=0.2, J=-1.0):
+    """Square lattice with DM vectors along z, D_ij = D (d_ij . x^) z^ (antisymmetric), so
+    H stays invariant under rotations about z."""
+    lat = synth.hypercubic(L, 2, True, J=J, Hz=Hz)
+    lat = synth.with_dm_anisotropy(lat, D=1.0, A=A)
+    Dz = np.zeros_like(lat.D)
+    Dz[..., 2] = D * lat.D[..., 0]
+    return lat, Dz
+
+
+def test_field_is_the_gradient_of_eq1():
+    """local_field (written from the derivative) equals the finite-difference gradient of
+    energy (written from Eq. 1 bond by bond), with exchange, DM, anisotropy and field."""
+    lat = synth.with_dm_anisotropy(synth.hypercubic(4, 3, True, J=0.7, Hz=0.3), D=0.45, A=0.6)
+    g = np.random.default_rng(3)
+    Y = g.standard_normal((1, lat.n_sites, 3))
+    h = dyn.local_field(Y, lat.nbr, lat.J, lat.Hz, lat.D, lat.A)
+    eps = 1e-6
+    for i in (0, 5, 17, 63):
+        for a in range(3):
+            Yp, Ym = Y.copy(), Y.copy()
+            Yp[0, i, a] += eps
+            Ym[0, i, a] -= eps
+            fd = (dyn.energy(Yp, lat.nbr, lat.J, lat.Hz, lat.D, lat.A) -
+                  dyn.energy(Ym, lat.nbr, lat.J, lat.Hz, lat.D, lat.A))[0] / (2 * eps)
+            assert abs(fd - h[0, i, a]) < 1e-6, (i, a, fd, h[0, i, a])
+
+
+def test_anisotropy_precession_closed_form():
+    """A single spin under -A (S^z)^2 only: h = -2 A S^z z^, so S^z is constant and the
+    azimuth turns at -2 A S^z."""
+    lat = synth.open_chain(1, J=0.0)
+    A, dt, F = 1.3, 0.001, 401
+    s0 = np.array([[[0.6, 0.0, 0.8]]])
+    tr = dyn.ll_rk4(s0, lat.nbr, lat.J, 0.0, dt, F, A=A)[0, 0]
+    t = dt * np.arange(F)
+    phi = -2.0 * A * 0.8 * t
+    ref = np.stack([0.6 * np.cos(phi), 0.6 * np.sin(phi), np.full(F, 0.8)], 1)
+    assert np.abs(tr - ref).max() < 1e-9
+
+
+def test_dm_along_z_conserves_total_sz_and_energy():
+    lat, Dz = _dm_z_lattice()
+    s0 = synth.random_unit(lat.n_sites, 8).reshape(1, lat.n_sites, 3).astype(np.float64)
+    tr = dyn.ll_rk4(s0, lat.nbr, lat.J, lat.Hz, 0.005, 201, D=Dz, A=lat.A)
+    Sz = tr[:, 0, :, 2].sum(0)
+    assert np.abs(Sz - Sz[0]).max() < 1e-9
+    E0 = dyn.energy(s0, lat.nbr, lat.J, lat.Hz, Dz, lat.A)[0]
+    E1 = dyn.energy(np.transpose(tr[:, :, -1], (1, 0, 2)), lat.nbr, lat.J, lat.Hz, Dz, lat.A)[0]
+    assert abs(E1 - E0) < 1e-8 * lat.n_sites
+
+
+def _single_spin_anisotropy_chain(proposal, A=1.5, T=0.5, S=4000, sweeps=160):
+    lat = synth.open_chain(1, J=0.0)
+    g = np.random.default_rng(21)
+    Y = synth.random_unit(S, 2).reshape(S, 1, 3).astype(np.float64)
+    zz = []
+    for k in range(sweeps):
+        u = g.random((S, 1, 4))
+        u[..., :2] = 1.0 - u[..., :2]
+        Y, _, _ = dyn.mc_sweep(Y, lat.nbr, lat.J, 0.0, T, u, lat.colors, proposal, A=A)
+        if k >= 40:
+            zz.append(Y[:, 0, 2] ** 2)
+    per_chain = np.mean(zz, axis=0)
+    x = np.linspace(-1.0, 1.0, 20001)
+    w = np.exp(A / T * x * x)
+    exact = np.trapezoid(x * x * w, x) / np.trapezoid(w, x)
+    return per_chain.mean(), per_chain.std() / np.sqrt(S), exact
+
+
+def test_metropolis_samples_the_anisotropy():
+    m, se, exact = _single_spin_anisotropy_chain("metropolis")
+    assert abs(m - exact) < 5 * se + 1e-3, (m, se, exact)
+
+
+def test_heatbath_with_correction_samples_the_anisotropy():
+    m, se, exact = _single_spin_anisotropy_chain("heatbath")
+    assert abs(m - exact) < 5 * se + 1e-3, (m, se, exact)
