@@ -101,7 +101,11 @@ typedef struct asd_corr_desc {
     int32_t cluster;        /* 0 = automatic, 1, or 4: CTAs sharing one B tile via TMA
                                multicast                                                 */
     int32_t epi_warps;      /* 0 = automatic, 4 or 8 epilogue warps per CTA            */
-    int32_t reserved[2];    /* must be zero                                            */
+    int32_t phase_sine;     /* 0: Sq_sum[t][q] holds the cosine part of Eq. 3's phase sum;
+                               1: Sq_sum[t][q][2] holds (cosine, sine) parts, the sine
+                               part sum_ij sin(q.(r_i - r_j)) G_ij(t) (Eq. 3's imaginary
+                               part is its negative)                                     */
+    int32_t reserved[1];    /* must be zero                                            */
 } asd_corr_desc;
 
 typedef struct asd_corr_plan asd_corr_plan;

@@ -53,7 +53,7 @@ def _load():
             lib.oracle_pair_corr.argtypes = [i64, i64, i64, i64, i64, i32p, f32p, ctypes.c_int,
                                              i32p, i32p, ctypes.c_int, f32p, ctypes.c_double, i64,
                                              i64, f64p, ctypes.c_int, i64, i64, f64p, f64p, f64p,
-                                             f64p, i64p]
+                                             f64p, f64p, i64p]
             lib.oracle_pair_corr_eq4.restype = ctypes.c_int
             lib.oracle_pair_corr_eq4.argtypes = [i64, i64, i64, i64, i64, i32p, f32p, ctypes.c_int,
                                                  i32p, i32p, ctypes.c_int, f32p, ctypes.c_double,
@@ -106,8 +106,8 @@ def pair_corr(traj, T0, t_list, geometry: Geometry, w, n_bins, q=None, center=Fa
     """Binned sums and phase sums of Eqs. 3-6 (see paircorr_ref.c).
 
     traj [N][S][F][3] (or [N][F][3]) FP32.  Returns dict with C_sum, M_abs
-    [n_t][n_bins], Sq_sum [n_t][n_q], counts [n_bins] (int64), all over the rows
-    `rows=(i0,i1)` (default all) and every column."""
+    [n_t][n_bins], Sq_sum (cosine part) and Sq_im (sine part) [n_t][n_q], counts
+    [n_bins] (int64), all over the rows `rows=(i0,i1)` (default all) and every column."""
     lib = _load()
     tr = np.asarray(traj, np.float32)
     if tr.ndim == 3:
@@ -123,6 +123,7 @@ def pair_corr(traj, T0, t_list, geometry: Geometry, w, n_bins, q=None, center=Fa
     M = np.zeros((n_tl, n_bins))
     P = np.zeros((n_tl, n_bins))
     Sq = np.zeros((n_tl, max(n_q, 1)))
+    Sqi = np.zeros((n_tl, max(n_q, 1)))
     cnt = np.zeros(n_bins, np.int64)
     g = geometry
     rc = lib.oracle_pair_corr(N, F, S, T0, n_tl, _p(tl, ctypes.c_int32), _p(tr, ctypes.c_float),
@@ -131,10 +132,12 @@ def pair_corr(traj, T0, t_list, geometry: Geometry, w, n_bins, q=None, center=Fa
                               _p(qq, ctypes.c_double), int(bool(center)), i0, i1,
                               _p(C, ctypes.c_double), _p(M, ctypes.c_double),
                               _p(P, ctypes.c_double), _p(Sq, ctypes.c_double),
+                              _p(Sqi, ctypes.c_double),
                               _p(cnt, ctypes.c_int64))
     if rc != 0:
         raise ValueError(f"oracle_pair_corr rejected its arguments (code {rc})")
-    return {"C_sum": C, "M_abs": M, "P_abs": P, "Sq_sum": Sq[:, :n_q], "counts": cnt,
+    return {"C_sum": C, "M_abs": M, "P_abs": P, "Sq_sum": Sq[:, :n_q], "Sq_im": Sqi[:, :n_q],
+            "counts": cnt,
             "N": N, "S": S, "T0": T0}
 
 

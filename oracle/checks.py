@@ -76,8 +76,9 @@ def lattice_fft_corr(traj, T0, t_list, coords, L, periodic, w, n_bins):
     return out
 
 
-def separable_phase_sum(traj, T0, t_list, pos, q, center=False):
-    """Sq_sum[t][q] = sum_ij cos(q.(r_i-r_j)) G_ij(t) through the factorised transform.
+def separable_phase_sum(traj, T0, t_list, pos, q, center=False, part="cos"):
+    """Sq_sum[t][q] = sum_ij cos(q.(r_i-r_j)) G_ij(t) through the factorised transform
+    (part="sin": sum_ij sin(q.(r_i-r_j)) G_ij(t) = sum F^s_A F^c_B - F^c_A F^s_B).
 
     F^c = C^T X and F^s = S^T X with C[i][q] = cos(q.r_i), S[i][q] = sin(q.r_i) and X the
     trajectory flattened to [N][S*F*3] (FP64 matrix products), then per t the sum over
@@ -104,7 +105,10 @@ def separable_phase_sum(traj, T0, t_list, pos, q, center=False):
         return w
     Bc, Bs = window(Fc, 0), window(Fs, 0)
     for k, t in enumerate(t_list):
-        out[k] = (window(Fc, t) * Bc).sum(axis=(1, 2, 3)) + (window(Fs, t) * Bs).sum(axis=(1, 2, 3))
+        if part == "sin":
+            out[k] = (window(Fs, t) * Bc).sum(axis=(1, 2, 3)) - (window(Fc, t) * Bs).sum(axis=(1, 2, 3))
+        else:
+            out[k] = (window(Fc, t) * Bc).sum(axis=(1, 2, 3)) + (window(Fs, t) * Bs).sum(axis=(1, 2, 3))
     return out
 
 

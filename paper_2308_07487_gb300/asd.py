@@ -40,7 +40,8 @@ class asd_corr_desc(ctypes.Structure):
                 ("n_q", ctypes.c_int32), ("q", c_f64p), ("tile_n", ctypes.c_int32),
                 ("raster_m", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("k_chunks", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("epi_warps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("epi_warps", ctypes.c_int32), ("phase_sine", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class asd_system(ctypes.Structure):
@@ -142,7 +143,8 @@ class CorrPlan:
 
     def __init__(self, N, F, T0, n_t, precision="split_bf16", S=1, center=False, coords=None,
                  L=(1, 1, 1), periodic=False, pos=None, bin_width=1.0, n_bins=0, q=None,
-                 tile_n=0, raster_m=0, stages=0, k_chunks=0, cluster=0, epi_warps=0):
+                 tile_n=0, raster_m=0, stages=0, k_chunks=0, cluster=0, epi_warps=0,
+                 phase_sine=False):
         d = asd_corr_desc()
         d.n_sites, d.n_frames, d.n_samples, d.T0, d.n_t = N, F, S, T0, n_t
         d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -174,6 +176,8 @@ class CorrPlan:
         d.k_chunks = int(k_chunks)
         d.cluster = int(cluster)
         d.epi_warps = int(epi_warps)
+        d.phase_sine = int(bool(phase_sine))
+        self.q_parts = 1 + d.phase_sine  # Sq_sum is [n_t][n_q] or [n_t][n_q][2]
         self.desc = d
         self.N, self.F, self.S, self.T0, self.n_t = N, F, S, T0, n_t
         self.n_bins, self.n_q = int(n_bins), int(d.n_q)

@@ -77,6 +77,7 @@ struct EpiParams {
                             // packed-coordinate d2, table entries are private-bin offsets
     uint32_t Lpk;           // fast: per-byte minimum-image modulus (x | y<<8 | z<<16)
     int nq_pad;             // row length of cs (n_q rounded up to the q-chunk, zero padded)
+    int q_parts;            // 1: cosine part of the phase sum; 2: cosine and sine parts
     const float2 *cs;       // [N][nq_pad] (cos, sin)(q.r_i)
     double *C_sum;          // [n_t][n_bins]
     double *Sq_sum;         // [n_t][n_q]
@@ -163,6 +164,7 @@ struct asd_corr_plan {
     int n_lut;
     float2 *cs;
     double *sqF;               // separable phase form: transforms [2 n_q][S*3F] (n_q > 0)
+    int q_parts;               // 1 + desc.phase_sine: values per (t, q) in Sq_sum
     int tiles_m_all, tiles_n;
     int use_window;
     int NW;

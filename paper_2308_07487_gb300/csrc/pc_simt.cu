@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
 {
     __shared__ __align__(16) float As[2][TK][TM];
     __shared__ __align__(16) float Bs[2][TK][TN];
-    extern __shared__ double red[];  // [n_bins] then [n_q]
+    extern __shared__ double red[];  // [n_bins] then [n_q][q_parts]
     double *sbins = red;
     double *sq = red + P.e.n_bins;
 
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
     const int t = blockIdx.z;
     const int m0 = P.row_begin + blockIdx.x * TM;
     const int n0 = blockIdx.y * TN;
-    for (int k = tid; k < P.e.n_bins + P.e.n_q; k += 256) red[k] = 0.0;
+    for (int k = tid; k < P.e.n_bins + P.e.n_q * P.e.q_parts; k += 256) red[k] = 0.0;
 
     // loader mapping: one row (or column) and 4 consecutive k per thread
     const int lr = tid >> 1, lk = (tid & 1) * 4;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
     if (e.n_q > 0) {
         const int lane = tid & 31;
         for (int q = 0; q < e.n_q; ++q) {
-            float part = 0.f;
+            float part = 0.f, part_s = 0.f;
             float2 wc[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c)
@@ -150,18 +150,24 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
                     u = fmaf(wc[c].x, acc[r][c], u);
                     v = fmaf(wc[c].y, acc[r][c], v);
                 }
-                part = fmaf(wr.x, u, fmaf(wr.y, v, part));
+                part = fmaf(wr.x, u, fmaf(wr.y, v, part));        // cos(a - b)
+                part_s = fmaf(wr.y, u, fmaf(-wr.x, v, part_s));   // sin(a - b)
             }
             double dp = part;
             for (int o = 16; o > 0; o >>= 1) dp += __shfl_xor_sync(0xffffffffu, dp, o);
-            if (lane == 0) atomicAdd(&sq[q], dp);
+            if (lane == 0) atomicAdd(&sq[q * e.q_parts], dp);
+            if (e.q_parts == 2) {
+                double ds = part_s;
+                for (int o = 16; o > 0; o >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, o);
+                if (lane == 0) atomicAdd(&sq[2 * q + 1], ds);
+            }
         }
     }
     __syncthreads();
     for (int b = tid; b < e.n_bins; b += 256)
         if (sbins[b] != 0.0) atomicAdd(&e.C_sum[(int64_t)t * e.n_bins + b], sbins[b]);
-    for (int q = tid; q < e.n_q; q += 256)
-        if (sq[q] != 0.0) atomicAdd(&e.Sq_sum[(int64_t)t * e.n_q + q], sq[q]);
+    for (int o = tid; o < e.n_q * e.q_parts; o += 256)
+        if (sq[o] != 0.0) atomicAdd(&e.Sq_sum[(int64_t)t * e.n_q * e.q_parts + o], sq[o]);
 }
 
 }  // namespace
@@ -193,6 +199,7 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
     e.pos = p->pos;
     e.thr = p->thr;
     e.nq_pad = (p->n_q + kQChunk - 1) / kQChunk * kQChunk;
+    e.q_parts = p->q_parts;
     e.cs = p->cs;
     e.C_sum = C_sum;
     e.Sq_sum = Sq_sum;
@@ -202,7 +209,7 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
         set_error_text("FP32 form: grid too large (N or n_t)");
         return ASD_EUNSUPPORTED;
     }
-    size_t smem = sizeof(double) * (p->n_bins + p->n_q);
+    size_t smem = sizeof(double) * (p->n_bins + p->n_q * p->q_parts);
     simt_kernel<<<grid, 256, smem, s>>>(P);
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;

@@ -369,9 +369,10 @@ __host__ __device__ inline EpiLayout epi_layout(uint32_t vb, int nb, int nq, int
     EpiLayout L;
     uint32_t o = 0;
     L.cacc = take(o, 8u * (nb > 0 ? nb : 1));
-    L.qacc = take(o, 8u * (nq > 0 ? nq : 1));
+    // phase sums per q: (cosine, sine) parts
+    L.qacc = take(o, 8u * 2 * (nq > 0 ? nq : 1));
     // one slot per (pass, warp, q): the passes of a tile are reduced once at its end
-    L.qred = take(o, 8u * ew * (nq > 0 ? (nq + kQP - 1) / kQP * kQP : kQP));
+    L.qred = take(o, 8u * 2 * ew * (nq > 0 ? (nq + kQP - 1) / kQP * kQP : kQP));
     L.fb = take(o, 4u * (nb > 0 ? nb : 1));
     L.colgeo = take(o, 16u * BN);
     L.colpk = take(o, 4u * BN);
@@ -487,7 +488,7 @@ enum { BIN_LUT = 0, BIN_THR = 1, BIN_POS = 2 };
 // MODE: BIN_LUT (lattice, d2 -> bin table), BIN_THR (lattice, thresholds), BIN_POS
 // (FP32 positions, thresholds).
 template <int MODE, int STRIDE>
-__device__ __forceinline__ void bin_chunk(const uint32_t (&g)[32], float scale, int4 ri, float4 rp,
+__device__ __forceinline__ void bin_chunk(const uint32_t (&g)[32], bool row_ok, int4 ri, float4 rp,
                                           const float4 *__restrict__ cgeo,
                                           const float *__restrict__ thr,
                                           float *__restrict__ myb, float *__restrict__ fb,
@@ -516,7 +517,9 @@ __device__ __forceinline__ void bin_chunk(const uint32_t (&g)[32], float scale, 
     }
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        const float val = scale * __uint_as_float(g[k]);
+        // rows past the range: their accumulator rows may come from A rows that were
+        // never prepared, so the value is replaced (a product with 0 would keep a NaN)
+        const float val = row_ok ? __uint_as_float(g[k]) : 0.f;
         if (slot[k] < 0) atomicAdd(&fb[-1 - slot[k]], val);
         else myb[slot[k] * STRIDE] += val;
     }
@@ -747,7 +750,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             fb[k] = 0.f;
             cacc[k] = 0.0;
         }
-        for (int k = et; k < args.NQ; k += kEpiThreads) qacc[k] = 0.0;
+        for (int k = et; k < 2 * args.NQ; k += kEpiThreads) qacc[k] = 0.0;
 
         int cur_p = -1, cur_t = -1, tab_p = -1;
         WorkCursor cu;
@@ -792,10 +795,13 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 if (cacc[b] != 0.0) atomicAdd(&Cs[(int64_t)t * E.n_bins + b], cacc[b]);
                 cacc[b] = 0.0;
             }
-            for (int q = et; q < E.n_q; q += kEpiThreads) {
-                if (qacc[q] != 0.0) atomicAdd(&Qs[(int64_t)t * E.n_q + q], qacc[q]);
-                qacc[q] = 0.0;
-            }
+            for (int q = et; q < E.n_q; q += kEpiThreads)
+                for (int part = 0; part < E.q_parts; ++part) {
+                    double &acc = qacc[2 * q + part];
+                    if (acc != 0.0)
+                        atomicAdd(&Qs[((int64_t)t * E.n_q + q) * E.q_parts + part], acc);
+                    acc = 0.0;
+                }
         };
         for (int64_t tau = cid; tau < args.total_tiles; tau += n_clusters, ++v) {
             const TileInfo ti = decode<CL>(cu, probs, args.n_probs, args.ov, tau, BN, rank);
@@ -926,7 +932,6 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 ba.blo = E.use_window ? blo : 0;
                 ba.nwp = E.use_window ? E.NW : E.n_bins;
                 ba.trash = E.NW;
-                const float scale = row_ok ? 1.f : 0.f;
                 const int mode = !lattice ? BIN_POS : (E.n_lut > 0 ? BIN_LUT : BIN_THR);
                 if (fast_ok(E)) {
                     // rows past the range skip the pairs (the TMEM loads stay warp-wide)
@@ -959,11 +964,11 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     const float4 *cg = colgeo + ch * 32;
                     float *mb = bins + r + kBM * half;
                     if (mode == BIN_LUT)
-                        bin_chunk<BIN_LUT, kBinStride>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
+                        bin_chunk<BIN_LUT, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fb, ba);
                     else if (mode == BIN_THR)
-                        bin_chunk<BIN_THR, kBinStride>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
+                        bin_chunk<BIN_THR, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fb, ba);
                     else
-                        bin_chunk<BIN_POS, kBinStride>(g, scale, ri, rp, cg, thr_s, mb, fb, ba);
+                        bin_chunk<BIN_POS, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fb, ba);
                 }
             }
             if (E.n_q > 0) {
@@ -992,6 +997,12 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                             u[rr][q] = 0.f;
                             vv[rr][q] = 0.f;
                         }
+                    // rows of this thread past the range (unprepared A rows): values replaced
+                    bool okr[4];
+#pragma unroll
+                    for (int rr = 0; rr < 4; ++rr)
+                        okr[rr] = ti.m0 + q4 * 32 + 16 * (rr >> 1) + 8 * (rr & 1) + (lane >> 2) <
+                                  ti.row_end;
                     auto chunk = [&](const uint32_t (&g)[2][16], int ch) {
 #pragma unroll
                         for (int m = 0; m < 4; ++m) {
@@ -1003,7 +1014,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                                     const float4 w4 = w[q2 * 8];
 #pragma unroll
                                     for (int rr = 0; rr < 4; ++rr) {
-                                        const float gv = __uint_as_float(g[rr >> 1][4 * m + 2 * (rr & 1) + e]);
+                                        const float gv =
+                                            okr[rr] ? __uint_as_float(g[rr >> 1][4 * m + 2 * (rr & 1) + e])
+                                                    : 0.f;
                                         u[rr][2 * q2] = fmaf(w4.x, gv, u[rr][2 * q2]);
                                         vv[rr][2 * q2] = fmaf(w4.y, gv, vv[rr][2 * q2]);
                                         u[rr][2 * q2 + 1] = fmaf(w4.z, gv, u[rr][2 * q2 + 1]);
@@ -1020,10 +1033,14 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         tmem_wait16x2(g[0], g[1]);
                         chunk(g, ch);
                     }
-                    // row weights of the thread's 4 rows (rows past the range weigh 0)
-                    float x[kQP];
+                    // row weights of the thread's 4 rows (rows past the range weigh 0):
+                    // cosine part c_r u + s_r v, sine part s_r u - c_r v (angle difference)
+                    float x[kQP], y[kQP];
 #pragma unroll
-                    for (int q = 0; q < kQP; ++q) x[q] = 0.f;
+                    for (int q = 0; q < kQP; ++q) {
+                        x[q] = 0.f;
+                        y[q] = 0.f;
+                    }
 #pragma unroll
                     for (int rr = 0; rr < 4; ++rr) {
                         const int rrow = q4 * 32 + 16 * (rr >> 1) + 8 * (rr & 1) + (lane >> 2);
@@ -1032,39 +1049,48 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         for (int q2 = 0; q2 < kQP / 2; ++q2) {
                             float4 w = rb[q2 * kBM + rrow];
                             if (!ok_r) w = make_float4(0.f, 0.f, 0.f, 0.f);
-                            x[2 * q2] = fmaf(w.x, u[rr][2 * q2], fmaf(w.y, vv[rr][2 * q2], x[2 * q2]));
-                            x[2 * q2 + 1] = fmaf(w.z, u[rr][2 * q2 + 1],
-                                                 fmaf(w.w, vv[rr][2 * q2 + 1], x[2 * q2 + 1]));
+                            const float u0 = u[rr][2 * q2], v0 = vv[rr][2 * q2];
+                            const float u1 = u[rr][2 * q2 + 1], v1 = vv[rr][2 * q2 + 1];
+                            x[2 * q2] = fmaf(w.x, u0, fmaf(w.y, v0, x[2 * q2]));
+                            x[2 * q2 + 1] = fmaf(w.z, u1, fmaf(w.w, v1, x[2 * q2 + 1]));
+                            y[2 * q2] = fmaf(w.y, u0, fmaf(-w.x, v0, y[2 * q2]));
+                            y[2 * q2 + 1] = fmaf(w.w, u1, fmaf(-w.z, v1, y[2 * q2 + 1]));
                         }
                     }
                     // sum over the warp's 32 lanes by recursive halving: each exchange sends
                     // the half of the q-values this lane does not keep; after three steps a
                     // lane holds one q (set by lane bits 4..2), the last two add the rest
+                    auto warp_sum8 = [&](float (&z)[kQP]) {
 #pragma unroll
-                    for (int hh = kQP / 2, o = 16; hh >= 1; hh >>= 1, o >>= 1) {
-                        const bool up = (lane & o) != 0;
+                        for (int hh = kQP / 2, o = 16; hh >= 1; hh >>= 1, o >>= 1) {
+                            const bool up = (lane & o) != 0;
 #pragma unroll
-                        for (int k = 0; k < hh; ++k) {
-                            const float send = up ? x[k] : x[k + hh];
-                            const float keep = up ? x[k + hh] : x[k];
-                            x[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                            for (int k = 0; k < hh; ++k) {
+                                const float send = up ? z[k] : z[k + hh];
+                                const float keep = up ? z[k + hh] : z[k];
+                                z[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                            }
                         }
-                    }
-                    x[0] += __shfl_xor_sync(0xffffffffu, x[0], 2);
-                    x[0] += __shfl_xor_sync(0xffffffffu, x[0], 1);
-                    if ((lane & 3) == 0) {
-                        const int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 +
-                                      ((lane >> 2) & 1);
-                        qred[(pass * kEpiWarps + ew) * kQP + q] = (double)x[0];
+                        z[0] += __shfl_xor_sync(0xffffffffu, z[0], 2);
+                        z[0] += __shfl_xor_sync(0xffffffffu, z[0], 1);
+                    };
+                    const int qme = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                    double *slot = qred + ((pass * kEpiWarps + ew) * kQP + qme) * 2;
+                    warp_sum8(x);
+                    if ((lane & 3) == 0) slot[0] = (double)x[0];
+                    if (E.q_parts == 2) {
+                        warp_sum8(y);
+                        if ((lane & 3) == 0) slot[1] = (double)y[0];
                     }
                 }
                 epi_sync(kEpiThreads);
-                for (int q = et; q < E.n_q; q += kEpiThreads) {
-                    double sq = 0.0;
-                    for (int w = 0; w < kEpiWarps; ++w)
-                        sq += qred[((q / kQP) * kEpiWarps + w) * kQP + q % kQP];
-                    qacc[q] += sq;
-                }
+                for (int q = et; q < E.n_q; q += kEpiThreads)
+                    for (int part = 0; part < E.q_parts; ++part) {
+                        double sq = 0.0;
+                        for (int w = 0; w < kEpiWarps; ++w)
+                            sq += qred[(((q / kQP) * kEpiWarps + w) * kQP + q % kQP) * 2 + part];
+                        qacc[2 * q + part] += sq;
+                    }
             }
             // accumulator buffer free for the MMA warp
             tc_before();

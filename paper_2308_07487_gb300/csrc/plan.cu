@@ -103,6 +103,7 @@ static EpiParams epi_of(const asd_corr_plan *p)
         }
     }
     e.nq_pad = (p->n_q + kQChunk - 1) / kQChunk * kQChunk;
+    e.q_parts = p->q_parts;
     e.cs = p->cs;
     return e;
 }
@@ -289,7 +290,8 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         ASD_CHECK_ARG(!(d->tile_n == 128 && (d->cluster == 4 || ew != 4)),
                       "tile_n = 128 needs cluster 1 and 4 epilogue warps");
     }
-    for (int k = 0; k < 2; ++k) ASD_CHECK_ARG(d->reserved[k] == 0, "reserved fields must be 0");
+    ASD_CHECK_ARG(d->reserved[0] == 0, "reserved fields must be 0");
+    ASD_CHECK_ARG(d->phase_sine == 0 || d->phase_sine == 1, "phase_sine: 0 or 1");
     if (d->geometry == ASD_GEOM_LATTICE) {
         ASD_CHECK_ARG(d->coords, "coords required for lattice geometry");
         for (int a = 0; a < 3; ++a) ASD_CHECK_ARG(d->L[a] >= 1 && d->L[a] <= 1 << 20, "bad L");
@@ -329,6 +331,7 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
     p->n_t = d->n_t;
     p->n_bins = d->n_bins;
     p->n_q = d->n_q;
+    p->q_parts = 1 + d->phase_sine;
     p->prec = d->precision;
     p->center = d->center;
     p->R = R;
@@ -753,10 +756,11 @@ int asd_pair_corr_normalize(const asd_corr_plan *p, const double *C_sum, const d
     ASD_CHECK_ARG(!C_sum || p->n_bins > 0, "plan has no bins");
     ASD_CHECK_ARG(!Sq_sum || p->n_q > 0, "plan has no q-vectors");
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n = std::max<int64_t>((int64_t)p->n_t * p->n_bins, (int64_t)p->n_t * p->n_q);
+    const int64_t n =
+        std::max<int64_t>((int64_t)p->n_t * p->n_bins, (int64_t)p->n_t * p->n_q * p->q_parts);
     const double inv_nq = 1.0 / ((double)p->N * p->S * p->T0);
     normalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-        C_sum, C, p->n_t, p->n_bins, p->inv_counts, Sq_sum, Sq, p->n_q, inv_nq);
+        C_sum, C, p->n_t, p->n_bins, p->inv_counts, Sq_sum, Sq, p->n_q * p->q_parts, inv_nq);
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;
 }

@@ -97,7 +97,8 @@ constexpr int kTPB = 8;  // displacements per block
 
 __global__ void __launch_bounds__(256) sq_corr_kernel(const double *__restrict__ Fb, int64_t K,
                                                       int S, int F, int T0, int n_t, int center,
-                                                      int n_q, double *__restrict__ Sq_sum)
+                                                      int n_q, int parts,
+                                                      double *__restrict__ Sq_sum)
 {
     __shared__ double red[8];
     const int q = blockIdx.x;
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(256) sq_corr_kernel(const double *__restrict__
     }
     const int tb = blockIdx.y * kTPB;
     for (int t = tb; t < tb + kTPB && t < n_t; ++t) {
-        double v = 0.0;
+        double v = 0.0, vs = 0.0;
         for (int e = threadIdx.x; e < n_terms; e += blockDim.x) {
             const int a = e % 3, st = e / 3;
             const int s = st / T0, t0 = st % T0;
@@ -128,9 +129,16 @@ __global__ void __launch_bounds__(256) sq_corr_kernel(const double *__restrict__
             const int64_t ka = kb + 3 * (int64_t)t;
             v = fma(fc[ka], fc[kb] - mc[a], v);
             v = fma(fs[ka], fs[kb] - ms[a], v);
+            // sine part: sin(a - b) = sin a cos b - cos a sin b
+            vs = fma(fs[ka], fc[kb] - mc[a], vs);
+            vs = fma(-fc[ka], fs[kb] - ms[a], vs);
         }
         v = block_sum(v, red);
-        if (threadIdx.x == 0) Sq_sum[(int64_t)t * n_q + q] += v;
+        if (threadIdx.x == 0) Sq_sum[((int64_t)t * n_q + q) * parts] += v;
+        if (parts == 2) {
+            vs = block_sum(vs, red);
+            if (threadIdx.x == 0) Sq_sum[((int64_t)t * n_q + q) * 2 + 1] += vs;
+        }
     }
 }
 
@@ -155,7 +163,7 @@ int asd_pair_corr_sq_separable(asd_corr_plan *p, const float *traj, double *Sq_s
     ASD_CUDA_TRY(cudaGetLastError());
     dim3 g2((unsigned)p->n_q, (unsigned)((p->n_t + kTPB - 1) / kTPB), 1);
     sq_corr_kernel<<<g2, 256, 0, s>>>(p->sqF, K, p->S, p->F, p->T0, p->n_t, p->center, p->n_q,
-                                      Sq_sum);
+                                      p->q_parts, Sq_sum);
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;
 }

@@ -209,3 +209,65 @@ def test_phase_on_lattice_row_range(asd, form):
     got = run_gpu(asd, lat, tr, 16, 6, 1.0, 15, form, q=q, rows=rows)
     ref = oracle_ref(lat, tr, 16, 6, 1.0, 15, q=q, rows=rows)
     assert_parity(got, ref, form, q=True)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_phase_sine_part(asd, form):
+    """Cosine and sine parts of Eq. 3's phase sum (jittered open cube, 13 q, rows from
+    mid-tile), in the [n_t][n_q][2] layout; the sine part vanishes at t = 0."""
+    lat = synth.hypercubic(7, 3, False, jitter=0.1, seed=3)
+    q = synth.q_vectors_glass()[::5]
+    tr = synth.traj_precess(lat.n_sites, 30, seed=8)
+    rows = (20, 300)
+    plan = asd.CorrPlan.for_lattice(lat, 30, 18, 9, 0.5, 12, precision=form, q=q,
+                                    phase_sine=True)
+    C = torch.zeros((9, 12), dtype=torch.float64, device="cuda")
+    Sq = torch.zeros((9, len(q), 2), dtype=torch.float64, device="cuda")
+    plan.run(torch.from_numpy(np.ascontiguousarray(tr[:, None])).cuda(), C, Sq, rows=rows)
+    Sep = torch.zeros((9, len(q), 2), dtype=torch.float64, device="cuda")
+    plan.sq_separable(torch.from_numpy(np.ascontiguousarray(tr[:, None])).cuda(), Sep)
+    assert asd.sync_status() == 0
+    plan.close()
+    ref = oracle.pair_corr(tr, 18, list(range(9)), oracle.Geometry.of_lattice(lat), 0.5, 12,
+                           q=q, rows=rows)
+    full = oracle.pair_corr(tr, 18, list(range(9)), oracle.Geometry.of_lattice(lat), 0.5, 1, q=q)
+    got = Sq.cpu().numpy()
+    scale = np.abs(ref["Sq_sum"]).max()
+    assert np.abs(got[..., 0] - ref["Sq_sum"]).max() / scale <= 10 * TOL[form]
+    assert np.abs(got[..., 1] - ref["Sq_im"]).max() / scale <= 10 * TOL[form]
+    assert oracle.bin_error(C.cpu().numpy(), ref).max() <= TOL[form]
+    sep = Sep.cpu().numpy()
+    fs = np.abs(full["Sq_sum"]).max()
+    assert np.abs(sep[..., 0] - full["Sq_sum"]).max() / fs <= 1e-5
+    assert np.abs(sep[..., 1] - full["Sq_im"]).max() / fs <= 1e-5
+    assert np.abs(sep[0, :, 1]).max() <= 1e-5 * fs
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_rows_past_the_range_are_ignored(asd, form):
+    """A rows outside the contracted range may hold anything (here NaN from an earlier
+    preparation of the whole range): bins, phase and sine parts of the range stay
+    exact.  Positions geometry (threshold binning) with phase weights."""
+    lat = synth.hypercubic(7, 3, False, jitter=0.1, seed=3)
+    q = synth.q_vectors_glass()[::5]
+    tr = synth.traj_precess(lat.n_sites, 30, seed=8)
+    bad = np.full_like(tr, np.nan)
+    rows = (20, 300)
+    plan = asd.CorrPlan.for_lattice(lat, 30, 18, 9, 0.5, 12, precision=form, q=q,
+                                    phase_sine=True)
+    plan.prepare(torch.from_numpy(np.ascontiguousarray(bad[:, None])).cuda())
+    d_tr = torch.from_numpy(np.ascontiguousarray(tr[:, None])).cuda()
+    plan.prepare(d_tr, rows=rows)
+    C = torch.zeros((9, 12), dtype=torch.float64, device="cuda")
+    Sq = torch.zeros((9, len(q), 2), dtype=torch.float64, device="cuda")
+    plan.contract(C, Sq, rows=rows)
+    assert asd.sync_status() == 0
+    plan.close()
+    got_c, got_q = C.cpu().numpy(), Sq.cpu().numpy()
+    assert np.isfinite(got_c).all() and np.isfinite(got_q).all()
+    ref = oracle.pair_corr(tr, 18, list(range(9)), oracle.Geometry.of_lattice(lat), 0.5, 12,
+                           q=q, rows=rows)
+    assert oracle.bin_error(got_c, ref).max() <= TOL[form]
+    scale = np.abs(ref["Sq_sum"]).max()
+    assert np.abs(got_q[..., 0] - ref["Sq_sum"]).max() / scale <= 10 * TOL[form]
+    assert np.abs(got_q[..., 1] - ref["Sq_im"]).max() / scale <= 10 * TOL[form]

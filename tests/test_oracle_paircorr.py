@@ -147,6 +147,12 @@ def test_phase_form_matches_separable_transform():
         r = oracle.pair_corr(tr, 8, [0, 2, 6], geo, 0.5, 10, q=q, center=center)
         ref = checks.separable_phase_sum(tr, 8, [0, 2, 6], lat.pos, q, center=center)
         np.testing.assert_allclose(r["Sq_sum"], ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+        ref_s = checks.separable_phase_sum(tr, 8, [0, 2, 6], lat.pos, q, center=center,
+                                           part="sin")
+        np.testing.assert_allclose(r["Sq_im"], ref_s, rtol=0, atol=1e-10 * np.abs(ref).max())
+        # sine weights are odd and G(0) is symmetric: the sine part vanishes at t = 0
+        assert np.abs(r["Sq_im"][0]).max() <= 1e-12 * np.abs(r["Sq_sum"]).max()
+        assert np.abs(r["Sq_im"][1:]).max() > 1e-6 * np.abs(r["Sq_sum"]).max()
 
 
 def test_q_zero_is_total_moment_correlation():
@@ -211,6 +217,8 @@ def test_time_reversal_swaps_the_pair_roles(periodic, jitter):
     b = oracle.pair_corr(rev, T0, [n_t - 1], geo, 0.5, 8, q=q)
     np.testing.assert_allclose(a["C_sum"], b["C_sum"], rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(a["Sq_sum"], b["Sq_sum"], rtol=1e-12, atol=1e-12)
+    # the sine weight is odd in (i, j): reversal flips the sign of the sine part
+    np.testing.assert_allclose(a["Sq_im"], -b["Sq_im"], rtol=1e-12, atol=1e-12)
     # a planted swap of i and j in one term would break it: t = 1 is not invariant
     c = oracle.pair_corr(tr, T0, [1], geo, 0.5, 8)
     d = oracle.pair_corr(rev, T0, [1], geo, 0.5, 8)
