@@ -646,10 +646,19 @@ def run_learned(args):
         hist_e[prop] = np.concatenate(e_smp)
         hist_m[prop] = np.concatenate(m_smp)
         es = np.array(es)
-        # integrated autocorrelation time of the energy (initial positive sequence)
-        x = es - es.mean()
-        c = np.correlate(x, x, "full")[len(x) - 1:] / (x.var() * len(x))
-        tau = 0.5 + sum(v for v in c[1:20] if v > 0)
+        # integrated autocorrelation time of the energy per site, in units of the 2-sweep
+        # measurement interval: normalised autocorrelation of each chain's series, averaged
+        # over the chains, summed up to its first non-positive lag
+        E = np.stack(e_smp, 1)                                   # [chains][measurements]
+        X = E - E.mean(axis=1, keepdims=True)
+        var = (X * X).mean()
+        n_meas = X.shape[1]
+        rho = [float((X[:, :n_meas - k] * X[:, k:]).mean() / var) for k in range(1, 30)]
+        tau = 0.5
+        for r in rho:
+            if r <= 0:
+                break
+            tau += r
         return s2, {"acceptance": acc / pr, "energy_per_site": float(es.mean()),
                     "energy_sem": float(es.std() / math.sqrt(len(es))), "tau_int_energy": tau,
                     "magnetisation": float(np.mean(ms))}
