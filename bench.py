@@ -438,6 +438,21 @@ def run_glass(args):
 
     import oracle
     from paper_2308_07487_gb300 import asd, synth
+    if args.ncu:
+        # profiling case of the same kernel shapes: 32^3 jittered +-J glass (32768 sites),
+        # F = 640, T0 = 512, 2 displacements, 256 bins, 64 q; one launch with bins only,
+        # then one with bins and phase weights (capture the second: -s 1 -c 1)
+        lat = synth.hypercubic(32, 3, False, pm_j=True, p=0.5, seed=7, block=(4, 4, 8),
+                               jitter=0.1)
+        tr_s = torch.from_numpy(synth.traj_precess(lat.n_sites, 640, seed=5)).cuda()
+        for q in (None, synth.q_vectors_glass()):
+            plan = asd.CorrPlan.for_lattice(lat, 640, 512, 2, 0.5, 256, q=q)
+            C = torch.zeros((2, 256), dtype=torch.float64, device="cuda")
+            Sq = torch.zeros((2, 64), dtype=torch.float64, device="cuda") if q is not None else None
+            plan.run(tr_s, C, Sq)
+            asd.check(asd.sync_status(), "glass profiling case")
+            plan.close()
+        return
     cfg = synth.cfg_glass64()
     lat = cfg.lattice
     N = lat.n_sites

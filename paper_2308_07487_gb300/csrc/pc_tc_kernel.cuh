@@ -9,23 +9,25 @@
 //               trajectory copies) and BN-row B tiles into a shared-memory ring;
 //   warp 1      allocates TMEM and, from one thread, issues tcgen05.mma into one of two
 //               128 x BN FP32 accumulators in tensor memory (double buffered), committing
-//               each stage back to the ring and each finished tile to the epilogue;
-//   warps 2-5   epilogue: tcgen05.ld one accumulator row per thread and reduce it --
-//               per-thread private FP32 bins in shared memory (conflict-free [bin][row]
-//               layout), phase weights from per-site cos/sin tables -- then FP64.
+//               each stage back to the ring and each finished work item to the epilogue;
+//   warps 2..   epilogue (EW = 4 or 8 warps): reads the accumulator from TMEM and
+//               reduces it -- per-thread private FP32 bins in shared memory
+//               (conflict-free [bin][row] layout), phase weights from per-site cos/sin
+//               tables -- then FP64 per-CTA sums and FP64 atomics into the outputs.
 //
 // The accumulator living in TMEM plays the role of the paper's OTF_SM shared-memory
 // staging of the C tile (Section 3.4): the epilogue never holds the tile in registers.
-// The per-pair phase factor uses cos(a - b) = cos a cos b + sin a sin b on tables made
-// once per plan, so no transcendental is evaluated per pair (the register-spill
-// problem of the paper's OTF_REG variant).
+// The per-pair phase factor uses cos(a - b) = cos a cos b + sin a sin b (and
+// sin(a - b) = sin a cos b - cos a sin b for the sine part) on tables made once per
+// plan, so no transcendental is evaluated per pair (the register-spill problem of the
+// paper's OTF_REG variant).
 //
-// Persistent: one CTA per SM walks a static round-robin list of
-// (problem, t, row tile, column tile) work items, grouped 8 row tiles at a time so
-// concurrently running CTAs share A and B panels in L2.  Several problems (a batched
-// ensemble) share the list.  Every wait is bounded: after kTimeoutNs a role records
-// an error in the device error word and stops; the CTA then drains its own in-flight
-// copies and MMAs, frees TMEM and exits.
+// Persistent: one CTA per SM walks a static round-robin list of (problem, t, K chunk,
+// row tile, column tile) work items in grouped raster order (raster_m row tiles per
+// group, 16 by default) so concurrently running CTAs share A and B panels in L2.
+// Several problems (a batched ensemble) share the list.  Every wait is bounded: after
+// kTimeoutNs a role records an error in the device error word and stops; the CTA then
+// drains its own in-flight copies and MMAs, frees TMEM and exits.
 #pragma once
 
 #include <cuda_bf16.h>
