@@ -271,3 +271,35 @@ def test_rows_past_the_range_are_ignored(asd, form):
     scale = np.abs(ref["Sq_sum"]).max()
     assert np.abs(got_q[..., 0] - ref["Sq_sum"]).max() / scale <= 10 * TOL[form]
     assert np.abs(got_q[..., 1] - ref["Sq_im"]).max() / scale <= 10 * TOL[form]
+
+
+@pytest.mark.parametrize("form", ["split_bf16", "bf16", "tf32", "fp32"])
+def test_degenerate_shapes(asd, form):
+    """The paper's own averaging (one origin, M samples: T0 = 1, S = M), one displacement
+    with F = T0 + n_t - 1 exactly, a single bin, and an empty row range (a no-op)."""
+    lat = synth.hypercubic(9, 2, True)
+    # M = 50 realisations at one origin, 3 frames: K = 3 * 1 * 50
+    tr = synth.traj_precess(lat.n_sites, 3, seed=14, S=50)
+    got = run_gpu(asd, lat, tr, 1, 3, 1.0, 7, form)
+    ref = oracle_ref(lat, tr, 1, 3, 1.0, 7)
+    assert_parity(got, ref, form)
+    # a single displacement, F = T0 exactly, one bin (every pair within r < w)
+    tr2 = synth.traj_precess(lat.n_sites, 16, seed=15)
+    got = run_gpu(asd, lat, tr2, 16, 1, 100.0, 1, form)
+    ref = oracle_ref(lat, tr2, 16, 1, 100.0, 1)
+    assert got["counts"][0] == lat.n_sites ** 2
+    assert_parity(got, ref, form)
+    # empty row range: nothing is added
+    got = run_gpu(asd, lat, tr2, 8, 4, 1.0, 7, form, rows=(40, 40))
+    assert not got["C_sum"].any()
+
+
+def test_maximum_q_count(asd):
+    """n_q = 256 (the largest accepted): all phase passes, every chunk full."""
+    lat = synth.hypercubic(5, 3, False, jitter=0.1, seed=2)
+    g = np.random.default_rng(3)
+    q = g.standard_normal((256, 3))
+    tr = synth.traj_precess(lat.n_sites, 12, seed=6)
+    got = run_gpu(asd, lat, tr, 8, 3, 0.5, 6, "split_bf16", q=q)
+    ref = oracle_ref(lat, tr, 8, 3, 0.5, 6, q=q)
+    assert_parity(got, ref, "split_bf16", q=True)
