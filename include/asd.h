@@ -105,7 +105,9 @@ typedef struct asd_corr_desc {
                                1: Sq_sum[t][q][2] holds (cosine, sine) parts, the sine
                                part sum_ij sin(q.(r_i - r_j)) G_ij(t) (Eq. 3's imaginary
                                part is its negative)                                     */
-    int32_t reserved[1];    /* must be zero                                            */
+    int32_t static_schedule;/* 0: work items claimed from a global counter (dynamic,
+                               the default; clusters always run static); 1: static
+                               round-robin order                                         */
 } asd_corr_desc;
 
 typedef struct asd_corr_plan asd_corr_plan;

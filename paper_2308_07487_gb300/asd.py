@@ -41,7 +41,7 @@ class asd_corr_desc(ctypes.Structure):
                 ("raster_m", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("k_chunks", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("epi_warps", ctypes.c_int32), ("phase_sine", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("static_schedule", ctypes.c_int32)]
 
 
 class asd_system(ctypes.Structure):
@@ -144,7 +144,7 @@ class CorrPlan:
     def __init__(self, N, F, T0, n_t, precision="split_bf16", S=1, center=False, coords=None,
                  L=(1, 1, 1), periodic=False, pos=None, bin_width=1.0, n_bins=0, q=None,
                  tile_n=0, raster_m=0, stages=0, k_chunks=0, cluster=0, epi_warps=0,
-                 phase_sine=False):
+                 phase_sine=False, static_schedule=False):
         d = asd_corr_desc()
         d.n_sites, d.n_frames, d.n_samples, d.T0, d.n_t = N, F, S, T0, n_t
         d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -177,6 +177,7 @@ class CorrPlan:
         d.cluster = int(cluster)
         d.epi_warps = int(epi_warps)
         d.phase_sine = int(bool(phase_sine))
+        d.static_schedule = int(bool(static_schedule))
         self.q_parts = 1 + d.phase_sine  # Sq_sum is [n_t][n_q] or [n_t][n_q][2]
         self.desc = d
         self.N, self.F, self.S, self.T0, self.n_t = N, F, S, T0, n_t

@@ -121,6 +121,7 @@ struct TcLaunchArgs {
     TcOverride ov;
     int stages;
     uint32_t VB;           // bytes of the per-problem epilogue region (largest problem)
+    unsigned long long *counter;  // dynamic schedule: work-item counter (zero at launch), or null
     int NB, NQ;            // epilogue shared-memory layout maxima
     int *err;
 };
@@ -164,6 +165,7 @@ struct asd_corr_plan {
     int n_lut;
     float2 *cs;
     double *sqF;               // separable phase form: transforms [2 n_q][S*3F] (n_q > 0)
+    unsigned long long *counter;  // work-item counter of the dynamic schedule
     int q_parts;               // 1 + desc.phase_sine: values per (t, q) in Sq_sum
     int tiles_m_all, tiles_n;
     int use_window;
@@ -195,7 +197,8 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
 int tc_configure(asd_corr_plan *p);    // stages / smem for the plan's form
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
               int BN, int swizzle_bytes, int stages, size_t smem, uint32_t var_bytes,
-              int max_nb, int max_nq, int cl, int ew, int sm_count, cudaStream_t s);
+              int max_nb, int max_nq, int cl, int ew, int sm_count, unsigned long long *counter,
+              cudaStream_t s);
 // work items of one problem: n_t * k_chunks * ceil(tiles_m / cl) * tiles_n
 inline int64_t tc_work_items(int n_t, int k_chunks, int tiles_m, int tiles_n, int cl)
 {

@@ -80,7 +80,8 @@ int tc_configure(asd_corr_plan *p)
 
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
               int BN, int swizzle_bytes, int stages, size_t smem, uint32_t var_bytes_,
-              int max_nb, int max_nq, int cl, int ew, int sm_count, cudaStream_t s)
+              int max_nb, int max_nq, int cl, int ew, int sm_count, unsigned long long *counter,
+              cudaStream_t s)
 {
     if (total_tiles <= 0) return ASD_OK;
     LaunchArgs a{};
@@ -90,6 +91,9 @@ int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOver
     a.ov = ov;
     a.stages = stages;
     a.VB = var_bytes_;
+    // dynamic schedule: the counter starts at zero for every launch (stream-ordered)
+    a.counter = cl == 1 ? counter : nullptr;
+    if (a.counter) ASD_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s));
     a.NB = max_nb;
     a.NQ = max_nq;
     a.err = device_error_word();

@@ -45,6 +45,12 @@ constexpr int kQC = kQChunk;                  // (cos, sin) rows are padded to w
 constexpr int kQP = 8;                        // q-vectors per pass of the phase loop
 static_assert(kQP == 8 && kQC % kQP == 0, "the phase reduction maps lane bits 4..2 to q");
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
+// Work items are handed from the TMA thread to the MMA thread and the epilogue warps
+// through a ring of kWQ slots in shared memory.  With the dynamic schedule the TMA thread
+// claims each item from a global counter, so the items in flight across the grid stay
+// together whatever each item costs (L2 reuse of A / B panels, no drift, balanced tail);
+// the static schedule takes items cid, cid + n_clusters, ... (clusters use it).
+constexpr int kWQ = 4;
 // Private bins are a [bin][128 * EW/4] array: epilogue thread (row r, column half h)
 // only ever touches column r + 128 h, i.e. bank r mod 32, so the per-pair accumulation
 // is free of bank conflicts whatever the bins of the 32 lanes are (with an odd stride,
@@ -593,8 +599,12 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     uint8_t *epi = tiles + (size_t)stages * kStageBytes;
     const EpiLayout EL = epi_layout(args.VB, args.NB, args.NQ, BN, EW);
     uint64_t *bars = reinterpret_cast<uint64_t *>(epi + EL.total);
-    // bars: full[stages], empty[stages], tfull[2], tempty[2], drain
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 5);
+    // bars: full[stages], empty[stages], tfull[2], tempty[2], drain, wqfull[kWQ],
+    // wqempty[kWQ]; then the work ring wq[kWQ] and the TMEM address slot
+    const uint32_t wqfull0 = saddr(bars + 2 * stages + 5);
+    const uint32_t wqempty0 = saddr(bars + 2 * stages + 5 + kWQ);
+    volatile int64_t *wq = reinterpret_cast<volatile int64_t *>(bars + 2 * stages + 5 + 2 * kWQ);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 5 + 3 * kWQ);
     const uint32_t full0 = saddr(bars), empty0 = saddr(bars + stages);
     const uint32_t tfull0 = saddr(bars + 2 * stages), tempty0 = saddr(bars + 2 * stages + 2);
     const uint32_t drain = saddr(bars + 2 * stages + 4);
@@ -611,6 +621,11 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             mbar_init(tempty0 + 8 * a, kEpiWarps);
         }
         mbar_init(drain, 1);
+        for (int k = 0; k < kWQ; ++k) {
+            mbar_init(wqfull0 + 8 * k, 1);
+            // released by the MMA thread and one lane of every epilogue warp
+            mbar_init(wqempty0 + 8 * k, 1 + kEpiWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) tmem_alloc(saddr(tmem_slot), kTmemCols);
@@ -631,7 +646,21 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             uint32_t phase = 0;
             bool ok = true;
             WorkCursor cu;
-            for (int64_t tau = cid; tau < args.total_tiles && ok; tau += n_clusters) {
+            for (int64_t v = 0; ok; ++v) {
+                // publish the next work item (-1: none left) once its ring slot is free
+                const int qs = (int)(v % kWQ);
+                if (!mbar_wait(wqempty0 + 8 * qs, (uint32_t)((v / kWQ) & 1) ^ 1u, args.err,
+                               DEV_TIMEOUT_TMA)) {
+                    ok = false;
+                    break;
+                }
+                int64_t tau = (CL == 1 && args.counter)
+                                  ? (int64_t)atomicAdd(args.counter, 1ull)
+                                  : cid + v * n_clusters;
+                if (tau >= args.total_tiles) tau = -1;
+                wq[qs] = tau;
+                mbar_arrive(wqfull0 + 8 * qs);  // release: the slot is visible to the waiters
+                if (tau < 0) break;
                 const TileInfo ti = decode<CL>(cu, probs, args.n_probs, args.ov, tau, BN, rank);
                 const TcProblem &P = probs[ti.p];
                 for (int kg = ti.kg0; kg < ti.kg1; ++kg) {
@@ -681,7 +710,15 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             uint32_t v = 0;
             bool ok = true;
             WorkCursor cu;
-            for (int64_t tau = cid; tau < args.total_tiles && ok; tau += n_clusters, ++v) {
+            for (;; ++v) {
+                const int qs = (int)(v % kWQ);
+                if (!mbar_wait(wqfull0 + 8 * qs, (v / kWQ) & 1, args.err, DEV_TIMEOUT_MMA)) {
+                    ok = false;
+                    break;
+                }
+                const int64_t tau = wq[qs];
+                mbar_arrive(wqempty0 + 8 * qs);
+                if (tau < 0) break;
                 const TileInfo ti = decode<CL>(cu, probs, args.n_probs, args.ov, tau, BN, rank);
                 const uint32_t acc = v & 1, use = v >> 1;
                 if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, args.err, DEV_TIMEOUT_MMA)) {
@@ -805,7 +842,18 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     acc = 0.0;
                 }
         };
-        for (int64_t tau = cid; tau < args.total_tiles; tau += n_clusters, ++v) {
+        for (;; ++v) {
+            const int qs = (int)(v % kWQ);
+            {
+                const bool gotq = mbar_wait(wqfull0 + 8 * qs, (v / kWQ) & 1, args.err,
+                                            DEV_TIMEOUT_EPI);
+                ok = epi_sync_and(gotq, kEpiThreads);
+                if (!ok) break;
+            }
+            const int64_t tau = wq[qs];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(wqempty0 + 8 * qs);
+            if (tau < 0) break;
             const TileInfo ti = decode<CL>(cu, probs, args.n_probs, args.ov, tau, BN, rank);
             const TcProblem &P = probs[ti.p];
             const EpiParams &E = P.epi;

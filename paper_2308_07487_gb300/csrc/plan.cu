@@ -244,6 +244,7 @@ void asd_pair_corr_plan_destroy(asd_corr_plan *p)
     cudaFree(p->lut);
     cudaFree(p->cs);
     cudaFree(p->sqF);
+    cudaFree(p->counter);
     cudaFree(p->inv_counts);
     cudaFree(p->d_prob);
     delete p->h_prob;
@@ -290,7 +291,7 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         ASD_CHECK_ARG(!(d->tile_n == 128 && (d->cluster == 4 || ew != 4)),
                       "tile_n = 128 needs cluster 1 and 4 epilogue warps");
     }
-    ASD_CHECK_ARG(d->reserved[0] == 0, "reserved fields must be 0");
+    ASD_CHECK_ARG(d->static_schedule == 0 || d->static_schedule == 1, "static_schedule: 0 or 1");
     ASD_CHECK_ARG(d->phase_sine == 0 || d->phase_sine == 1, "phase_sine: 0 or 1");
     if (d->geometry == ASD_GEOM_LATTICE) {
         ASD_CHECK_ARG(d->coords, "coords required for lattice geometry");
@@ -560,7 +561,8 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
     // ---- tensor maps for the whole row range ----
     if (tc) {
         p->h_prob = new (std::nothrow) TcProblem;
-        if (!p->h_prob || cudaMalloc(&p->d_prob, sizeof(TcProblem)) != cudaSuccess) {
+        if (!p->h_prob || cudaMalloc(&p->d_prob, sizeof(TcProblem)) != cudaSuccess ||
+            cudaMalloc(&p->counter, sizeof(unsigned long long)) != cudaSuccess) {
             cudaGetLastError();
             return fail(ASD_ENOMEM);
         }
@@ -625,7 +627,8 @@ int asd_pair_corr_contract(asd_corr_plan *p, int64_t row_begin, int64_t row_end,
     ov.Sq_sum = Sq_sum;
     return launch_tc(p->d_prob, 1, ov.n_tiles, ov, p->prec, p->BN, p->swizzle_bytes, p->stages,
                      p->smem_bytes, tc_var_bytes(p->NW, p->n_bins, p->n_lut, p->EW), p->n_bins,
-                     p->n_q, p->CL, p->EW, p->sm_count, s);
+                     p->n_q, p->CL, p->EW, p->sm_count,
+                     p->d.static_schedule ? nullptr : p->counter, s);
 }
 
 int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs, int n,
@@ -727,7 +730,8 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
             cudaFree(dbuf);
             dbuf = nullptr;
             cap_n = 0;
-            if (cudaMalloc(&dbuf, sizeof(TcProblem) * n) != cudaSuccess) {
+            // descriptors, then the work-item counter of the dynamic schedule
+            if (cudaMalloc(&dbuf, sizeof(TcProblem) * n + 256) != cudaSuccess) {
                 cudaGetLastError();
                 return ASD_ENOMEM;
             }
@@ -742,8 +746,13 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
         if (rc) return rc;
     }
     TcOverride ov{};
+    // dynamic schedule unless any plan of the batch asks for the static order; the
+    // counter lives behind the work list
+    bool dyn = true;
+    for (int k = 0; k < n; ++k) dyn = dyn && !plans[k]->d.static_schedule;
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(dbuf + cap_n);
     return launch_tc(dbuf, n, total, ov, p0->prec, p0->BN, p0->swizzle_bytes, stages, smem, vb,
-                     max_nb, max_nq, p0->CL, p0->EW, p0->sm_count, s);
+                     max_nb, max_nq, p0->CL, p0->EW, p0->sm_count, dyn ? ctr : nullptr, s);
 }
 
 int asd_pair_corr_normalize(const asd_corr_plan *p, const double *C_sum, const double *Sq_sum,
