@@ -245,6 +245,19 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// (u, v) += (wc, ws) * g as one packed two-wide FP32 FMA (each lane rounds like fmaf).
+__device__ __forceinline__ void fma2(float &u, float &v, float wc, float ws, float g)
+{
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %4};\n\t"
+        "mov.b64 pc, {%0, %1};\n\t"
+        "fma.rn.f32x2 pc, pa, pb, pc;\n\t"
+        "mov.b64 {%0, %1}, pc;\n\t}"
+        : "+f"(u), "+f"(v)
+        : "f"(wc), "f"(ws), "f"(g));
+}
+
 // Issue half of tmem_ld32: the registers are valid only after tmem_wait32 on them.
 __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32])
 {
@@ -1067,10 +1080,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                                         const float gv =
                                             okr[rr] ? __uint_as_float(g[rr >> 1][4 * m + 2 * (rr & 1) + e])
                                                     : 0.f;
-                                        u[rr][2 * q2] = fmaf(w4.x, gv, u[rr][2 * q2]);
-                                        vv[rr][2 * q2] = fmaf(w4.y, gv, vv[rr][2 * q2]);
-                                        u[rr][2 * q2 + 1] = fmaf(w4.z, gv, u[rr][2 * q2 + 1]);
-                                        vv[rr][2 * q2 + 1] = fmaf(w4.w, gv, vv[rr][2 * q2 + 1]);
+                                        fma2(u[rr][2 * q2], vv[rr][2 * q2], w4.x, w4.y, gv);
+                                        fma2(u[rr][2 * q2 + 1], vv[rr][2 * q2 + 1], w4.z, w4.w, gv);
                                     }
                                 }
                             }
