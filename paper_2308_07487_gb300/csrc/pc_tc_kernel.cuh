@@ -33,6 +33,7 @@
 #include <cuda_bf16.h>
 
 #include "asd_internal.h"
+#include "fma2.cuh"
 #include "geom.cuh"
 
 namespace asd {
@@ -244,19 +245,6 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// (u, v) += (wc, ws) * g as one packed two-wide FP32 FMA (each lane rounds like fmaf).
-__device__ __forceinline__ void fma2(float &u, float &v, float wc, float ws, float g)
-{
-    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
-        "mov.b64 pa, {%2, %3};\n\t"
-        "mov.b64 pb, {%4, %4};\n\t"
-        "mov.b64 pc, {%0, %1};\n\t"
-        "fma.rn.f32x2 pc, pa, pb, pc;\n\t"
-        "mov.b64 {%0, %1}, pc;\n\t}"
-        : "+f"(u), "+f"(v)
-        : "f"(wc), "f"(ws), "f"(g));
-}
 
 // Issue half of tmem_ld32: the registers are valid only after tmem_wait32 on them.
 __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32])
