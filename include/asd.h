@@ -90,7 +90,8 @@ typedef struct asd_corr_desc {
     int32_t n_bins;         /* 0 .. 4096                                               */
     int32_t n_q;            /* 0 .. 256                                                */
     const double *q;        /* host [n_q][3]                                           */
-    int32_t tile_n;         /* 0 = chosen by the autotuner, else 128 or 256 (tensor forms) */
+    int32_t tile_n;         /* 0 = automatic (128 for N <= 4096, else 256), else 128 or
+                               256 (tensor forms)                                        */
     int32_t raster_m;       /* 0 = automatic, else row tiles per raster group (1..64)  */
     int32_t stages;         /* 0 = automatic, else shared-memory pipeline stages (2..8) */
     int32_t k_chunks;       /* 0 = automatic (split-BF16: one per ~1536 K elements;
@@ -100,7 +101,8 @@ typedef struct asd_corr_desc {
                                one (FP32 within a tile, FP64 across tiles)               */
     int32_t cluster;        /* 0 = automatic, 1, or 4: CTAs sharing one B tile via TMA
                                multicast                                                 */
-    int32_t epi_warps;      /* 0 = automatic, 4 or 8 epilogue warps per CTA            */
+    int32_t epi_warps;      /* 0 = automatic (4), 4 or 8 epilogue warps per CTA (8 needs
+                               tile_n 256 and cluster 1)                                 */
     int32_t phase_sine;     /* 0: Sq_sum[t][q] holds the cosine part of Eq. 3's phase sum;
                                1: Sq_sum[t][q][2] holds (cosine, sine) parts, the sine
                                part sum_ij sin(q.(r_i - r_j)) G_ij(t) (Eq. 3's imaginary

@@ -22,10 +22,11 @@
 // plan, so no transcendental is evaluated per pair (the register-spill problem of the
 // paper's OTF_REG variant).
 //
-// Persistent: one CTA per SM walks a static round-robin list of (problem, t, K chunk,
-// row tile, column tile) work items in grouped raster order (raster_m row tiles per
-// group, 16 by default) so concurrently running CTAs share A and B panels in L2.
-// Several problems (a batched ensemble) share the list.  Every wait is bounded: after
+// Persistent: one CTA per SM takes (problem, t, K chunk, row tile, column tile) work
+// items in grouped raster order (raster_m row tiles per group, 16 by default) so
+// concurrently running CTAs share A and B panels in L2; the TMA thread claims each item
+// from a global counter (or, static, takes every n-th) and passes its index to the other
+// roles.  Several problems (a batched ensemble) share the list.  Every wait is bounded: after
 // kTimeoutNs a role records an error in the device error word and stops; the CTA then
 // drains its own in-flight copies and MMAs, frees TMEM and exits.
 #pragma once
