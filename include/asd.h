@@ -102,7 +102,8 @@ typedef struct asd_corr_desc {
     int32_t cluster;        /* 0 = automatic, 1, or 4: CTAs sharing one B tile via TMA
                                multicast                                                 */
     int32_t epi_warps;      /* 0 = automatic (4), 4 or 8 epilogue warps per CTA (8 needs
-                               tile_n 256 and cluster 1)                                 */
+                               tile_n 256 and cluster 1; its phase loop takes 4 q per
+                               pass instead of 8)                                        */
     int32_t phase_sine;     /* 0: Sq_sum[t][q] holds the cosine part of Eq. 3's phase sum;
                                1: Sq_sum[t][q][2] holds (cosine, sine) parts, the sine
                                part sum_ij sin(q.(r_i - r_j)) G_ij(t) (Eq. 3's imaginary

@@ -44,8 +44,10 @@ namespace {
 // 8 (two per quarter, half the columns each).  Threads = TMA warp + MMA warp + EW warps.
 constexpr int kMaxEpiWarps = 8;
 constexpr int kQC = kQChunk;                  // (cos, sin) rows are padded to whole kQC
-constexpr int kQP = 8;                        // q-vectors per pass of the phase loop
-static_assert(kQP == 8 && kQC % kQP == 0, "the phase reduction maps lane bits 4..2 to q");
+// q-vectors per pass of the phase loop: 8 with 4 epilogue warps; 4 with 8 warps, whose
+// register budget (two warps per scheduler) has no room for 8 q of accumulators
+__host__ __device__ constexpr int qp_of(int ew) { return ew == 8 ? 4 : 8; }
+static_assert(kQC % qp_of(4) == 0 && kQC % qp_of(8) == 0, "q passes tile the padded q rows");
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
 // Work items are handed from the TMA thread to the MMA thread and the epilogue warps
 // through a ring of kWQ slots in shared memory.  With the dynamic schedule the TMA thread
@@ -382,13 +384,14 @@ __host__ __device__ inline EpiLayout epi_layout(uint32_t vb, int nb, int nq, int
     // phase sums per q: (cosine, sine) parts
     L.qacc = take(o, 8u * 2 * (nq > 0 ? nq : 1));
     // one slot per (pass, warp, q): the passes of a tile are reduced once at its end
-    L.qred = take(o, 8u * 2 * ew * (nq > 0 ? (nq + kQP - 1) / kQP * kQP : kQP));
+    const int qp = qp_of(ew);
+    L.qred = take(o, 8u * 2 * ew * (nq > 0 ? (nq + qp - 1) / qp * qp : qp));
     L.fb = take(o, 4u * (nb > 0 ? nb : 1));
     L.colgeo = take(o, 16u * BN);
     L.colpk = take(o, 4u * BN);
     // phase weights of one pass, double buffered: columns (BN) and rows (128) of the tile
-    L.colcs = nq > 0 ? take(o, 2u * 8u * BN * kQP) : 0u;
-    L.rowcs = nq > 0 ? take(o, 2u * 8u * kBM * kQP) : 0u;
+    L.colcs = nq > 0 ? take(o, 2u * 8u * BN * qp) : 0u;
+    L.rowcs = nq > 0 ? take(o, 2u * 8u * kBM * qp) : 0u;
     L.boxred = take(o, 4u * ew * 12);
     L.var = take(o, vb);
     L.total = (o + 1023u) & ~1023u;
@@ -578,6 +581,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     constexpr int kEpiThreads = 32 * EW;
     constexpr int kBinStride = bin_stride(EW);
     constexpr int kHalves = EW / 4;
+    constexpr int kQP = qp_of(EW);
     constexpr bool kTF32 = FORM == ASD_TF32;
     constexpr int kPlanes = FORM == ASD_SPLIT_BF16 ? 2 : 1;
     constexpr uint32_t kABytes = kBM * SWB;
@@ -1108,9 +1112,11 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         }
                     }
                     // sum over the warp's 32 lanes by recursive halving: each exchange sends
-                    // the half of the q-values this lane does not keep; after three steps a
-                    // lane holds one q (set by lane bits 4..2), the last two add the rest
-                    auto warp_sum8 = [&](float (&z)[kQP]) {
+                    // the half of the q-values this lane does not keep; after log2(kQP)
+                    // steps a lane holds one q (set by its top lane bits), the remaining
+                    // exchanges add the lanes that hold the same q
+                    constexpr int kLanesPerQ = 32 / kQP;
+                    auto warp_sum = [&](float (&z)[kQP]) {
 #pragma unroll
                         for (int hh = kQP / 2, o = 16; hh >= 1; hh >>= 1, o >>= 1) {
                             const bool up = (lane & o) != 0;
@@ -1121,16 +1127,17 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                                 z[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                             }
                         }
-                        z[0] += __shfl_xor_sync(0xffffffffu, z[0], 2);
-                        z[0] += __shfl_xor_sync(0xffffffffu, z[0], 1);
+#pragma unroll
+                        for (int o = kLanesPerQ / 2; o >= 1; o >>= 1)
+                            z[0] += __shfl_xor_sync(0xffffffffu, z[0], o);
                     };
-                    const int qme = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                    const int qme = lane / kLanesPerQ;
                     double *slot = qred + ((pass * kEpiWarps + ew) * kQP + qme) * 2;
-                    warp_sum8(x);
-                    if ((lane & 3) == 0) slot[0] = (double)x[0];
+                    warp_sum(x);
+                    if (lane % kLanesPerQ == 0) slot[0] = (double)x[0];
                     if (E.q_parts == 2) {
-                        warp_sum8(y);
-                        if ((lane & 3) == 0) slot[1] = (double)y[0];
+                        warp_sum(y);
+                        if (lane % kLanesPerQ == 0) slot[1] = (double)y[0];
                     }
                 }
                 epi_sync(kEpiThreads);

@@ -363,8 +363,9 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         // (measured: sharing B by multicast does not pay here, so clusters are opt-in)
         p->CL = d->cluster ? d->cluster : 1;
         // epilogue warps: 4 by default (one launch of a batch needs one count).  8 warps
-        // (opt-in) cap the registers at 168: they help single-product BF16 binning with a
-        // short K on one large problem and lose with phase weights (measured)
+        // (opt-in, 4 q per phase pass) cap the registers at 168: measured, they help
+        // single-product BF16 binning with a short K on one large problem and bins + 64 q
+        // on the jittered glass by 3-4 %, and lose 4-7 % with bins alone there
         p->EW = d->epi_warps ? d->epi_warps : 4;
         // instantiated kernels: 256-wide tiles with either warp count; 128-wide tiles with
         // one CTA per cluster and 4 warps; clusters of 4 with 4 warps

@@ -28,16 +28,15 @@ DEFAULT_SPACE = {
 
 def candidates(space=None, n_q=0, N=None):
     """Valid combinations of the knobs (the plan's instantiated kernels): 128-wide tiles
-    run with 4 epilogue warps; 8 warps are skipped with phase weights (their 168-register
-    cap makes the phase loop spill); tiles wider than the problem are skipped."""
+    run with 4 epilogue warps; tiles wider than the problem are skipped.  `n_q` is kept
+    for callers: 8 epilogue warps are valid with phase weights too (their phase loop takes
+    4 q per pass and fits the 168-register cap)."""
     sp = dict(DEFAULT_SPACE if space is None else space)
     out = []
     keys = sorted(sp)
     for vals in itertools.product(*(sp[k] for k in keys)):
         c = dict(zip(keys, vals))
         if c.get("tile_n") == 128 and c.get("epi_warps", 4) != 4:
-            continue
-        if n_q > 0 and c.get("epi_warps", 4) == 8:
             continue
         if N is not None and c.get("tile_n") == 256 and N <= 128:
             continue

@@ -211,6 +211,35 @@ def test_phase_on_lattice_row_range(asd, form):
     assert_parity(got, ref, form, q=True)
 
 
+@pytest.mark.parametrize("form", ["split_bf16", "bf16", "tf32"])
+@pytest.mark.parametrize("sine", [False, True])
+def test_phase_eight_epilogue_warps(asd, form, sine):
+    """Eight epilogue warps (two per TMEM lane quarter, half the columns each; 4 q per
+    pass of the phase loop): 13 q (a partial last pass), bins at the same time, rows from
+    mid-tile, cosine and sine parts."""
+    lat = synth.hypercubic(9, 3, False, jitter=0.1, seed=5)
+    q = synth.q_vectors_glass()[::5]
+    tr = synth.traj_precess(lat.n_sites, 30, seed=9)
+    rows = (20, 700)
+    plan = asd.CorrPlan.for_lattice(lat, 30, 18, 7, 0.5, 16, precision=form, q=q,
+                                    phase_sine=sine, tile_n=256, epi_warps=8)
+    C = torch.zeros((7, 16), dtype=torch.float64, device="cuda")
+    Sq = torch.zeros((7, len(q), 2) if sine else (7, len(q)), dtype=torch.float64,
+                     device="cuda")
+    plan.run(torch.from_numpy(np.ascontiguousarray(tr[:, None])).cuda(), C, Sq, rows=rows)
+    assert asd.sync_status() == 0
+    plan.close()
+    ref = oracle.pair_corr(tr, 18, list(range(7)), oracle.Geometry.of_lattice(lat), 0.5, 16,
+                           q=q, rows=rows)
+    got = Sq.cpu().numpy()
+    cos_part = got[..., 0] if sine else got
+    scale = np.abs(ref["Sq_sum"]).max()
+    assert np.abs(cos_part - ref["Sq_sum"]).max() / scale <= 10 * TOL[form]
+    if sine:
+        assert np.abs(got[..., 1] - ref["Sq_im"]).max() / scale <= 10 * TOL[form]
+    assert oracle.bin_error(C.cpu().numpy(), ref).max() <= TOL[form]
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_phase_sine_part(asd, form):
     """Cosine and sine parts of Eq. 3's phase sum (jittered open cube, 13 q, rows from

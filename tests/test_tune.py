@@ -8,7 +8,8 @@ from paper_2308_07487_gb300 import synth, tune
 def test_candidates_respect_the_instantiated_kernels():
     cs = tune.candidates()
     assert cs and all(not (c["tile_n"] == 128 and c["epi_warps"] != 4) for c in cs)
-    assert {c["epi_warps"] for c in tune.candidates(n_q=8)} == {4}
+    # with phase weights both warp counts are instantiated without spills
+    assert {c["epi_warps"] for c in tune.candidates(n_q=8)} == {4, 8}
     assert all(c["tile_n"] == 128 for c in tune.candidates(N=100))
     # every combination appears once
     assert len({json.dumps(c, sort_keys=True) for c in cs}) == len(cs)
