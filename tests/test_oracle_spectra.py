@@ -27,6 +27,27 @@ def test_cosine_on_the_grid_peaks_with_closed_form_height():
     assert abs(grid[np.argmax(spec)] - w0) <= grid[1] - grid[0]
 
 
+def test_hann_window_of_a_constant_at_zero_frequency():
+    """S(t) = 1, w = 0: dt (1 + sum_{t=1}^{n-1} (1 + cos(pi t / n))) = dt n exactly, the
+    cosines cancelling in pairs t <-> n - t."""
+    for n in (7, 64, 301):
+        val = spectra.sq_omega(np.ones((n, 1)), 0.02, [0.0], kind="hann")[0, 0]
+        assert abs(val - 0.02 * n) < 1e-12 * n
+
+
+def test_gaussian_window_of_a_constant_is_a_gaussian_in_frequency():
+    """S(t) = 1 with the Gaussian window of width sigma = width * n_t (decayed long before
+    n_t): the transform is dt sum_{t in Z} exp(-t^2 / (2 sigma^2)) cos(w t dt), which by
+    Poisson summation is dt sigma sqrt(2 pi) exp(-sigma^2 (w dt)^2 / 2) for |w dt| < pi
+    (the aliased terms are below exp(-2 pi^2 sigma^2 (1 - |w dt| / pi)^2), i.e. zero here)."""
+    n, dt, width = 2000, 0.01, 0.05
+    sigma = width * n
+    omega = np.array([0.0, 0.5, 1.0, 2.0, 3.0])
+    got = spectra.sq_omega(np.ones((n, 1)), dt, omega, kind="gauss", width=width)[:, 0]
+    want = dt * sigma * np.sqrt(2 * np.pi) * np.exp(-0.5 * (sigma * omega * dt) ** 2)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
 def test_spin_wave_frequency_matches_linearised_ll():
     """A single plane-wave deviation on a 16^2 ferromagnet (J = -1, Hz = 0.5) integrated
     with the oracle's RK4 precesses at w(q) = Hz + 4 - 2 cos qx - 2 cos qy."""
