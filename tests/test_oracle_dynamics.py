@@ -76,7 +76,7 @@ def test_vmf_inverse_cdf_moments():
         assert abs(w.mean() - (1 / math.tanh(kappa) - 1 / kappa)) < 1e-4
 
 
-def _chain_bond_corr(proposal, T, J=1.0, n=64, sweeps=3000, seed=1):
+def _chain_bond_corr(proposal, T, J=1.0, n=64, sweeps=3000, seed=1, cone=0.0):
     lat = synth.open_chain(n, J=J)
     g = np.random.default_rng(seed)
     Y = synth.random_unit(n, seed)[None].astype(np.float64)
@@ -84,7 +84,7 @@ def _chain_bond_corr(proposal, T, J=1.0, n=64, sweeps=3000, seed=1):
     for sw in range(sweeps):
         u = g.random((1, n, 4))
         u[..., :2] = 1.0 - u[..., :2]  # (0, 1]
-        Y, _, _ = dyn.mc_sweep(Y, lat.nbr, lat.J, 0.0, T, u, lat.colors, proposal, cone=0.0)
+        Y, _, _ = dyn.mc_sweep(Y, lat.nbr, lat.J, 0.0, T, u, lat.colors, proposal, cone=cone)
         if sw >= 300:
             acc.append((Y[0, :-1] * Y[0, 1:]).sum(-1).mean())
     return float(np.mean(acc))
@@ -95,6 +95,17 @@ def test_open_chain_bond_correlation_metropolis():
     bJ = 1.0
     ref = -(1 / math.tanh(bJ) - 1 / bJ)
     got = _chain_bond_corr("metropolis", 1.0)
+    assert abs(got - ref) < 0.02, (got, ref)
+
+
+def test_open_chain_bond_correlation_cone_proposal():
+    """Metropolis with moves uniform on a cap of half-angle 0.8 about the current spin (a
+    symmetric proposal: its density depends only on the angle moved) samples the same
+    Boltzmann law: <S_i.S_i+1> = -(coth(bJ) - 1/(bJ)).  A cap centred anywhere but on the
+    current spin fails this."""
+    bJ = 1.0
+    ref = -(1 / math.tanh(bJ) - 1 / bJ)
+    got = _chain_bond_corr("metropolis", 1.0, cone=0.8, seed=3)
     assert abs(got - ref) < 0.02, (got, ref)
 
 
