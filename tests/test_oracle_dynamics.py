@@ -155,6 +155,29 @@ def test_field_is_the_gradient_of_eq1():
             assert abs(fd - h[0, i, a]) < 1e-6, (i, a, fd, h[0, i, a])
 
 
+def test_dm_chain_spiral_energy_and_pitch():
+    """Open chain along x with FM exchange J < 0 and DM vectors D z^ on the bonds i -> i+1
+    (-D z^ on i+1 -> i).  For the planar spiral S_k = (cos k theta, sin k theta, 0) each bond
+    contributes J cos theta - D sin theta (Eq. 1's -D_ij.(S_i x S_j) with S_i x S_i+1 =
+    sin theta z^), so the spiral of lowest energy has pitch atan(D / |J|), turning
+    counter-clockwise about z for D > 0 and clockwise for D < 0."""
+    n, J = 24, -1.0
+    lat = synth.open_chain(n, J=J)
+    thetas = np.linspace(-np.pi, np.pi, 3601)
+    for Dm in (0.6, -0.35):
+        Dv = np.zeros((n, 2, 3))
+        Dv[:-1, 0, 2] = Dm    # slot 0: bond i -> i + 1
+        Dv[1:, 1, 2] = -Dm    # slot 1: bond i + 1 -> i
+        k = np.arange(n)[None, :]
+        Y = np.stack([np.cos(k * thetas[:, None]), np.sin(k * thetas[:, None]),
+                      np.zeros((len(thetas), n))], axis=-1)
+        E = dyn.energy(Y, lat.nbr, lat.J, 0.0, Dv, 0.0)
+        np.testing.assert_allclose(E, (n - 1) * (J * np.cos(thetas) - Dm * np.sin(thetas)),
+                                   rtol=0, atol=1e-10)
+        best = thetas[np.argmin(E)]
+        assert abs(best - math.atan(Dm / abs(J))) <= thetas[1] - thetas[0]
+
+
 def test_anisotropy_precession_closed_form():
     """A single spin under -A (S^z)^2 only: h = -2 A S^z z^, so S^z is constant and the
     azimuth turns at -2 A S^z."""
