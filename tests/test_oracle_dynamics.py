@@ -1,6 +1,9 @@
 """Pins of the FP64 producer oracle (LL RK4, Monte Carlo) against closed forms and
 invariants: single-spin precession, the exchange dimer, total-spin conservation,
-energy conservation, the open-chain bond correlation -L(beta J), vMF moments."""
+energy conservation, the open-chain bond correlation -L(beta J) (uniform, cone and
+heat-bath proposals), vMF moments; for the DM and anisotropy terms of Eq. 1 the
+gradient of the energy, DM spiral energies and pitch, anisotropy precession, S^z
+conservation with DM along z, and the sampled <(S^z)^2> of an anisotropic spin."""
 import math
 
 import numpy as np
