@@ -144,6 +144,9 @@ int asd_pair_corr_counts(const asd_corr_plan *plan, int64_t *counts);
  * The caller zeroes them; row ranges therefore compose (the row split of the
  * paper's Section 3.5).  Either output may be NULL when its count is 0.
  * traj: device FP32 [N][S][F][3], 16-byte aligned.
+ * A plan owns one operand workspace and one work-item counter (the dynamic schedule):
+ * calls on one plan must not overlap on the GPU (issue them on one stream or order the
+ * streams); different plans are independent.
  */
 int asd_pair_corr(asd_corr_plan *plan, const float *traj, int64_t row_begin, int64_t row_end,
                   double *C_sum, double *Sq_sum, void *stream);
@@ -166,7 +169,11 @@ int asd_pair_corr_contract(asd_corr_plan *plan, int64_t row_begin, int64_t row_e
  * persistent launch over a flattened (problem, t, tile) work list.  All plans must
  * use the same tensor-core precision, tile width and cluster size.  Operand preparation
  * for every problem is enqueued first on the same stream.  Capturable into a CUDA
- * graph (no host synchronisation, no allocation).
+ * graph (no host synchronisation, no allocation) once the same batch has run eagerly:
+ * the work list and its counter live in the first plan (about 10 MB of device memory,
+ * allocated by its first batched call, never moved), so a captured graph stays valid
+ * until that plan leads a batch of other problems or is destroyed.  None of the plans
+ * may be in use by another call that can overlap on the GPU.
  */
 int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs, int n,
                           double *const *C_sum, double *const *Sq_sum, void *stream);

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/asd.h"
 
@@ -175,6 +176,11 @@ struct asd_corr_plan {
     // single-problem descriptor (tensor forms): host copy + device copy uploaded once
     asd::TcProblem *d_prob;
     asd::TcProblem *h_prob;
+    // work list of a batched launch whose first plan this is: device descriptors for
+    // kMaxProblems problems followed by the launch's work-item counter (allocated once, so
+    // a captured graph's pointer never dangles), and the host copy of the last upload
+    asd::TcProblem *batch_desc;
+    std::vector<asd::TcProblem> *batch_last;
     int stages;
     size_t smem_bytes;
     int CL;                    // cluster size (CTAs sharing a B tile)

@@ -247,6 +247,8 @@ void asd_pair_corr_plan_destroy(asd_corr_plan *p)
     cudaFree(p->counter);
     cudaFree(p->inv_counts);
     cudaFree(p->d_prob);
+    cudaFree(p->batch_desc);
+    delete p->batch_last;
     delete p->h_prob;
     delete[] p->counts_h;
     delete p;
@@ -689,12 +691,28 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
         if (smem < kMinSmem) smem = kMinSmem;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // Work list: built on the host every call, uploaded only when it differs from the
-    // previous upload of this thread (the first call for a batch may synchronise and
-    // allocate; repeated identical calls only enqueue kernels, so they can be captured).
-    static thread_local std::vector<TcProblem> last;
-    static thread_local TcProblem *dbuf = nullptr;
-    static thread_local int cap_n = 0;
+    // Work list: built on the host every call and kept in the first plan, uploaded only
+    // when it differs from that plan's previous upload (the first call for a batch may
+    // synchronise and allocate; repeated identical calls only enqueue kernels, so they
+    // can be captured, and a captured graph stays valid until its first plan leads a
+    // different batch or is destroyed).
+    asd_corr_plan *owner = plans[0];
+    if (!owner->batch_desc) {
+        // descriptors for the largest batch, then the work-item counter
+        if (cudaMalloc(&owner->batch_desc, sizeof(TcProblem) * kMaxProblems + 256) != cudaSuccess) {
+            cudaGetLastError();
+            owner->batch_desc = nullptr;
+            return ASD_ENOMEM;
+        }
+        owner->batch_last = new (std::nothrow) std::vector<TcProblem>();
+        if (!owner->batch_last) {
+            cudaFree(owner->batch_desc);
+            owner->batch_desc = nullptr;
+            return ASD_ENOMEM;
+        }
+    }
+    std::vector<TcProblem> &last = *owner->batch_last;
+    TcProblem *dbuf = owner->batch_desc;
     // The work list takes the problems largest first (longest-processing-time order):
     // measured on a mixed ensemble, this order matches the throughput of one launch per
     // problem, while the caller's order may interleave sizes and lose 10-15 %.  Each
@@ -727,17 +745,6 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     const bool same = last.size() == h.size() &&
                       memcmp(last.data(), h.data(), sizeof(TcProblem) * h.size()) == 0;
     if (!same) {
-        if (cap_n < n) {
-            cudaFree(dbuf);
-            dbuf = nullptr;
-            cap_n = 0;
-            // descriptors, then the work-item counter of the dynamic schedule
-            if (cudaMalloc(&dbuf, sizeof(TcProblem) * n + 256) != cudaSuccess) {
-                cudaGetLastError();
-                return ASD_ENOMEM;
-            }
-            cap_n = n;
-        }
         ASD_CUDA_TRY(cudaStreamSynchronize(s));
         ASD_CUDA_TRY(cudaMemcpy(dbuf, h.data(), sizeof(TcProblem) * n, cudaMemcpyHostToDevice));
         last = h;
@@ -751,7 +758,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     // counter lives behind the work list
     bool dyn = true;
     for (int k = 0; k < n; ++k) dyn = dyn && !plans[k]->d.static_schedule;
-    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(dbuf + cap_n);
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(dbuf + kMaxProblems);
     return launch_tc(dbuf, n, total, ov, p0->prec, p0->BN, p0->swizzle_bytes, stages, smem, vb,
                      max_nb, max_nq, p0->CL, p0->EW, p0->sm_count, dyn ? ctr : nullptr, s);
 }

@@ -84,3 +84,42 @@ def test_batched_graph_capture_replay(asd):
         np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=1e-9, atol=1e-9)
     for p in plans:
         p.close()
+
+
+def test_graph_survives_a_batch_led_by_another_plan(asd):
+    """The work list of a batched launch lives in its first plan: a larger batch led by
+    another plan, run between capture and replay, leaves the captured graph's work list
+    alone, and both batches match the oracle."""
+    ens_a, F, T0, n_t = _ensemble(n=3, seed=11)
+    ens_b, _, _, _ = _ensemble(n=7, seed=12)
+
+    def make(ens):
+        plans, trajs, Cs = [], [], []
+        for lat, tr, w, nb in ens:
+            plans.append(asd.CorrPlan.for_lattice(lat, F, T0, n_t, w, nb,
+                                                  precision="split_bf16", tile_n=128))
+            trajs.append(torch.from_numpy(np.ascontiguousarray(tr[:, None])).cuda())
+            Cs.append(torch.zeros((n_t, nb), dtype=torch.float64, device="cuda"))
+        return plans, trajs, Cs
+
+    pa, ta, ca = make(ens_a)
+    pb, tb, cb = make(ens_b)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        asd.pair_corr_batched(pa, ta, ca, stream=s)   # uploads batch A's work list
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for c in ca:
+            c.zero_()
+        asd.pair_corr_batched(pa, ta, ca, stream=s)
+    with torch.cuda.stream(s):
+        asd.pair_corr_batched(pb, tb, cb, stream=s)   # uploads batch B's work list
+    g.replay()
+    torch.cuda.synchronize()
+    assert asd.sync_status() == 0
+    for (lat, tr, w, nb), c in zip(ens_a + ens_b, ca + cb):
+        ref = oracle.pair_corr(tr, T0, list(range(n_t)), oracle.Geometry.of_lattice(lat), w, nb)
+        assert oracle.bin_error(c.cpu().numpy(), ref).max() <= 1e-5
+    for p in pa + pb:
+        p.close()
