@@ -244,10 +244,15 @@ class CorrPlan:
 
 
 def pair_corr_batched(plans, trajs, C_sums, Sq_sums=None, stream=None):
+    """asd_pair_corr_batched: every plan's problem in one persistent launch, accumulating
+    into C_sums[k] / Sq_sums[k] (device FP64; an entry may be None when its plan has no
+    bins / q-vectors, a whole list None when no plan has any).  Preparation is enqueued
+    on the same stream.  The work list lives in plans[0]: a CUDA graph captured from a
+    repeated call stays valid until plans[0] leads another batch or is closed."""
     n = len(plans)
     P = (_VP * n)(*[p.handle.value for p in plans])
     T = (_VP * n)(*[_ptr(t) for t in trajs])
-    C = (_VP * n)(*[_ptr(c) for c in C_sums])
+    C = (_VP * n)(*[_ptr(c) for c in C_sums]) if C_sums is not None else None
     Q = (_VP * n)(*[_ptr(q) for q in Sq_sums]) if Sq_sums is not None else None
     check(lib.asd_pair_corr_batched(P, T, n, C, Q, _stream(stream)), "pair_corr_batched")
 
