@@ -167,7 +167,6 @@ def oracle_sample(W, tr_np, rows, t_list):
 def run_reference(args, W, ws, rank):
     if rank != 0:
         return
-    import numpy as np
     from paper_2308_07487_gb300 import synth
     N = W["lat"].n_sites
     tr = synth.traj_precess(N, W["F"], seed=23082)
@@ -194,7 +193,6 @@ def run_reference(args, W, ws, rank):
                          "sample": sample},
         "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
-    np.asarray(0)
 
 
 # -------------------------------------------------------------------------------------
