@@ -167,7 +167,12 @@ def oracle_sample(W, tr_np, rows, t_list):
 def run_reference(args, W, ws, rank):
     if rank != 0:
         return
+    import oracle
     from paper_2308_07487_gb300 import synth
+    if ws > 1:
+        # the other ranks do no work: rank 0 takes every CPU of the process, as at one GPU
+        # (the launcher pins each rank to one OpenMP thread)
+        oracle.set_threads(len(os.sched_getaffinity(0)))
     N = W["lat"].n_sites
     tr = synth.traj_precess(N, W["F"], seed=23082)
     rows, t_list = (0, 8), [0, W["n_t"] // 2, W["n_t"] - 1]
@@ -182,7 +187,7 @@ def run_reference(args, W, ws, rank):
         times.append(dt)
     t = max(times)
     v = flops / t / 1e12
-    cores = os.cpu_count()
+    cores = oracle.threads()
     sample = f"rows {rows[0]}..{rows[1]} x all {N} columns x t in {t_list} (K = {3 * W['T0']})"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
@@ -199,7 +204,6 @@ def run_reference(args, W, ws, rank):
 # our arm
 # -------------------------------------------------------------------------------------
 def run_ours(args, W, ws, rank, local):
-    import numpy as np
     import torch
 
     from paper_2308_07487_gb300 import asd, synth
@@ -304,7 +308,7 @@ def run_ours(args, W, ws, rank, local):
            # contraction, normalisation (the memset of C_sum is torch's)
            "gpu_launches": args.steps * (1 + 4 * (F - 1) + (1 if args.form == "fp32" else 2) + 1 + 1)}
 
-    # ---- extras: other forms on a sample, CPU oracle baseline + parity, e2e ----
+    # ---- extras: other forms on a sample, CPU oracle baseline + parity (rank 0) ----
     if not args.no_extras and rank == 0:
         nt_s = min(8, n_t)
         tr_np = None
@@ -365,30 +369,35 @@ def run_ours(args, W, ws, rank, local):
                        f"{N * N * 4 / 1e9:.1f} GB per displacement")
         out["unfused_cublas"] = unf
 
-        # CPU oracle on rows 0..R (about 10-15 s on 16 host cores), three displacements, and
-        # the per-bin error of the timed form on the same rows
-        rows = (0, 256)
-        t_list = [0, n_t // 2, n_t - 1]
-        tr_np = traj.cpu().numpy()
-        res, dt, fl = oracle_sample(W, tr_np, rows, t_list)
-        import oracle
-        cs = torch.zeros((n_t, nb), dtype=torch.float64, device=dev)
-        plan.prepare(traj, rows=rows, stream=stream)
-        plan.contract(cs, rows=rows, stream=stream)
-        torch.cuda.synchronize()
-        err = oracle.bin_error(cs.cpu().numpy()[t_list], res).max()
-        out["cpu_baseline"] = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
-                               "kind": "oracle",
-                               "sample": f"rows {rows[0]}..{rows[1]} x {N} columns x t {t_list}, "
-                                         f"K={K}, {dt:.1f} s"}
-        out["max_bin_err"] = float(err)
+        # the oracle baseline is timed at one GPU only
+        if ws == 1:
+            # CPU oracle on rows 0..R (about 10-15 s on 16 host cores), three displacements, and
+            # the per-bin error of the timed form on the same rows
+            rows = (0, 256)
+            t_list = [0, n_t // 2, n_t - 1]
+            tr_np = traj.cpu().numpy()
+            res, dt, fl = oracle_sample(W, tr_np, rows, t_list)
+            import oracle
+            cs = torch.zeros((n_t, nb), dtype=torch.float64, device=dev)
+            plan.prepare(traj, rows=rows, stream=stream)
+            plan.contract(cs, rows=rows, stream=stream)
+            torch.cuda.synchronize()
+            err = oracle.bin_error(cs.cpu().numpy()[t_list], res).max()
+            out["cpu_baseline"] = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.threads(),
+                                   "kind": "oracle",
+                                   "sample": f"rows {rows[0]}..{rows[1]} x {N} columns x t {t_list}, "
+                                             f"K={K}, {dt:.1f} s"}
+            out["max_bin_err"] = float(err)
 
-        # e2e through the public API: pinned host spins -> device, full step, C -> host
+    if not args.no_extras:
+        # e2e through the public API on every rank: pinned host spins -> device, full step,
+        # C -> host; the job's time is the slowest rank's
         h_in = torch.from_numpy(spins0.cpu().numpy()).pin_memory()
         h_out = torch.empty((n_t, nb), dtype=torch.float64).pin_memory()
-        torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
+        barrier(ws)
+        torch.cuda.synchronize()
         with Clocks(local) as clk_e2e, torch.cuda.stream(stream):
             t0 = time.perf_counter()
             a.record(stream)
@@ -399,14 +408,15 @@ def run_ours(args, W, ws, rank, local):
             b.record(stream)
             torch.cuda.synchronize()
             wall = (time.perf_counter() - t0) / args.steps
-        te = a.elapsed_time(b) / 1e3 / args.steps
+        barrier(ws)
+        te = allmax(ws, a.elapsed_time(b) / 1e3 / args.steps)
+        wall = allmax(ws, wall)
         # (a separate run of the same steps: its SM clock under the power cap is recorded,
         # since it can differ from the clock of the device-timed run)
-        out["e2e"] = {"value": flops_step / te / 1e12, "unit": "TFLOP/s",
+        out["e2e"] = {"value": flops_step * ws / te / 1e12, "unit": "TFLOP/s",
                       "h2d_bytes_per_step": int(h_in.numel() * 4),
                       "d2h_bytes_per_step": int(h_out.numel() * 8),
                       "wall_s_per_step": wall, "clocks": clk_e2e.summary()}
-        _ = np
     if rank == 0:
         print(json.dumps(out))
     plan.close()

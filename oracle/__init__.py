@@ -63,10 +63,24 @@ def _load():
                                                ctypes.c_double, i64, i64, i64, i64p]
             lib.oracle_bin_of_d2.restype = ctypes.c_int
             lib.oracle_bin_of_d2.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.oracle_threads.restype = ctypes.c_int
+            lib.oracle_threads.argtypes = []
+            lib.oracle_set_threads.restype = None
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
             lib.oracle_pair_d2.restype = ctypes.c_double
             lib.oracle_pair_d2.argtypes = [ctypes.c_int, i64, i64, i32p, i32p, ctypes.c_int, f32p]
             _lib = lib
     return _lib
+
+
+def threads() -> int:
+    """Threads the oracle's parallel loops use (for reporting a timing's core count)."""
+    return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's following parallel loops."""
+    _load().oracle_set_threads(int(n))
 
 
 def _p(a, ct):

@@ -42,6 +42,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* smallest k >= 0 with ((k+1) w)^2 > d2, i.e. the largest k with (k w)^2 <= d2 */
 static int64_t bin_of_d2(double d2, double w)
@@ -82,6 +85,27 @@ static double pair_d2(int geom, int64_t i, int64_t j, const int32_t *coords,
 }
 
 int oracle_bin_of_d2(double d2, double w) { return (int)bin_of_d2(d2, w); }
+
+/* Threads of the next parallel loop (OMP_NUM_THREADS, else the CPUs this process may
+ * run on): the core count a timing of the oracle reports. */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Sets the threads of the following parallel loops (n >= 1). */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
 
 double oracle_pair_d2(int geom, int64_t i, int64_t j, const int32_t *coords,
                       const int32_t *L, int periodic, const float *pos)
