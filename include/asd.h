@@ -29,7 +29,7 @@
 extern "C" {
 #endif
 
-#define ASD_ABI_VERSION 1
+#define ASD_ABI_VERSION 2
 
 enum asd_status {
     ASD_OK = 0,
@@ -99,18 +99,15 @@ typedef struct asd_corr_desc {
                                (1..256): each starts from zero, which bounds the
                                tensor-core FP32 accumulation error; the epilogue bins each
                                one (FP32 within a tile, FP64 across tiles)               */
-    int32_t cluster;        /* 0 = automatic, 1, or 4: CTAs sharing one B tile via TMA
-                               multicast                                                 */
     int32_t epi_warps;      /* 0 = automatic (4), 4 or 8 epilogue warps per CTA (8 needs
-                               tile_n 256 and cluster 1; its phase loop takes 4 q per
-                               pass instead of 8)                                        */
+                               tile_n 256; its phase loop takes 4 q per pass instead
+                               of 8)                                                     */
     int32_t phase_sine;     /* 0: Sq_sum[t][q] holds the cosine part of Eq. 3's phase sum;
                                1: Sq_sum[t][q][2] holds (cosine, sine) parts, the sine
                                part sum_ij sin(q.(r_i - r_j)) G_ij(t) (Eq. 3's imaginary
                                part is its negative)                                     */
     int32_t static_schedule;/* 0: work items claimed from a global counter (dynamic,
-                               the default; clusters always run static); 1: static
-                               round-robin order                                         */
+                               the default); 1: static round-robin order                 */
 } asd_corr_desc;
 
 typedef struct asd_corr_plan asd_corr_plan;
@@ -167,7 +164,7 @@ int asd_pair_corr_contract(asd_corr_plan *plan, int64_t row_begin, int64_t row_e
 /*
  * Several independent problems (each its own plan, trajectory and outputs) in ONE
  * persistent launch over a flattened (problem, t, tile) work list.  All plans must
- * use the same tensor-core precision, tile width and cluster size.  Operand preparation
+ * use the same tensor-core precision, tile width and epilogue warp count.  Operand preparation
  * for every problem is enqueued first on the same stream.  Capturable into a CUDA
  * graph (no host synchronisation, no allocation) once the same batch has run eagerly:
  * the work list and its counter live in the first plan (about 10 MB of device memory,

@@ -39,9 +39,8 @@ class asd_corr_desc(ctypes.Structure):
                 ("bin_width", ctypes.c_double), ("n_bins", ctypes.c_int32),
                 ("n_q", ctypes.c_int32), ("q", c_f64p), ("tile_n", ctypes.c_int32),
                 ("raster_m", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("k_chunks", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("epi_warps", ctypes.c_int32), ("phase_sine", ctypes.c_int32),
-                ("static_schedule", ctypes.c_int32)]
+                ("k_chunks", ctypes.c_int32), ("epi_warps", ctypes.c_int32),
+                ("phase_sine", ctypes.c_int32), ("static_schedule", ctypes.c_int32)]
 
 
 class asd_system(ctypes.Structure):
@@ -143,7 +142,7 @@ class CorrPlan:
 
     def __init__(self, N, F, T0, n_t, precision="split_bf16", S=1, center=False, coords=None,
                  L=(1, 1, 1), periodic=False, pos=None, bin_width=1.0, n_bins=0, q=None,
-                 tile_n=0, raster_m=0, stages=0, k_chunks=0, cluster=0, epi_warps=0,
+                 tile_n=0, raster_m=0, stages=0, k_chunks=0, epi_warps=0,
                  phase_sine=False, static_schedule=False):
         d = asd_corr_desc()
         d.n_sites, d.n_frames, d.n_samples, d.T0, d.n_t = N, F, S, T0, n_t
@@ -174,7 +173,6 @@ class CorrPlan:
         d.raster_m = int(raster_m)
         d.stages = int(stages)
         d.k_chunks = int(k_chunks)
-        d.cluster = int(cluster)
         d.epi_warps = int(epi_warps)
         d.phase_sine = int(bool(phase_sine))
         d.static_schedule = int(bool(static_schedule))

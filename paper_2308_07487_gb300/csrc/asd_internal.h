@@ -128,7 +128,7 @@ struct TcLaunchArgs {
 };
 
 template <int FORM>
-int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int cl, int ew, int sm_count,
+int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int ew, int sm_count,
                    cudaStream_t s);
 
 }  // namespace asd
@@ -183,7 +183,6 @@ struct asd_corr_plan {
     std::vector<asd::TcProblem> *batch_last;
     int stages;
     size_t smem_bytes;
-    int CL;                    // cluster size (CTAs sharing a B tile)
     int EW;                    // epilogue warps (4 or 8)
     int k_chunks;
     // last asd_pair_corr_prepare
@@ -203,12 +202,12 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
 int tc_configure(asd_corr_plan *p);    // stages / smem for the plan's form
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
               int BN, int swizzle_bytes, int stages, size_t smem, uint32_t var_bytes,
-              int max_nb, int max_nq, int cl, int ew, int sm_count, unsigned long long *counter,
+              int max_nb, int max_nq, int ew, int sm_count, unsigned long long *counter,
               cudaStream_t s);
-// work items of one problem: n_t * k_chunks * ceil(tiles_m / cl) * tiles_n
-inline int64_t tc_work_items(int n_t, int k_chunks, int tiles_m, int tiles_n, int cl)
+// work items of one problem: n_t * k_chunks * tiles_m * tiles_n
+inline int64_t tc_work_items(int n_t, int k_chunks, int tiles_m, int tiles_n)
 {
-    return (int64_t)n_t * k_chunks * ((tiles_m + cl - 1) / cl) * tiles_n;
+    return (int64_t)n_t * k_chunks * tiles_m * tiles_n;
 }
 size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut, int ew);
 // bytes of the per-problem epilogue region (private bins + bin table)

@@ -6,12 +6,12 @@
 namespace asd {
 
 // instantiated in the per-form translation units
-extern template int tc_launch_form<ASD_BF16>(const TcLaunchArgs &, size_t, int, int, int, int,
+extern template int tc_launch_form<ASD_BF16>(const TcLaunchArgs &, size_t, int, int, int,
                                              cudaStream_t);
-extern template int tc_launch_form<ASD_TF32>(const TcLaunchArgs &, size_t, int, int, int, int,
+extern template int tc_launch_form<ASD_TF32>(const TcLaunchArgs &, size_t, int, int, int,
                                              cudaStream_t);
 extern template int tc_launch_form<ASD_SPLIT_BF16>(const TcLaunchArgs &, size_t, int, int, int,
-                                                   int, cudaStream_t);
+                                                   cudaStream_t);
 
 uint32_t tc_var_bytes(int NW, int n_bins, int n_lut, int ew) { return var_bytes(NW, n_bins, n_lut, ew); }
 
@@ -80,7 +80,7 @@ int tc_configure(asd_corr_plan *p)
 
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
               int BN, int swizzle_bytes, int stages, size_t smem, uint32_t var_bytes_,
-              int max_nb, int max_nq, int cl, int ew, int sm_count, unsigned long long *counter,
+              int max_nb, int max_nq, int ew, int sm_count, unsigned long long *counter,
               cudaStream_t s)
 {
     if (total_tiles <= 0) return ASD_OK;
@@ -92,7 +92,7 @@ int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOver
     a.stages = stages;
     a.VB = var_bytes_;
     // dynamic schedule: the counter starts at zero for every launch (stream-ordered)
-    a.counter = cl == 1 ? counter : nullptr;
+    a.counter = counter;
     if (a.counter) ASD_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s));
     a.NB = max_nb;
     a.NQ = max_nq;
@@ -100,9 +100,9 @@ int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOver
     if (!a.err) return ASD_ECUDA;
     (void)swizzle_bytes;
     switch (prec) {
-    case ASD_BF16: return tc_launch_form<ASD_BF16>(a, smem, BN, cl, ew, sm_count, s);
-    case ASD_TF32: return tc_launch_form<ASD_TF32>(a, smem, BN, cl, ew, sm_count, s);
-    case ASD_SPLIT_BF16: return tc_launch_form<ASD_SPLIT_BF16>(a, smem, BN, cl, ew, sm_count, s);
+    case ASD_BF16: return tc_launch_form<ASD_BF16>(a, smem, BN, ew, sm_count, s);
+    case ASD_TF32: return tc_launch_form<ASD_TF32>(a, smem, BN, ew, sm_count, s);
+    case ASD_SPLIT_BF16: return tc_launch_form<ASD_SPLIT_BF16>(a, smem, BN, ew, sm_count, s);
     default: return ASD_EINVAL;
     }
 }

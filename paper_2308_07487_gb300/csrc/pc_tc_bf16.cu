@@ -2,5 +2,5 @@
 #include "pc_tc_kernel.cuh"
 
 namespace asd {
-template int tc_launch_form<ASD_BF16>(const TcLaunchArgs &, size_t, int, int, int, int, cudaStream_t);
+template int tc_launch_form<ASD_BF16>(const TcLaunchArgs &, size_t, int, int, int, cudaStream_t);
 }  // namespace asd

@@ -53,7 +53,7 @@ constexpr unsigned long long kTimeoutNs = 4000000000ull;
 // through a ring of kWQ slots in shared memory.  With the dynamic schedule the TMA thread
 // claims each item from a global counter, so the items in flight across the grid stay
 // together whatever each item costs (L2 reuse of A / B panels, no drift, balanced tail);
-// the static schedule takes items cid, cid + n_clusters, ... (clusters use it).
+// the static schedule takes items cid, cid + gridDim.x, ...
 constexpr int kWQ = 4;
 // Private bins are a [bin][128 * EW/4] array: epilogue thread (row r, column half h)
 // only ever touches column r + 128 h, i.e. bank r mod 32, so the per-pair accumulation
@@ -136,31 +136,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// Multicast variant: the box lands at the same shared-memory offset (and signals the
-// mbarrier at the same offset) in every CTA of `mask` within the cluster.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                               int x, int y, uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                     : "memory");
-}
-
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_slot, uint32_t ncols)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_slot),
@@ -182,17 +157,6 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
-}
-
-// Arrive (when this thread's MMAs complete) on the mbarrier at offset `bar` in every CTA
-// of `mask`.
-__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar),
-        "h"(mask)
-        : "memory");
 }
 
 template <bool TF32>
@@ -403,10 +367,8 @@ struct TileInfo {
     int kg0, kg1;  // K blocks [kg0, kg1) of the S * nkb blocks of a full row
 };
 
-// Work item `tau` -> (problem, t, K chunk, row tile, column tile).  With clusters of CL
-// CTAs, a work item is a cluster tile: CL consecutive row tiles that share one column
-// tile; CTA `rank` of the cluster takes row tile mc * CL + rank.  K chunks split the
-// contraction so that each partial accumulator starts from zero (see kChunkK).
+// Work item `tau` -> (problem, t, K chunk, row tile, column tile).  K chunks split the
+// contraction so that each partial accumulator starts from zero.
 // Per-role walk over the work list.  A role visits its work items in increasing order,
 // so the problem of the next item is found by stepping forward from the current one, and
 // the fields that decoding needs stay in registers until the problem changes (a batched
@@ -414,14 +376,13 @@ struct TileInfo {
 struct WorkCursor {
     int p = -1;
     int64_t begin = 0, end = 0;  // flattened items [begin, end) belong to problem p
-    int tiles_mc, tiles_n, kch, G, nk, row_begin, row_end;
+    int tiles_m, tiles_n, kch, G, nk, row_begin, row_end;
     int64_t per_kc;
 };
 
-template <int CL>
 __device__ __forceinline__ TileInfo decode(WorkCursor &cu, const TcProblem *__restrict__ probs,
                                            int n_probs, const TcOverride &ov, int64_t tau,
-                                           int BN, int rank)
+                                           int BN)
 {
     if (cu.p < 0 || tau >= cu.end) {
         int p = cu.p < 0 ? 0 : cu.p;
@@ -443,14 +404,14 @@ __device__ __forceinline__ TileInfo decode(WorkCursor &cu, const TcProblem *__re
         const int tiles_m = ov.active ? ov.tiles_m : P.tiles_m;
         cu.begin = ov.active ? 0 : P.tile_begin;
         cu.end = cu.begin + (ov.active ? ov.n_tiles : P.n_tiles);
-        cu.tiles_mc = (tiles_m + CL - 1) / CL;
+        cu.tiles_m = tiles_m;
         cu.tiles_n = P.tiles_n;
         cu.kch = P.k_chunks;
-        cu.G = max(1, P.group_m / CL);
+        cu.G = max(1, P.group_m);
         cu.nk = P.S * P.nkb;
         cu.row_begin = ov.active ? ov.row_begin : P.row_begin;
         cu.row_end = ov.active ? ov.row_end : P.row_end;
-        cu.per_kc = (int64_t)cu.tiles_mc * cu.tiles_n;
+        cu.per_kc = (int64_t)cu.tiles_m * cu.tiles_n;
     }
     const int64_t l = tau - cu.begin;
     TileInfo ti;
@@ -461,9 +422,9 @@ __device__ __forceinline__ TileInfo decode(WorkCursor &cu, const TcProblem *__re
     const int64_t rem = rem0 % cu.per_kc;
     const int64_t gspan = (int64_t)cu.G * cu.tiles_n;
     const int first_m = (int)(rem / gspan) * cu.G;
-    const int gsz = min(cu.G, cu.tiles_mc - first_m);
+    const int gsz = min(cu.G, cu.tiles_m - first_m);
     const int64_t r2 = rem % gspan;
-    ti.m0 = cu.row_begin + ((first_m + (int)(r2 % gsz)) * CL + rank) * kBM;
+    ti.m0 = cu.row_begin + (first_m + (int)(r2 % gsz)) * kBM;
     ti.n0 = (int)(r2 / gsz) * BN;
     ti.row_end = cu.row_end;
     ti.kg0 = (int)((int64_t)kc * cu.nk / cu.kch);
@@ -574,7 +535,7 @@ using LaunchArgs = TcLaunchArgs;
 // ------------------------------------------------------------------------------------
 // the kernel
 // ------------------------------------------------------------------------------------
-template <int FORM, int BN, int SWB, int CL, int EW>
+template <int FORM, int BN, int SWB, int EW>
 __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_constant__ LaunchArgs args)
 {
     constexpr int kEpiWarps = EW;
@@ -586,10 +547,6 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     constexpr int kPlanes = FORM == ASD_SPLIT_BF16 ? 2 : 1;
     constexpr uint32_t kABytes = kBM * SWB;
     constexpr uint32_t kBBytes = BN * SWB;
-    // With a cluster of CL CTAs (consecutive row tiles, one column tile), each CTA loads
-    // BN/CL rows of the B tile and multicasts them to every CTA of the cluster.
-    constexpr int kBSlice = BN / CL;
-    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
     constexpr uint32_t kStageBytes = kPlanes * (kABytes + kBBytes);
     constexpr int kKSteps = SWB / 32;          // one MMA k-step covers 32 bytes of K
     constexpr int kBK = SWB / (kTF32 ? 4 : 2); // K elements per stage
@@ -619,8 +576,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            // a stage is free again once the MMAs of every CTA of the cluster consumed it
-            mbar_init(empty0 + 8 * s, CL);
+            // a stage is free again once the MMAs that read it have completed
+            mbar_init(empty0 + 8 * s, 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
@@ -638,12 +595,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     tc_before();
     __syncthreads();
     tc_after();
-    // every CTA's barriers are initialised before any CTA multicasts into them
-    if (CL > 1) cluster_sync();
     const uint32_t tmem = *tmem_slot;
     const TcProblem *__restrict__ probs = args.probs;
-    const int rank = CL > 1 ? (int)cluster_rank() : 0;
-    const int64_t cid = blockIdx.x / CL, n_clusters = gridDim.x / CL;
+    const int64_t cid = blockIdx.x, n_ctas = gridDim.x;
 
     if (warp == 0) {
         // ======================= TMA producer =======================
@@ -660,14 +614,13 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     ok = false;
                     break;
                 }
-                int64_t tau = (CL == 1 && args.counter)
-                                  ? (int64_t)atomicAdd(args.counter, 1ull)
-                                  : cid + v * n_clusters;
+                int64_t tau = args.counter ? (int64_t)atomicAdd(args.counter, 1ull)
+                                           : cid + v * n_ctas;
                 if (tau >= args.total_tiles) tau = -1;
                 wq[qs] = tau;
                 mbar_arrive(wqfull0 + 8 * qs);  // release: the slot is visible to the waiters
                 if (tau < 0) break;
-                const TileInfo ti = decode<CL>(cu, probs, args.n_probs, args.ov, tau, BN, rank);
+                const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau, BN);
                 const TcProblem &P = probs[ti.p];
                 for (int kg = ti.kg0; kg < ti.kg1; ++kg) {
                     const int s = kg / P.nkb, kb = kg % P.nkb;
@@ -684,12 +637,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     for (int pl = 0; pl < kPlanes; ++pl) {
                         tma_load_2d(saddr(st + pl * kABytes), &P.mapA[pl][c], fb,
                                     xw - c + kb * kBK, ti.m0);
-                        const uint32_t bdst = saddr(st + kPlanes * kABytes + pl * kBBytes);
-                        if (CL == 1)
-                            tma_load_2d(bdst, &P.mapB[pl], fb, s * P.Kseg + kb * kBK, ti.n0);
-                        else
-                            tma_load_2d_mc(bdst + rank * kBSlice * SWB, &P.mapB[pl], fb,
-                                           s * P.Kseg + kb * kBK, ti.n0 + rank * kBSlice, kMask);
+                        tma_load_2d(saddr(st + kPlanes * kABytes + pl * kBBytes), &P.mapB[pl], fb,
+                                    s * P.Kseg + kb * kBK, ti.n0);
                     }
                     if (++stage == stages) {
                         stage = 0;
@@ -725,7 +674,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 const int64_t tau = wq[qs];
                 mbar_arrive(wqempty0 + 8 * qs);
                 if (tau < 0) break;
-                const TileInfo ti = decode<CL>(cu, probs, args.n_probs, args.ov, tau, BN, rank);
+                const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau, BN);
                 const uint32_t acc = v & 1, use = v >> 1;
                 if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, args.err, DEV_TIMEOUT_MMA)) {
                     ok = false;
@@ -757,8 +706,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                             tc_mma<false>(d, a1 + off, b0 + off, kIdesc, 1u);     // lo*hi
                         }
                     }
-                    if (CL == 1) tc_commit(empty0 + 8 * stage);
-                    else tc_commit_mc(empty0 + 8 * stage, kMask);
+                    tc_commit(empty0 + 8 * stage);
                     if (++stage == stages) {
                         stage = 0;
                         phase ^= 1;
@@ -860,12 +808,12 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             __syncwarp();
             if (lane == 0) mbar_arrive(wqempty0 + 8 * qs);
             if (tau < 0) break;
-            const TileInfo ti = decode<CL>(cu, probs, args.n_probs, args.ov, tau, BN, rank);
+            const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau, BN);
             const TcProblem &P = probs[ti.p];
             const EpiParams &E = P.epi;
             const int i = ti.m0 + r;
             const bool row_ok = i < ti.row_end;
-            // rows past the range (ragged tiles, or a cluster's surplus row tiles) read the
+            // rows past the range (ragged tiles) read the
             // geometry of a valid site and contribute zeros
             const int ic = row_ok ? i : P.N - 1;
             const bool lattice = E.geom == ASD_GEOM_LATTICE;
@@ -1192,71 +1140,34 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         tc_after();
         tmem_dealloc(tmem, kTmemCols);
     }
-    // no CTA leaves while a peer may still multicast into its shared memory or arrive on
-    // its barriers (each CTA drained its own copies and MMAs above)
-    if (CL > 1) {
-        __syncwarp();
-        cluster_sync();
-    }
 }
 
-template <int FORM, int BN, int SWB, int CL, int EW>
-int launch_cl(const LaunchArgs &a, size_t smem, int sm_count, cudaStream_t s)
+template <int FORM, int BN, int SWB, int EW>
+int launch_one(const LaunchArgs &a, size_t smem, int sm_count, cudaStream_t s)
 {
-    auto k = pc_tc_kernel<FORM, BN, SWB, CL, EW>;
+    auto k = pc_tc_kernel<FORM, BN, SWB, EW>;
     constexpr int kThreads = 64 + 32 * EW;
     ASD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if constexpr (CL == 1) {
-        const int grid = (int)(a.total_tiles < sm_count ? a.total_tiles : sm_count);
-        k<<<grid, kThreads, smem, s>>>(a);
-        ASD_CUDA_TRY(cudaGetLastError());
-        return ASD_OK;
-    } else {
-    ASD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
-    cudaLaunchConfig_t cfg{};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    // as many clusters as can be resident at once (one CTA per SM), no more than needed
-    cfg.gridDim = dim3((unsigned)(sm_count / CL * CL), 1, 1);
-    int max_clusters = 0;
-    ASD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&max_clusters, (void *)k, &cfg));
-    if (max_clusters < 1) {
-        set_error_text("no cluster of the tensor-core kernel fits on the device");
-        return ASD_EUNSUPPORTED;
-    }
-    const int64_t nc = a.total_tiles < max_clusters ? a.total_tiles : max_clusters;
-    cfg.gridDim = dim3((unsigned)(nc * CL), 1, 1);
-    ASD_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, a));
+    // persistent: one CTA per SM, no more CTAs than work items
+    const int grid = (int)(a.total_tiles < sm_count ? a.total_tiles : sm_count);
+    k<<<grid, kThreads, smem, s>>>(a);
+    ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;
-    }
 }
 
 }  // namespace
 
 // Launch one precision form.  Instantiated combinations (the rest are rejected):
-//   BN = 256: cluster 1 with 4 or 8 epilogue warps; cluster 4 with 4 warps;
-//   BN = 128: cluster 1 with 4 warps.
+//   BN = 256 with 4 or 8 epilogue warps; BN = 128 with 4 warps.
 template <int FORM>
-int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int cl, int ew, int sm_count,
+int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int ew, int sm_count,
                    cudaStream_t s)
 {
     constexpr int SWB = FORM == ASD_SPLIT_BF16 ? 64 : 128;
-    constexpr int EWD = 4;
-    if (BN == 256 && cl == 1 && ew == 4) return launch_cl<FORM, 256, SWB, 1, 4>(a, smem, sm_count, s);
-    if (BN == 256 && cl == 1 && ew == 8) return launch_cl<FORM, 256, SWB, 1, 8>(a, smem, sm_count, s);
-    if (BN == 256 && cl == 4 && ew == EWD)
-        return launch_cl<FORM, 256, SWB, 4, EWD>(a, smem, sm_count, s);
-    if (BN == 128 && cl == 1 && ew == EWD)
-        return launch_cl<FORM, 128, SWB, 1, EWD>(a, smem, sm_count, s);
-    set_error_text("tensor-core kernel: unsupported (tile width, cluster, epilogue warps)");
+    if (BN == 256 && ew == 4) return launch_one<FORM, 256, SWB, 4>(a, smem, sm_count, s);
+    if (BN == 256 && ew == 8) return launch_one<FORM, 256, SWB, 8>(a, smem, sm_count, s);
+    if (BN == 128 && ew == 4) return launch_one<FORM, 128, SWB, 4>(a, smem, sm_count, s);
+    set_error_text("tensor-core kernel: unsupported (tile width, epilogue warps)");
     return ASD_EUNSUPPORTED;
 }
 

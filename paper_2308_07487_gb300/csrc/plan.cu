@@ -165,7 +165,6 @@ static int encode_2d(CUtensorMap *m, void *base, int elem_bytes, uint64_t inner,
 static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int64_t row_end)
 {
     memset(tp, 0, sizeof(*tp));
-    const int box_rows_b = p->BN / p->CL;  // each CTA of a cluster loads a slice of B
     for (int pl = 0; pl < p->n_planes; ++pl) {
         for (int c = 0; c < p->n_copies; ++c) {
             int rc = encode_2d(&tp->mapA[pl][c], p->A[pl][c], p->elem_bytes, (uint64_t)p->Rpad,
@@ -173,7 +172,7 @@ static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int6
             if (rc) return rc;
         }
         int rc = encode_2d(&tp->mapB[pl], p->B[pl], p->elem_bytes, (uint64_t)p->Kb, (uint64_t)p->N,
-                           (uint32_t)p->BK, (uint32_t)box_rows_b, p->swizzle_bytes);
+                           (uint32_t)p->BK, (uint32_t)p->BN, p->swizzle_bytes);
         if (rc) return rc;
     }
     tp->N = (int)p->N;
@@ -189,7 +188,7 @@ static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int6
     tp->n_copies = p->n_copies;
     tp->group_m = p->d.raster_m > 0 ? p->d.raster_m : 16;
     tp->k_chunks = p->k_chunks;
-    tp->n_tiles = tc_work_items(p->n_t, p->k_chunks, tp->tiles_m, tp->tiles_n, p->CL);
+    tp->n_tiles = tc_work_items(p->n_t, p->k_chunks, tp->tiles_m, tp->tiles_n);
     tp->epi = epi_of(p);
     return ASD_OK;
 }
@@ -283,15 +282,12 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
     ASD_CHECK_ARG(d->raster_m >= 0 && d->raster_m <= 64, "raster_m: 0..64");
     ASD_CHECK_ARG(d->stages == 0 || (d->stages >= 2 && d->stages <= 8), "stages: 0 or 2..8");
     ASD_CHECK_ARG(d->k_chunks >= 0 && d->k_chunks <= 256, "k_chunks: 0..256");
-    ASD_CHECK_ARG(d->cluster == 0 || d->cluster == 1 || d->cluster == 4, "cluster: 0, 1 or 4");
     ASD_CHECK_ARG(d->epi_warps == 0 || d->epi_warps == 4 || d->epi_warps == 8, "epi_warps: 0, 4 or 8");
     {
-        // instantiated tensor-core kernels: 256-wide tiles with either warp count (cluster 4
-        // with 4 warps); 128-wide tiles with cluster 1 and 4 warps
+        // instantiated tensor-core kernels: 256-wide tiles with either warp count; 128-wide
+        // tiles with 4 warps
         const int ew = d->epi_warps ? d->epi_warps : 4;
-        ASD_CHECK_ARG(!(d->cluster == 4 && ew != 4), "cluster 4 runs with 4 epilogue warps");
-        ASD_CHECK_ARG(!(d->tile_n == 128 && (d->cluster == 4 || ew != 4)),
-                      "tile_n = 128 needs cluster 1 and 4 epilogue warps");
+        ASD_CHECK_ARG(!(d->tile_n == 128 && ew != 4), "tile_n = 128 needs 4 epilogue warps");
     }
     ASD_CHECK_ARG(d->static_schedule == 0 || d->static_schedule == 1, "static_schedule: 0 or 1");
     ASD_CHECK_ARG(d->phase_sine == 0 || d->phase_sine == 1, "phase_sine: 0 or 1");
@@ -360,19 +356,14 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         p->BN = d->tile_n ? d->tile_n : (p->N <= 4096 ? 128 : 256);
         p->Rpad = (R + 7) / 8 * 8;
         p->Kseg = ((int64_t)3 * d->T0 + p->BK - 1) / p->BK * p->BK;
-        // clusters of 4 row tiles share each B tile once there are enough row tiles
-        const int64_t tiles_m_all = (p->N + kBM - 1) / kBM;
-        // (measured: sharing B by multicast does not pay here, so clusters are opt-in)
-        p->CL = d->cluster ? d->cluster : 1;
         // epilogue warps: 4 by default (one launch of a batch needs one count).  8 warps
         // (opt-in, 4 q per phase pass) cap the registers at 168: measured, they help
         // single-product BF16 binning with a short K on one large problem and bins + 64 q
         // on the jittered glass by 3-4 %, and lose 4-7 % with bins alone there
         p->EW = d->epi_warps ? d->epi_warps : 4;
         // instantiated kernels: 256-wide tiles with either warp count; 128-wide tiles with
-        // one CTA per cluster and 4 warps; clusters of 4 with 4 warps
-        if (p->CL == 4 || p->EW != 4) p->BN = 256;  // combination checked up front
-        (void)tiles_m_all;
+        // 4 warps
+        if (p->EW != 4) p->BN = 256;  // combination checked up front
         // K chunks: split-BF16 is the FP32-accurate form; each chunk's accumulator starts
         // from zero, bounding the FP32 accumulation error of the tensor core to ~1536
         // terms per partial sum at any K (measured: 16 chunks of 6144 at K = 98304 leave
@@ -625,12 +616,12 @@ int asd_pair_corr_contract(asd_corr_plan *p, int64_t row_begin, int64_t row_end,
     ov.row_begin = (int)row_begin;
     ov.row_end = (int)row_end;
     ov.tiles_m = (int)((row_end - row_begin + kBM - 1) / kBM);
-    ov.n_tiles = tc_work_items(p->n_t, p->k_chunks, ov.tiles_m, p->h_prob->tiles_n, p->CL);
+    ov.n_tiles = tc_work_items(p->n_t, p->k_chunks, ov.tiles_m, p->h_prob->tiles_n);
     ov.C_sum = C_sum;
     ov.Sq_sum = Sq_sum;
     return launch_tc(p->d_prob, 1, ov.n_tiles, ov, p->prec, p->BN, p->swizzle_bytes, p->stages,
                      p->smem_bytes, tc_var_bytes(p->NW, p->n_bins, p->n_lut, p->EW), p->n_bins,
-                     p->n_q, p->CL, p->EW, p->sm_count,
+                     p->n_q, p->EW, p->sm_count,
                      p->d.static_schedule ? nullptr : p->counter, s);
 }
 
@@ -645,8 +636,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     for (int k = 0; k < n; ++k) {
         const asd_corr_plan *p = plans[k];
         ASD_CHECK_ARG(p && trajs[k], "null plan or trajectory");
-        ASD_CHECK_ARG(p->tc && p->prec == p0->prec && p->BN == p0->BN && p->CL == p0->CL &&
-                          p->EW == p0->EW,
+        ASD_CHECK_ARG(p->tc && p->prec == p0->prec && p->BN == p0->BN && p->EW == p0->EW,
                       "batched plans must share precision and tile width");
         ASD_CHECK_ARG(p->device == p0->device, "plans on different devices");
         ASD_CHECK_ARG(p->n_bins == 0 || (C_sum && C_sum[k]), "C_sum required");
@@ -722,7 +712,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     auto items = [&](int k) {
         const asd_corr_plan *p = plans[k];
         return tc_work_items(p->n_t, p->k_chunks, (int)((p->N + kBM - 1) / kBM),
-                             p->h_prob->tiles_n, p->CL);
+                             p->h_prob->tiles_n);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return items(a) > items(b); });
     std::vector<TcProblem> h((size_t)n);
@@ -735,7 +725,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
         hk.row_begin = 0;
         hk.row_end = (int)p->N;
         hk.tiles_m = (int)((p->N + kBM - 1) / kBM);
-        hk.n_tiles = tc_work_items(p->n_t, p->k_chunks, hk.tiles_m, hk.tiles_n, p->CL);
+        hk.n_tiles = tc_work_items(p->n_t, p->k_chunks, hk.tiles_m, hk.tiles_n);
         hk.tile_begin = total;
         hk.epi.n_lut = nlut[k];  // 0: the threshold rule (see above)
         hk.epi.C_sum = C_sum ? C_sum[k] : nullptr;
@@ -760,7 +750,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     for (int k = 0; k < n; ++k) dyn = dyn && !plans[k]->d.static_schedule;
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(dbuf + kMaxProblems);
     return launch_tc(dbuf, n, total, ov, p0->prec, p0->BN, p0->swizzle_bytes, stages, smem, vb,
-                     max_nb, max_nq, p0->CL, p0->EW, p0->sm_count, dyn ? ctr : nullptr, s);
+                     max_nb, max_nq, p0->EW, p0->sm_count, dyn ? ctr : nullptr, s);
 }
 
 int asd_pair_corr_normalize(const asd_corr_plan *p, const double *C_sum, const double *Sq_sum,

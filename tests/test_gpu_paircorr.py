@@ -152,18 +152,17 @@ def test_tile_widths_static_fm(asd, form, tile_n):
 
 
 @pytest.mark.parametrize("form", ["split_bf16", "bf16", "tf32"])
-@pytest.mark.parametrize("cluster,k_chunks", [(1, 1), (1, 3), (4, 1), (4, 4)])
-def test_cluster_and_k_chunks(asd, form, cluster, k_chunks):
-    """4-CTA clusters sharing B by multicast (9^3 = 729 sites: 6 row tiles, so the second
-    cluster has two surplus CTAs) and K split into partial accumulators; a row range
-    that starts mid-tile as well."""
+@pytest.mark.parametrize("k_chunks", [1, 3, 4])
+def test_k_chunks(asd, form, k_chunks):
+    """K split into partial accumulators (9^3 = 729 sites: 6 row tiles, the last ragged),
+    over all rows and over a row range that starts mid-tile."""
     lat = synth.hypercubic(9, 3, True)
     tr = synth.traj_precess(lat.n_sites, 70, seed=21, S=2)
     for rows in (None, (100, 700)):
         tr2 = np.ascontiguousarray(tr)
         N, S, F, _ = tr2.shape
         plan = asd.CorrPlan.for_lattice(lat, F, 40, 6, 0.5, 14, precision=form, S=S,
-                                        cluster=cluster, k_chunks=k_chunks)
+                                        k_chunks=k_chunks)
         d_tr = torch.from_numpy(tr2).cuda()
         C = torch.zeros((6, 14), dtype=torch.float64, device="cuda")
         plan.run(d_tr, C, rows=rows)
