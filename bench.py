@@ -608,7 +608,6 @@ def run_learned(args):
     import numpy as np
     import torch
 
-    from oracle import mlp as omlp
     from paper_2308_07487_gb300 import asd, synth
     L, T, S = 128, 0.7, 64
     lat = synth.hypercubic(L, 2, True, J=1.0)
@@ -630,7 +629,7 @@ def run_learned(args):
     X, Y = torch.cat(xs), torch.cat(ys)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
-    net = asd.Mlp(12, omlp.init(12, 5))
+    net = asd.Mlp(12, seed=5)
     gen = torch.Generator(device="cuda").manual_seed(0)
     B, steps = 16384, 1500
     t0 = time.perf_counter()

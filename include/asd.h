@@ -283,9 +283,10 @@ int asd_ll_integrate(const asd_system *sys, int n_samples, const float *spins0, 
  * exits).  Limit: n_sites * n_samples <= 262144; larger requests return ASD_EINVAL and
  * launch nothing.  The first call on each device looks up that array's device address
  * (a runtime query, no allocation), so make that first call before any stream capture
- * begins.  All calls share the one array: calls whose work can overlap on the GPU (on
- * different streams without ordering) race on it and give wrong results; calls on one
- * stream are safe.  Nothing in the array needs to start at zero: every buffer is fully
+ * begins.  The address is looked up again when the device's context has changed (after
+ * a cudaDeviceReset, for instance).  All calls share the one array: calls whose work can
+ * overlap on the GPU (on different streams without ordering) race on it and give wrong
+ * results; calls on one stream are safe.  Nothing in the array needs to start at zero: every buffer is fully
  * written before it is read.  Allocates nothing (no cudaMalloc, cudaMallocAsync or
  * cudaFree).
  */
@@ -340,6 +341,19 @@ int asd_thermalize(const asd_system *sys, int n_samples, float *spins, float T, 
  * ------------------------------------------------------------------------------- */
 int64_t asd_mlp_param_count(int n_in);
 int64_t asd_mlp_param_count_bf16(int n_in);
+
+/* Initial parameters (Glorot / Xavier uniform): every weight of a layer with fan_in inputs
+ * and fan_out outputs is drawn from U(-a, a), a = sqrt(6 / (fan_in + fan_out)), biases are
+ * zero.  One Philox4x32-10 draw per parameter (counter = its index in the parameter vector,
+ * key = seed), so the result depends on the seed only.  params device FP32 [P], written;
+ * w_bf16 device [asd_mlp_param_count_bf16] (nullable) receives the BF16 weight copy.
+ * Random initial weights break the symmetry between hidden units that an all-zero start
+ * keeps through training.  ASD_EINVAL for n_in outside 3..24. */
+int asd_mlp_init(float *params, int n_in, uint64_t seed, uint16_t *w_bf16, void *stream);
+
+/* BF16 weight copy [W1][W2][W3] of a parameter vector (round to nearest even), for an
+ * asd_mlp view of parameters set by the caller.  params device FP32 [P]; w_bf16 device. */
+int asd_mlp_weights_bf16(const float *params, int n_in, uint16_t *w_bf16, void *stream);
 
 /* Training pairs: for sample s and site i (k = s*N + i), x[k] = the z neighbour spins
  * (3z floats, zeros for empty slots) and y[k] = S_i.  spins device [S][N][3];

@@ -53,7 +53,7 @@ def _load():
             lib.oracle_pair_corr.argtypes = [i64, i64, i64, i64, i64, i32p, f32p, ctypes.c_int,
                                              i32p, i32p, ctypes.c_int, f32p, ctypes.c_double, i64,
                                              i64, f64p, ctypes.c_int, i64, i64, f64p, f64p, f64p,
-                                             f64p, f64p, i64p]
+                                             f64p, f64p, f64p, f64p, i64p]
             lib.oracle_pair_corr_eq4.restype = ctypes.c_int
             lib.oracle_pair_corr_eq4.argtypes = [i64, i64, i64, i64, i64, i32p, f32p, ctypes.c_int,
                                                  i32p, i32p, ctypes.c_int, f32p, ctypes.c_double,
@@ -119,9 +119,10 @@ def pair_corr(traj, T0, t_list, geometry: Geometry, w, n_bins, q=None, center=Fa
               rows=None):
     """Binned sums and phase sums of Eqs. 3-6 (see paircorr_ref.c).
 
-    traj [N][S][F][3] (or [N][F][3]) FP32.  Returns dict with C_sum, M_abs
-    [n_t][n_bins], Sq_sum (cosine part) and Sq_im (sine part) [n_t][n_q], counts
-    [n_bins] (int64), all over the rows `rows=(i0,i1)` (default all) and every column."""
+    traj [N][S][F][3] (or [N][F][3]) FP32.  Returns dict with C_sum, M_abs, P_abs
+    [n_t][n_bins], Sq_sum (cosine part), Sq_im (sine part) and their magnitude sums
+    Sq_abs, Sq_im_abs [n_t][n_q], counts [n_bins] (int64), all over the rows
+    `rows=(i0,i1)` (default all) and every column."""
     lib = _load()
     tr = np.asarray(traj, np.float32)
     if tr.ndim == 3:
@@ -138,6 +139,8 @@ def pair_corr(traj, T0, t_list, geometry: Geometry, w, n_bins, q=None, center=Fa
     P = np.zeros((n_tl, n_bins))
     Sq = np.zeros((n_tl, max(n_q, 1)))
     Sqi = np.zeros((n_tl, max(n_q, 1)))
+    Sqa = np.zeros((n_tl, max(n_q, 1)))
+    Sqia = np.zeros((n_tl, max(n_q, 1)))
     cnt = np.zeros(n_bins, np.int64)
     g = geometry
     rc = lib.oracle_pair_corr(N, F, S, T0, n_tl, _p(tl, ctypes.c_int32), _p(tr, ctypes.c_float),
@@ -146,12 +149,12 @@ def pair_corr(traj, T0, t_list, geometry: Geometry, w, n_bins, q=None, center=Fa
                               _p(qq, ctypes.c_double), int(bool(center)), i0, i1,
                               _p(C, ctypes.c_double), _p(M, ctypes.c_double),
                               _p(P, ctypes.c_double), _p(Sq, ctypes.c_double),
-                              _p(Sqi, ctypes.c_double),
-                              _p(cnt, ctypes.c_int64))
+                              _p(Sqi, ctypes.c_double), _p(Sqa, ctypes.c_double),
+                              _p(Sqia, ctypes.c_double), _p(cnt, ctypes.c_int64))
     if rc != 0:
         raise ValueError(f"oracle_pair_corr rejected its arguments (code {rc})")
     return {"C_sum": C, "M_abs": M, "P_abs": P, "Sq_sum": Sq[:, :n_q], "Sq_im": Sqi[:, :n_q],
-            "counts": cnt,
+            "Sq_abs": Sqa[:, :n_q], "Sq_im_abs": Sqia[:, :n_q], "counts": cnt,
             "N": N, "S": S, "T0": T0}
 
 
@@ -221,3 +224,12 @@ def bin_error(C_sum_test, res):
     ref, M = res["C_sum"], res["M_abs"]
     d = np.abs(np.asarray(C_sum_test, np.float64) - ref)
     return np.where(M > 0, d / np.where(M > 0, M, 1.0), d)
+
+
+def phase_error(Sq_test, res, part="cos"):
+    """Per-(t, q) error of a tested phase sum against the oracle, scaled by that q's
+    magnitude sum: |Sq_test - Sq_ref| / Sq_abs (cosine part) or against Sq_im with
+    Sq_im_abs (sine part).  Entries with a zero scale use the absolute error."""
+    ref, A = (res["Sq_sum"], res["Sq_abs"]) if part == "cos" else (res["Sq_im"], res["Sq_im_abs"])
+    d = np.abs(np.asarray(Sq_test, np.float64) - ref)
+    return np.where(A > 0, d / np.where(A > 0, A, 1.0), d)

@@ -28,8 +28,10 @@
  * Eq. 5).  The normalised correlation is C(b,t) = C_sum / (S*T0*counts).
  * Phase form:  Sq_sum[t][q] = sum_{i,j} cos(q.(r_i - r_j)) G_ij(t);
  *              S(q,t) = Sq_sum / (N*S*T0).
+ *              Sq_abs[t][q] = sum_{i,j} |cos(q.(r_i - r_j)) G_ij(t)|  (scale of that q's
+ *              sum, for errors: the phase-form counterpart of M_abs)
  * Sine part:   Sq_im[t][q]  = sum_{i,j} sin(q.(r_i - r_j)) G_ij(t)  (Eq. 3's imaginary
- *              part of e^{-iq.(r_i - r_j)} is minus this).
+ *              part of e^{-iq.(r_i - r_j)} is minus this); Sq_im_abs likewise.
  *
  * Distance bins.  bin(i,j) = max{k >= 0 : (k*w)^2 <= d2(i,j)}, dropped if >= n_bins.
  *   lattice geometry:   d2 = exact integer squared displacement of the integer
@@ -138,7 +140,7 @@ int oracle_pair_counts(int64_t N, int geom, const int32_t *coords, const int32_t
 /*
  * traj: [N][S][F][3] FP32.  t_list: n_tl displacements, each with t + T0 <= F.
  * Outputs (caller-allocated, overwritten): C_sum, M_abs [n_tl][n_bins];
- * Sq_sum, Sq_im [n_tl][n_q] (may be NULL); counts [n_bins] (may be NULL).
+ * Sq_sum, Sq_im, Sq_abs, Sq_im_abs [n_tl][n_q] (may be NULL); counts [n_bins] (may be NULL).
  * q: [n_q][3] FP64.  Phase positions are the integer coordinates (geom 0) or pos.
  */
 int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
@@ -148,7 +150,7 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
                      int64_t n_q, const double *q, int center,
                      int64_t row_begin, int64_t row_end,
                      double *C_sum, double *M_abs, double *P_abs, double *Sq_sum,
-                     double *Sq_im, int64_t *counts)
+                     double *Sq_im, double *Sq_abs, double *Sq_im_abs, int64_t *counts)
 {
     if (row_begin < 0 || row_end > N || row_begin > row_end) return -1;
     for (int64_t k = 0; k < n_tl; ++k)
@@ -160,6 +162,8 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
     if (P_abs) memset(P_abs, 0, sizeof(double) * (size_t)nc);
     if (Sq_sum) memset(Sq_sum, 0, sizeof(double) * (size_t)nq);
     if (Sq_im) memset(Sq_im, 0, sizeof(double) * (size_t)nq);
+    if (Sq_abs) memset(Sq_abs, 0, sizeof(double) * (size_t)nq);
+    if (Sq_im_abs) memset(Sq_im_abs, 0, sizeof(double) * (size_t)nq);
     if (counts) memset(counts, 0, sizeof(int64_t) * (size_t)n_bins);
 
 #define TR(i, s, f, a) ((double)traj[(((i) * S + (s)) * F + (f)) * 3 + (a)])
@@ -187,10 +191,14 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
         double *p_loc = (double *)calloc((size_t)nc, sizeof(double));
         double *q_loc = (double *)calloc((size_t)(nq > 0 ? nq : 1), sizeof(double));
         double *qs_loc = (double *)calloc((size_t)(nq > 0 ? nq : 1), sizeof(double));
+        double *qa_loc = (double *)calloc((size_t)(nq > 0 ? nq : 1), sizeof(double));
+        double *qsa_loc = (double *)calloc((size_t)(nq > 0 ? nq : 1), sizeof(double));
         int64_t *n_loc = (int64_t *)calloc((size_t)n_bins, sizeof(int64_t));
         double *ph = (double *)calloc((size_t)(n_q > 0 ? n_q : 1), sizeof(double));
         double *phs = (double *)calloc((size_t)(n_q > 0 ? n_q : 1), sizeof(double));
-        if (!c_loc || !m_loc || !p_loc || !q_loc || !qs_loc || !n_loc || !ph || !phs) err = 1;
+        if (!c_loc || !m_loc || !p_loc || !q_loc || !qs_loc || !qa_loc || !qsa_loc || !n_loc ||
+            !ph || !phs)
+            err = 1;
 #pragma omp for schedule(dynamic, 1)
         for (int64_t i = row_begin; i < row_end; ++i) {
             if (err) continue;
@@ -232,13 +240,15 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
                     for (int64_t iq = 0; iq < n_q; ++iq) {
                         q_loc[k * n_q + iq] += ph[iq] * g;
                         qs_loc[k * n_q + iq] += phs[iq] * g;
+                        qa_loc[k * n_q + iq] += fabs(ph[iq] * g);
+                        qsa_loc[k * n_q + iq] += fabs(phs[iq] * g);
                     }
                 }
             }
         }
 #pragma omp critical
         {
-            if (c_loc && m_loc && p_loc && q_loc && qs_loc && n_loc) {
+            if (c_loc && m_loc && p_loc && q_loc && qs_loc && qa_loc && qsa_loc && n_loc) {
                 for (int64_t x = 0; x < nc; ++x) {
                     C_sum[x] += c_loc[x];
                     M_abs[x] += m_loc[x];
@@ -246,10 +256,13 @@ int oracle_pair_corr(int64_t N, int64_t F, int64_t S, int64_t T0,
                 }
                 if (Sq_sum) for (int64_t x = 0; x < nq; ++x) Sq_sum[x] += q_loc[x];
                 if (Sq_im) for (int64_t x = 0; x < nq; ++x) Sq_im[x] += qs_loc[x];
+                if (Sq_abs) for (int64_t x = 0; x < nq; ++x) Sq_abs[x] += qa_loc[x];
+                if (Sq_im_abs) for (int64_t x = 0; x < nq; ++x) Sq_im_abs[x] += qsa_loc[x];
                 if (counts) for (int64_t b = 0; b < n_bins; ++b) counts[b] += n_loc[b];
             }
         }
-        free(c_loc); free(m_loc); free(p_loc); free(q_loc); free(qs_loc); free(n_loc);
+        free(c_loc); free(m_loc); free(p_loc); free(q_loc); free(qs_loc); free(qa_loc);
+        free(qsa_loc); free(n_loc);
         free(ph); free(phs);
     }
 #undef TR

@@ -90,6 +90,8 @@ _SIGS = {
                                       ctypes.c_uint64, _VP, ctypes.POINTER(asd_mc_stats), _VP]),
     "asd_mlp_param_count": (ctypes.c_int64, [ctypes.c_int]),
     "asd_mlp_param_count_bf16": (ctypes.c_int64, [ctypes.c_int]),
+    "asd_mlp_init": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, _VP, _VP]),
+    "asd_mlp_weights_bf16": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "asd_mlp_gather": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP, _VP, _VP, _VP]),
     "asd_mlp_loss_grad": (ctypes.c_int, [ctypes.POINTER(asd_mlp), ctypes.c_int64, _VP, _VP, _VP, _VP,
                                          _VP]),
@@ -277,24 +279,30 @@ def selftest_timeout(limit_ns, stream=None):
 
 class Mlp:
     """Learned-proposal network: FP32 master parameters, BF16 weight copy, Adam moments
-    (device tensors) and the asd_mlp view the sampler reads."""
+    (device tensors) and the asd_mlp view the sampler reads.  Without `params` the
+    library draws Glorot-uniform weights from `seed` (asd_mlp_init)."""
 
-    def __init__(self, n_in, params=None, device="cuda"):
+    def __init__(self, n_in, params=None, device="cuda", seed=0):
         import torch
         self.n_in = n_in
         P = lib.asd_mlp_param_count(n_in)
         Pw = lib.asd_mlp_param_count_bf16(n_in)
         self.P = P
-        p = np.zeros(P, np.float32) if params is None else np.asarray(params, np.float32)
-        assert p.shape == (P,)
-        self.params = torch.from_numpy(p.copy()).to(device)
         self.grad = torch.zeros(P, dtype=torch.float32, device=device)
         self.m = torch.zeros(P, dtype=torch.float32, device=device)
         self.v = torch.zeros(P, dtype=torch.float32, device=device)
         self.wb = torch.zeros(Pw, dtype=torch.bfloat16, device=device)
         self.loss = torch.zeros(1, dtype=torch.float64, device=device)
         self.step = 0
-        self._refresh_bf16()
+        if params is None:
+            self.params = torch.empty(P, dtype=torch.float32, device=device)
+            check(lib.asd_mlp_init(_ptr(self.params), n_in, int(seed), _ptr(self.wb), None),
+                  "mlp_init")
+        else:
+            p = np.asarray(params, np.float32)
+            assert p.shape == (P,)
+            self.params = torch.from_numpy(p.copy()).to(device)
+            self._refresh_bf16()
         H, es = 64, self.params.element_size()
         c = asd_mlp()
         c.n_in, c.n_hidden = n_in, H
@@ -307,12 +315,8 @@ class Mlp:
         self.c = c
 
     def _refresh_bf16(self):
-        import torch
-        H, n = 64, self.n_in
-        p = self.params
-        w = torch.cat([p[:H * n], p[H * n + H:H * n + H + H * H],
-                       p[H * n + 2 * H + H * H:H * n + 2 * H + H * H + 4 * H]])
-        self.wb.copy_(w.to(torch.bfloat16))
+        check(lib.asd_mlp_weights_bf16(_ptr(self.params), self.n_in, _ptr(self.wb), None),
+              "mlp_weights_bf16")
 
     def loss_grad(self, x, y, n=None, stream=None):
         n = x.shape[0] if n is None else n

@@ -176,11 +176,43 @@ constexpr int kLLStaticMaxDevices = 64;
 static __device__ __align__(256) float g_ll_scratch[4 * 3 * kLLStaticMaxSiteSamples];
 
 std::mutex g_ll_scratch_mu;
-float *g_ll_scratch_addr[kLLStaticMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id;  // context the address belongs to (0: not looked up)
+    float *addr;
+};
+ScratchSlot g_ll_scratch_slot[kLLStaticMaxDevices] = {};
 
-// Device address of g_ll_scratch on the current device, looked up once per device.
-// In host code the symbol itself is only a host-side stand-in; kernels must be given
-// this address.
+// Unique ID of the calling thread's current context (cuCtxGetId through the runtime's
+// driver entry point; no link against libcuda), or 0 when the query is unavailable.
+typedef CUresult (*PFN_ctxGetCurrent)(CUcontext *);
+typedef CUresult (*PFN_ctxGetId)(CUcontext, unsigned long long *);
+unsigned long long current_context_id()
+{
+    static PFN_ctxGetCurrent get_cur = nullptr;
+    static PFN_ctxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &a, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPoint("cuCtxGetId", &b, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_cur = reinterpret_cast<PFN_ctxGetCurrent>(a);
+            get_id = reinterpret_cast<PFN_ctxGetId>(b);
+        }
+    });
+    if (!get_cur || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_ll_scratch in the current context.  In host code the symbol itself
+// is only a host-side stand-in; kernels must be given this address.  It is looked up
+// once per device and again whenever the device's context has changed (after
+// cudaDeviceReset the module, and with it the array, lives at a new address).
 int ll_scratch_address(float **out)
 {
     int dev = 0;
@@ -189,13 +221,19 @@ int ll_scratch_address(float **out)
         set_error_text("asd_ll_integrate_noalloc: device index out of range");
         return ASD_EUNSUPPORTED;
     }
+    // (cudaGetDevice above leaves the device's primary context current for this thread
+    // once the runtime has initialised it; with no context to identify, id is 0 and the
+    // address is looked up on every call)
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lock(g_ll_scratch_mu);
-    if (!g_ll_scratch_addr[dev]) {
+    ScratchSlot &sl = g_ll_scratch_slot[dev];
+    if (!sl.addr || id == 0 || sl.ctx_id != id) {
         void *p = nullptr;
         ASD_CUDA_TRY(cudaGetSymbolAddress(&p, g_ll_scratch));
-        g_ll_scratch_addr[dev] = static_cast<float *>(p);
+        sl.addr = static_cast<float *>(p);
+        sl.ctx_id = id;
     }
-    *out = g_ll_scratch_addr[dev];
+    *out = sl.addr;
     return ASD_OK;
 }
 

@@ -18,6 +18,7 @@
 
 #include "asd_internal.h"
 #include "mlp.cuh"
+#include "philox.cuh"
 
 namespace asd {
 namespace {
@@ -180,6 +181,29 @@ __global__ void __launch_bounds__(kChunk) loss_grad_kernel(MlpView net, int64_t 
     }
 }
 
+// Position of parameter e of the packed vector [W1][b1][W2][b2][W3][b3] in the packed
+// BF16 weight buffer [W1][W2][W3]; -1 for biases.  *fan receives fan_in + fan_out of the
+// weight's layer.
+__device__ __forceinline__ int64_t weight_slot(int64_t e, int nin, int *fan)
+{
+    const int64_t ob1 = (int64_t)H * nin, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H,
+                  ob3 = oW3 + 4 * H;
+    if (e < ob1) {
+        *fan = nin + H;
+        return e;
+    }
+    if (e >= oW2 && e < ob2) {
+        *fan = H + H;
+        return (int64_t)H * nin + (e - oW2);
+    }
+    if (e >= oW3 && e < ob3) {
+        *fan = H + 4;
+        return (int64_t)H * nin + H * H + (e - oW3);
+    }
+    *fan = 0;
+    return -1;
+}
+
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float scale,
                             float *__restrict__ m, float *__restrict__ v, int64_t P, int nin,
                             float lr, float b1, float b2, float eps, float c1, float c2,
@@ -195,13 +219,38 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
     const float np = p[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
     p[e] = np;
     // packed BF16 weights [W1][W2][W3]; biases are skipped
-    const int64_t oW1 = 0, ob1 = (int64_t)H * nin, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H,
-                  ob3 = oW3 + 4 * H;
-    int64_t w = -1;
-    if (e < ob1) w = e - oW1;
-    else if (e >= oW2 && e < ob2) w = (int64_t)H * nin + (e - oW2);
-    else if (e >= oW3 && e < ob3) w = (int64_t)H * nin + H * H + (e - oW3);
+    int fan = 0;
+    const int64_t w = weight_slot(e, nin, &fan);
     if (w >= 0) wb[w] = __float2bfloat16_rn(np);
+}
+
+// Glorot-uniform weights (U(-a, a), a = sqrt(6 / (fan_in + fan_out))) from one Philox draw
+// per parameter (counter = its index, key = the seed), zero biases; the BF16 copy beside.
+__global__ void init_kernel(float *__restrict__ p, int64_t P, int nin, uint32_t k0, uint32_t k1,
+                            __nv_bfloat16 *__restrict__ wb)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= P) return;
+    int fan = 0;
+    const int64_t w = weight_slot(e, nin, &fan);
+    float v = 0.f;
+    if (w >= 0) {
+        const U4 r = philox4x32_10(U4{(uint32_t)e, (uint32_t)(e >> 32), 0x6D6C7069u, 0u}, k0, k1);
+        const float a = sqrtf(6.f / (float)fan);
+        v = a * (2.f * u01(r.x) - 1.f);
+    }
+    p[e] = v;
+    if (w >= 0 && wb) wb[w] = __float2bfloat16_rn(v);
+}
+
+__global__ void bf16_kernel(const float *__restrict__ p, int64_t P, int nin,
+                            __nv_bfloat16 *__restrict__ wb)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= P) return;
+    int fan = 0;
+    const int64_t w = weight_slot(e, nin, &fan);
+    if (w >= 0) wb[w] = __float2bfloat16_rn(p[e]);
 }
 
 }  // namespace
@@ -263,6 +312,29 @@ int asd_mlp_adam_step(float *params, const float *grad, float grad_scale, float 
     adam_kernel<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
         params, grad, grad_scale, m, v, P, n_in, lr, beta1, beta2, eps, c1, c2,
         reinterpret_cast<__nv_bfloat16 *>(w_bf16));
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}
+
+int asd_mlp_init(float *params, int n_in, uint64_t seed, uint16_t *w_bf16, void *stream)
+{
+    ASD_CHECK_ARG(params, "null argument");
+    ASD_CHECK_ARG(n_in >= 3 && n_in <= kMlpMaxIn, "bad n_in (3..24)");
+    const int64_t P = n_params(n_in);
+    init_kernel<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        params, P, n_in, (uint32_t)seed, (uint32_t)(seed >> 32),
+        reinterpret_cast<__nv_bfloat16 *>(w_bf16));
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}
+
+int asd_mlp_weights_bf16(const float *params, int n_in, uint16_t *w_bf16, void *stream)
+{
+    ASD_CHECK_ARG(params && w_bf16, "null argument");
+    ASD_CHECK_ARG(n_in >= 3 && n_in <= kMlpMaxIn, "bad n_in (3..24)");
+    const int64_t P = n_params(n_in);
+    bf16_kernel<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        params, P, n_in, reinterpret_cast<__nv_bfloat16 *>(w_bf16));
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;
 }

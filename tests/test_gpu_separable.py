@@ -81,7 +81,9 @@ def test_matches_fused_phase_epilogue(asd):
     plan.close()
     ref = oracle.pair_corr(tr, 24, list(range(9)), oracle.Geometry.of_lattice(lat), 0.5, 1, q=q)
     assert rel(sep, ref["Sq_sum"]) <= TOL
-    assert rel(Sq.cpu().numpy(), ref["Sq_sum"]) <= 1e-4
+    # the fused split-BF16 sums at the accuracy bar, per (t, q) in units of that q's
+    # magnitude sum
+    assert oracle.phase_error(Sq.cpu().numpy(), ref).max() <= 1e-5
 
 
 @pytest.mark.slow

@@ -35,8 +35,35 @@ def test_two_site_hand_computed():
     np.testing.assert_allclose(r["M_abs"], g["M_abs"], rtol=0, atol=1e-12)
     np.testing.assert_array_equal(r["counts"], g["counts"])
     np.testing.assert_allclose(r["Sq_sum"], g["Sq_sum"], rtol=0, atol=1e-12)
-    rc = oracle.pair_corr(traj, g["T0"], g["t_list"], geo, g["w"], g["n_bins"], center=True)
+    np.testing.assert_allclose(r["P_abs"], g["P_abs"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r["Sq_abs"], g["Sq_abs"], rtol=0, atol=1e-12)
+    rc = oracle.pair_corr(traj, g["T0"], g["t_list"], geo, g["w"], g["n_bins"], center=True,
+                          q=np.array(g["q"]))
     np.testing.assert_allclose(rc["C_sum"], g["C_sum_center"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(rc["M_abs"], g["M_abs_center"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(rc["P_abs"], g["P_abs_center"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(rc["Sq_sum"], g["Sq_sum_center"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(rc["Sq_abs"], g["Sq_abs_center"], rtol=0, atol=1e-12)
+
+
+def test_two_site_mixed_signs_hand_computed():
+    """Scales of the error metrics: M_abs = sum|G| (not |sum G|), P_abs = sum|A B| (not
+    sum|G|), Sq_abs = sum|cos G| per q and the sine part with its scale, on a case where
+    each of those differs from the quantity it could be mistaken for."""
+    g = _load("two_site_signs.json")
+    traj = np.array(g["traj"], np.float32)
+    r = oracle.pair_corr(traj, g["T0"], g["t_list"], _two_site_geom(), g["w"], g["n_bins"],
+                         q=np.array(g["q"]))
+    for k in ("C_sum", "M_abs", "P_abs", "Sq_sum", "Sq_abs", "Sq_im", "Sq_im_abs"):
+        np.testing.assert_allclose(r[k], g[k], rtol=0, atol=1e-12, err_msg=k)
+    np.testing.assert_array_equal(r["counts"], g["counts"])
+    # the error helpers divide by exactly these scales
+    bumped = r["C_sum"] + 0.3
+    np.testing.assert_allclose(oracle.bin_error(bumped, r)[1], 0.3 / np.array(g["M_abs"][1]))
+    np.testing.assert_allclose(oracle.rounding_ratio(bumped, r)[1], 0.3 / np.array(g["P_abs"][1]))
+    np.testing.assert_allclose(oracle.phase_error(r["Sq_sum"] + 0.7, r)[1],
+                               0.7 / np.array(g["Sq_abs"][1]))
+    np.testing.assert_allclose(oracle.phase_error(r["Sq_im"] + 0.2, r, "sin")[1, 0], 0.2 / 4)
 
 
 def test_bin_rule_golden():
