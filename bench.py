@@ -1,18 +1,25 @@
 #!/usr/bin/env python3
 """Benchmark of the fused pair-correlation hot path on GB300.
 
-Workload (the throughput configuration): 40^3 periodic simple-cubic Heisenberg lattice,
-N = 64000, J = +1, thermalised at T = 1.2 J (Metropolis, adaptive cone); LL RK4 with
-dt = 0.01 and F = 1200 frames; C(r,t) over T0 = 1000 origins, n_t = 200 displacements,
-70 shell bins of width 0.5.  Contraction per displacement: N x N x 3*T0.
+Default workload (the precision-sweep configuration): 64^3 = 262144 spins at simple-cubic
+positions with Gaussian jitter sigma = 0.1, open boundaries, +-J couplings (p = 0.5),
+thermalised at T = 1.0 J (Metropolis, adaptive cone); LL RK4 with dt = 0.01 and F = 640
+frames; C(r,t) over T0 = 512 origins in 256 distance bins of width 0.5 plus S(q,t) for 64
+q-vectors (cos(q.r_ij) weights), 128 displacements.  Contraction per displacement:
+N x N x 3*T0 (K = 1536), about 2.1e14 flops.
 
-One step = the hot path on one batch: LL trajectory from the resident thermalised spins
-(asd_ll_integrate), operand preparation + fused contraction/binning (asd_pair_corr in
-split-BF16) and normalisation (asd_pair_corr_normalize).
-Metric: algorithmic contraction TFLOP/s = n_t * 2 N^2 (3 T0) / step time.
+One step = the hot path on one batch: the LL trajectory from the resident thermalised
+spins (asd_ll_integrate), operand preparation, the fused contraction with the binning and
+phase epilogues over one block of displacements (asd_pair_corr_contract_range; the step
+index picks the block, so consecutive steps walk through all 128 displacements), and
+normalisation (asd_pair_corr_normalize).  Every displacement costs the same, so a step
+is a fixed amount of work: n_t_per_step * 2 N^2 K flops.
+Metric: algorithmic contraction TFLOP/s = n_t_per_step * 2 N^2 (3 T0) / step time.
 
---impl reference runs the FP64 CPU oracle (the only reference this method has) on a
-bounded sample of the same workload.
+--workload cubic40 runs the 40^3 periodic lattice (N = 64000, K = 3000, 200
+displacements, 70 bins, all displacements per step); ensemble and learned print their
+own lines.  --impl reference runs the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -42,27 +49,48 @@ def parse():
     ap.add_argument("--medium", action="store_true", help="profiling workload (ncu)")
     ap.add_argument("--no-extras", action="store_true", help="skip form sweep, CPU baseline, e2e")
     ap.add_argument("--ncu", action="store_true", help="one step, nothing else (for ncu)")
-    ap.add_argument("--workload", default="cubic40",
-                    choices=["cubic40", "glass", "ensemble", "learned"],
-                    help="cubic40: the headline line; the others print their own lines")
+    ap.add_argument("--nt-per-step", type=int, default=0,
+                    help="displacements per step (0: the workload's default)")
+    ap.add_argument("--workload", default="glass64",
+                    choices=["glass64", "cubic40", "ensemble", "learned"],
+                    help="glass64: the headline line; cubic40 its own line; the others "
+                         "print their own lines")
     return ap.parse_args()
 
 
-def workload(small, medium=False):
+def workload(name, small=False, medium=False):
+    """Sizes of one bench workload.  nt_step = displacements per step."""
     from paper_2308_07487_gb300 import synth
+    if name == "glass64":
+        if medium:
+            # profiling case of the same kernel shapes (K, bins, q): 32^3 glass, 2 displacements
+            lat = synth.hypercubic(32, 3, False, pm_j=True, p=0.5, seed=7, block=(4, 4, 8),
+                                   jitter=0.1)
+            return dict(name="glass32_open_N32768", lat=lat, F=640, T0=512, n_t=2, w=0.5,
+                        n_bins=256, q=synth.q_vectors_glass(), T=1.0, sweeps=50, dt=0.01,
+                        nt_step=2)
+        if small:
+            lat = synth.hypercubic(16, 3, False, pm_j=True, p=0.5, seed=7, block=(4, 4, 8),
+                                   jitter=0.1)
+            return dict(name="glass16_open_N4096", lat=lat, F=160, T0=128, n_t=32, w=0.5,
+                        n_bins=256, q=synth.q_vectors_glass(), T=1.0, sweeps=50, dt=0.01,
+                        nt_step=8)
+        cfg = synth.cfg_glass64()
+        return dict(name=cfg.name, lat=cfg.lattice, F=cfg.F, T0=cfg.T0, n_t=cfg.n_t, w=cfg.w,
+                    n_bins=cfg.n_bins, q=cfg.q, T=cfg.T, sweeps=200, dt=0.01, nt_step=8)
     if medium:
         # profiling case: same K and bin width as the throughput workload, 26^3 sites,
         # 4 displacements (operands ~2 GB: larger than L2, small enough for ncu replay)
         lat = synth.hypercubic(26, 3, True, J=1.0, seed=23082)
         return dict(name="sc26_periodic_N17576", lat=lat, F=1003, T0=1000, n_t=4, w=0.5,
-                    n_bins=46, T=1.2, sweeps=200, dt=0.01)
+                    n_bins=46, q=None, T=1.2, sweeps=200, dt=0.01, nt_step=4)
     if small:
         lat = synth.hypercubic(16, 3, True, J=1.0, seed=23082)
         return dict(name="sc16_periodic_N4096", lat=lat, F=160, T0=128, n_t=32, w=0.5, n_bins=28,
-                    T=1.2, sweeps=200, dt=0.01)
+                    q=None, T=1.2, sweeps=200, dt=0.01, nt_step=32)
     cfg = synth.cfg_cubic40()
     return dict(name=cfg.name, lat=cfg.lattice, F=cfg.F, T0=cfg.T0, n_t=cfg.n_t, w=cfg.w,
-                n_bins=cfg.n_bins, T=cfg.T, sweeps=2000, dt=0.01)
+                n_bins=cfg.n_bins, q=None, T=cfg.T, sweeps=2000, dt=0.01, nt_step=cfg.n_t)
 
 
 def peaks():
@@ -153,11 +181,21 @@ def allmax(ws, x):
 # -------------------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle on a bounded sample of the same workload
 # -------------------------------------------------------------------------------------
+def oracle_rows(threads):
+    """Rows of an oracle sample: the oracle runs its OpenMP loop over rows, so four rows
+    per thread (at least 64) keep every thread busy."""
+    return max(64, 4 * threads)
+
+
 def oracle_sample(W, tr_np, rows, t_list):
+    """The FP64 oracle on rows [rows) x all columns at the displacements t_list, with
+    the workload's bins and q-vectors; flops counted like the GPU's (2 N_rows N K per
+    displacement)."""
     import oracle
     geo = oracle.Geometry.of_lattice(W["lat"])
     t0 = time.perf_counter()
-    res = oracle.pair_corr(tr_np, W["T0"], t_list, geo, W["w"], W["n_bins"], rows=rows)
+    res = oracle.pair_corr(tr_np, W["T0"], t_list, geo, W["w"], W["n_bins"], q=W["q"],
+                           rows=rows)
     dt = time.perf_counter() - t0
     N = W["lat"].n_sites
     flops = 2.0 * (rows[1] - rows[0]) * N * len(t_list) * 3 * W["T0"]
@@ -175,9 +213,9 @@ def run_reference(args, W, ws, rank):
         oracle.set_threads(len(os.sched_getaffinity(0)))
     N = W["lat"].n_sites
     tr = synth.traj_precess(N, W["F"], seed=23082)
-    rows, t_list = (0, 8), [0, W["n_t"] // 2, W["n_t"] - 1]
-    if args.small:
-        rows = (0, 256)
+    threads = oracle.threads()
+    rows = (0, min(N, oracle_rows(threads)))
+    t_list = [0, W["n_t"] - 1]
     oracle_sample(W, tr, (0, 1), [0])  # warm the OpenMP pool
     times, flops = [], 0.0
     for _ in range(args.warmup):
@@ -187,8 +225,9 @@ def run_reference(args, W, ws, rank):
         times.append(dt)
     t = max(times)
     v = flops / t / 1e12
-    cores = oracle.threads()
-    sample = f"rows {rows[0]}..{rows[1]} x all {N} columns x t in {t_list} (K = {3 * W['T0']})"
+    cores = min(threads, rows[1] - rows[0])
+    sample = (f"rows {rows[0]}..{rows[1]} x all {N} columns x t in {t_list} (K = {3 * W['T0']}, "
+              f"{W['n_bins']} bins, {0 if W['q'] is None else len(W['q'])} q)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
@@ -200,10 +239,39 @@ def run_reference(args, W, ws, rank):
     }))
 
 
+def measured_extra_peaks():
+    """TF32 tensor and FP32 (FFMA) GEMM rates of this GPU through cuBLAS (torch.matmul,
+    8192^3, best of 5 after a warm-up): the denominators of the TF32 and FP32-SIMT forms."""
+    import torch
+    n = 8192
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    out = {}
+    was = torch.backends.cuda.matmul.allow_tf32
+    for name, tf32 in (("tf32_tflops", True), ("fp32_sgemm_tflops", False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name] = 2.0 * n ** 3 / best / 1e12
+    torch.backends.cuda.matmul.allow_tf32 = was
+    del a, b
+    torch.cuda.empty_cache()
+    return out
+
+
 # -------------------------------------------------------------------------------------
 # our arm
 # -------------------------------------------------------------------------------------
 def run_ours(args, W, ws, rank, local):
+    import numpy as np
     import torch
 
     from paper_2308_07487_gb300 import asd, synth
@@ -213,216 +281,260 @@ def run_ours(args, W, ws, rank, local):
     stream = torch.cuda.current_stream()
     lat = W["lat"]
     N, F, T0, n_t, nb = lat.n_sites, W["F"], W["T0"], W["n_t"], W["n_bins"]
+    q = W["q"]
+    nq = 0 if q is None else len(q)
+    nt_step = args.nt_per_step or W["nt_step"]
+    nt_step = max(1, min(nt_step, n_t))
+    n_blocks = (n_t + nt_step - 1) // nt_step
     K = 3 * T0
-    flops_step = 2.0 * N * N * K * n_t              # algorithmic, per step
+    flops_disp = 2.0 * N * N * K                     # algorithmic, per displacement
     mult = {"split_bf16": 3, "bf16": 1, "tf32": 1, "fp32": 1}[args.form]
+
+    def block(k):
+        """Displacements of step k: consecutive blocks of nt_step, wrapping around."""
+        tb = (k % n_blocks) * nt_step
+        return tb, min(n_t, tb + nt_step)
 
     # ---- inputs: thermalised start (off the timed region) ----
     sysm = asd.System(lat)
-    spins0 = torch.from_numpy(synth.random_unit(N, 23082 + rank)[None]).to(dev)
+    spins0 = torch.from_numpy(synth.random_unit(N, 23083 + rank)[None]).to(dev)
     sysm.thermalize(spins0, W["T"], W["sweeps"], asd.ASD_METROPOLIS, cone=0.0, adapt=True,
-                    seed=23082 + rank)
+                    seed=23083 + rank)
     traj = torch.empty((N, 1, F, 3), dtype=torch.float32, device=dev)
-    plan = asd.CorrPlan.for_lattice(lat, F, T0, n_t, W["w"], nb, precision=args.form)
+    plan = asd.CorrPlan.for_lattice(lat, F, T0, n_t, W["w"], nb, precision=args.form, q=q)
     C_sum = torch.zeros((n_t, nb), dtype=torch.float64, device=dev)
     C = torch.zeros_like(C_sum)
+    Sq_sum = torch.zeros((n_t, nq), dtype=torch.float64, device=dev) if nq else None
+    Sq = torch.zeros_like(Sq_sum) if nq else None
+
     def new_event():
         return torch.cuda.Event(enable_timing=True)
 
-    def step(kernel_events=None):
-        """One pass of the hot path; kernel_events (start, end) bracket the contraction
-        kernel on the stream it is launched on."""
+    def step(k, kernel_events=None):
+        """One pass of the hot path over displacement block k; kernel_events (start,
+        end) bracket the contraction kernel on the stream it is launched on."""
+        tb, te = block(k)
         sysm.ll_integrate(spins0, W["dt"], F, 1, traj, stream=stream)
         C_sum.zero_()
+        if nq:
+            Sq_sum.zero_()
         plan.prepare(traj, stream=stream)
         if kernel_events is not None:
             kernel_events[0].record(stream)
-        plan.contract(C_sum, stream=stream)
+        plan.contract(C_sum, Sq_sum, stream=stream, t_range=(tb, te))
         if kernel_events is not None:
             kernel_events[1].record(stream)
-        plan.normalize(C_sum, None, C, None, stream=stream)
+        plan.normalize(C_sum, Sq_sum, C, Sq, stream=stream)
+        return te - tb
 
     if args.ncu:
-        step()
+        step(0)
         asd.check(asd.sync_status(stream), "step")
         return
 
-    for _ in range(args.warmup):
-        step()
+    for k in range(args.warmup):
+        step(k)
     asd.check(asd.sync_status(stream), "warmup")
 
-    ktimes = []
+    ktimes, work = [], 0
     t_start, t_end = new_event(), new_event()
     barrier(ws)
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         t_start.record(stream)
-        for _ in range(args.steps):
+        for k in range(args.steps):
             pair = (new_event(), new_event())
-            step(pair)
-            ktimes.append(pair)
+            nd = step(args.warmup + k, pair)
+            ktimes.append((pair, nd))
+            work += nd
         t_end.record(stream)
         torch.cuda.synchronize()
     barrier(ws)
     asd.check(asd.sync_status(stream), "timed steps")
-    t_step = t_start.elapsed_time(t_end) / 1e3 / args.steps
-    t_step = allmax(ws, t_step)
-    t_kernel = sum(a.elapsed_time(b) for a, b in ktimes) / 1e3 / len(ktimes)
+    t_total = t_start.elapsed_time(t_end) / 1e3
+    t_total = allmax(ws, t_total)
+    t_step = t_total / args.steps
+    t_kernel = sum(a.elapsed_time(b) for (a, b), _ in ktimes) / 1e3
     clocks = clk.summary()
-    value = flops_step * ws / t_step / 1e12
+    value = flops_disp * work * ws / t_total / 1e12
 
     pk, pk_kind = peaks()
+    extra_pk = measured_extra_peaks() if (not args.no_extras and rank == 0) else {}
     if args.form == "fp32":
-        peak, bound, punit = None, "alu", "TFLOP/s"
+        peak = extra_pk.get("fp32_sgemm_tflops")
+        bound, punit, psrc = "alu", "TFLOP/s", "measured cuBLAS FP32 SGEMM (FFMA) in this run"
+    elif args.form == "tf32":
+        peak = extra_pk.get("tf32_tflops")
+        bound, punit, psrc = "tensor", "TFLOP/s", "measured cuBLAS TF32 GEMM in this run"
     else:
-        # a kernel timed inside a seconds-long step: the sustained BF16 figure; TF32 at the
-        # nominal dense ratio 1.1/2.25 of BF16
-        peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25 if args.form == "tf32" else 1.0)
-        bound, punit = "tensor", "TFLOP/s"
-    achieved = flops_step * mult / t_kernel / 1e12
+        # a kernel timed inside a seconds-long step: the sustained BF16 figure
+        peak = pk["bf16_tflops_sustained"]
+        bound, punit, psrc = "tensor", "TFLOP/s", f"{pk_kind} bf16_tflops_sustained"
+    achieved = flops_disp * work * mult / t_kernel / 1e12
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
             "frac": (achieved / peak) if peak else None, "traffic": None,
-            "peak_source": f"{pk_kind} bf16_tflops_sustained" if peak else None,
+            "peak_source": psrc,
             "kernel": "pc_tc_kernel" if args.form != "fp32" else "simt_kernel",
-            "flops_per_launch": flops_step * mult,
-            "algorithmic_tflops": flops_step / t_kernel / 1e12,
-            "kernel_ms": t_kernel * 1e3}
+            "flops_per_launch": flops_disp * nt_step * mult,
+            "flops_note": "issued tensor flops of the contraction (x3 for split-BF16); the "
+                          "phase weights are extra work and not counted",
+            "algorithmic_tflops": flops_disp * work / t_kernel / 1e12,
+            "kernel_ms": t_kernel / args.steps * 1e3}
     tfile = os.path.join(ROOT, "profiles", f"traffic_{args.form}_{W['name']}.txt")
     if os.path.exists(tfile):
         for line in open(tfile):
             if line.startswith("dram_bytes_per_launch:"):
                 roof["traffic"] = float(line.split(":")[1])
+    if extra_pk:
+        roof["measured_peaks"] = extra_pk
 
+    # per step: LL frame 0 + 4 RK4 stages per step, prep B + prep A copies (the FP32 form
+    # prepares B only), the fused contraction, normalisation (the memsets are torch's)
+    per_step = 1 + 4 * (F - 1) + (1 if args.form == "fp32" else 2) + 1 + 1
     out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": {"split_bf16": "bf16x3", "bf16": "bf16", "tf32": "tf32", "fp32": "f32"}[args.form],
            "data": "synthetic",
-           "config": {"workload": W["name"], "N": N, "F": F, "T0": T0, "n_t": n_t, "n_bins": nb,
-                      "bin_width": W["w"], "K": K, "form": args.form,
-                      "parallelism": f"replicas x{ws}",
+           "config": {"workload": W["name"], "N": N, "F": F, "T0": T0, "n_t": n_t,
+                      "n_t_per_step": nt_step, "n_bins": nb, "bin_width": W["w"], "n_q": nq,
+                      "K": K, "form": args.form, "parallelism": f"replicas x{ws}",
                       "l2": "inputs larger than L2 (operand copies "
-                            f"{plan.workspace_bytes() / 1e9:.1f} GB)"},
+                            f"{plan.workspace_bytes() / 1e9:.1f} GB, trajectory "
+                            f"{traj.numel() * 4 / 1e9:.2f} GB)"},
            "roofline": roof, "clocks": clocks,
-           # per step: LL frame 0 + 4 RK4 stages per step, prep B + prep A copies, the fused
-           # contraction, normalisation (the memset of C_sum is torch's)
-           "gpu_launches": args.steps * (1 + 4 * (F - 1) + (1 if args.form == "fp32" else 2) + 1 + 1)}
+           "gpu_launches": args.steps * per_step}
 
-    # ---- extras: other forms on a sample, CPU oracle baseline + parity (rank 0) ----
+    # ---- extras (rank 0): precision forms, CPU oracle baseline + parity ----
     if not args.no_extras and rank == 0:
-        nt_s = min(8, n_t)
-        tr_np = None
+        tr_np = traj.cpu().numpy()
+        # the oracle's sample: 4 rows per OpenMP thread, at the first and last displacement
+        import oracle
+        rows_o = (N // 2, min(N, N // 2 + oracle_rows(oracle.threads())))
+        t_o = [0, n_t - 1]
+        res, dt_o, fl_o = oracle_sample(W, tr_np, rows_o, t_o)
+        out["cpu_baseline"] = {
+            "value": fl_o / dt_o / 1e12, "unit": "TFLOP/s",
+            "cores": min(oracle.threads(), rows_o[1] - rows_o[0]), "kind": "oracle",
+            "sample": f"rows {rows_o[0]}..{rows_o[1]} x {N} columns x t {t_o}, K={K}, {nb} bins, "
+                      f"{nq} q, {dt_o:.1f} s"}
+        # every form: time on whole-N displacement blocks (FP32: an eighth of the rows,
+        # scaled), errors on the oracle's rows
         forms = {}
+        nt_f = min(2, n_t)
         for form in ("fp32", "tf32", "bf16", "split_bf16"):
-            p2 = asd.CorrPlan.for_lattice(lat, F, T0, nt_s, W["w"], nb, precision=form)
-            c2 = torch.zeros((nt_s, nb), dtype=torch.float64, device=dev)
+            p2 = asd.CorrPlan.for_lattice(lat, F, T0, n_t, W["w"], nb, precision=form, q=q)
+            c2 = torch.zeros((n_t, nb), dtype=torch.float64, device=dev)
+            s2 = torch.zeros((n_t, nq), dtype=torch.float64, device=dev) if nq else None
             p2.prepare(traj, stream=stream)
-            p2.contract(c2, stream=stream)
+            rows_t = (0, N // 8) if form == "fp32" else (0, N)
+            scale = N / (rows_t[1] - rows_t[0])
+            p2.contract(c2, s2, rows=rows_t, stream=stream, t_range=(0, 1))
             torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a, b = new_event(), new_event()
             a.record(stream)
-            p2.contract(c2, stream=stream)
+            p2.contract(c2, s2, rows=rows_t, stream=stream, t_range=(0, nt_f))
             b.record(stream)
             torch.cuda.synchronize()
-            dt = a.elapsed_time(b) / 1e3
-            forms[form] = {"TFLOP/s": 2.0 * N * N * K * nt_s / dt / 1e12,
-                           "sample": f"{nt_s} displacements"}
+            dt = a.elapsed_time(b) / 1e3 * scale
+            c2.zero_()
+            if nq:
+                s2.zero_()
+            for t in t_o:
+                p2.contract(c2, s2, rows=rows_o, stream=stream, t_range=(t, t + 1))
+            asd.check(asd.sync_status(stream), f"form {form}")
+            rec = {"TFLOP/s": flops_disp * nt_f / dt / 1e12,
+                   "sample": f"{nt_f} displacements" + (", rows 0..N/8 scaled" if form == "fp32"
+                                                        else ""),
+                   "max_bin_err": float(oracle.bin_error(c2.cpu().numpy()[t_o], res).max())}
+            if nq:
+                rec["max_phase_err"] = float(oracle.phase_error(s2.cpu().numpy()[t_o], res).max())
+            forms[form] = rec
             p2.close()
         out["forms"] = forms
         out["speedup_split_bf16_vs_fp32"] = forms["split_bf16"]["TFLOP/s"] / forms["fp32"]["TFLOP/s"]
-
-        # Unfused comparison (context, library path): cuBLAS through torch.matmul forms the
-        # N x N matrix of one displacement in HBM; a separate binning pass must then read it
-        # back, which costs at least N^2 * 4 B at the measured copy bandwidth.
-        tv = traj.view(N, -1)
-        t_u = min(7, n_t - 1)
-        A_t, B_0 = tv[:, 3 * t_u:3 * t_u + K], tv[:, :K]
-        unf = {}
-        tf32_was = torch.backends.cuda.matmul.allow_tf32
-        for name in ("fp32", "tf32", "bf16"):
-            torch.backends.cuda.matmul.allow_tf32 = name == "tf32"
-            a_, b_ = (A_t.to(torch.bfloat16), B_0.to(torch.bfloat16)) if name == "bf16" else (A_t, B_0)
-            holder = {}
-
-            def gemm():
-                holder["G"] = None
-                holder["G"] = torch.matmul(a_, b_.t())
-            gemm()
+        if extra_pk:
+            out["fp32_form_frac_of_sgemm"] = forms["fp32"]["TFLOP/s"] / extra_pk["fp32_sgemm_tflops"]
+        out["max_bin_err"] = forms[args.form]["max_bin_err"]
+        if nq:
+            out["max_phase_err"] = forms[args.form]["max_phase_err"]
+            # the phase sums through the separable transform route (all displacements)
+            p3 = asd.CorrPlan.for_lattice(lat, F, T0, n_t, W["w"], 0, q=q)
+            s3 = torch.zeros((n_t, nq), dtype=torch.float64, device=dev)
+            p3.sq_separable(traj, s3, stream=stream)
             torch.cuda.synchronize()
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev0.record()
-            gemm()
-            ev1.record()
+            a, b = new_event(), new_event()
+            a.record(stream)
+            p3.sq_separable(traj, s3, stream=stream)
+            b.record(stream)
             torch.cuda.synchronize()
-            unf[name + "_gemm_ms"] = ev0.elapsed_time(ev1)
-            unf[name + "_gemm_output"] = str(holder["G"].dtype).replace("torch.", "")
-            holder.clear()
-            del a_, b_
-            torch.cuda.empty_cache()
-        torch.backends.cuda.matmul.allow_tf32 = tf32_was
-        pk0, _ = peaks()
-        unf["binning_read_lower_bound_ms"] = N * N * 4 / (pk0["hbm_gbs"] * 1e9) * 1e3
-        unf["fused_ms_per_displacement"] = {f: 2.0 * N * N * K / (forms[f]["TFLOP/s"] * 1e12) * 1e3
-                                            for f in forms}
-        unf["note"] = ("per displacement; cuBLAS fp32 is the accuracy peer of split_bf16, "
-                       "tf32 / bf16 of the fused tf32 / bf16 forms; N x N FP32 = "
-                       f"{N * N * 4 / 1e9:.1f} GB per displacement")
-        out["unfused_cublas"] = unf
-
-        # the oracle baseline is timed at one GPU only
-        if ws == 1:
-            # CPU oracle on rows 0..R (about 10-15 s on 16 host cores), three displacements, and
-            # the per-bin error of the timed form on the same rows
-            rows = (0, 256)
-            t_list = [0, n_t // 2, n_t - 1]
-            tr_np = traj.cpu().numpy()
-            res, dt, fl = oracle_sample(W, tr_np, rows, t_list)
-            import oracle
-            cs = torch.zeros((n_t, nb), dtype=torch.float64, device=dev)
-            plan.prepare(traj, rows=rows, stream=stream)
-            plan.contract(cs, rows=rows, stream=stream)
+            s3.zero_()
+            p3.sq_separable(traj, s3, stream=stream)
+            asd.check(asd.sync_status(stream), "separable")
+            out["separable_phase"] = {
+                "displacements": n_t, "ms": a.elapsed_time(b),
+                "max_phase_err_vs_oracle": float(oracle.phase_error(s3.cpu().numpy()[t_o],
+                                                                    res).max())}
+            p3.close()
+            # the same kernel with bins only (what the phase epilogue costs)
+            p4 = asd.CorrPlan.for_lattice(lat, F, T0, n_t, W["w"], nb, precision=args.form)
+            c4 = torch.zeros((n_t, nb), dtype=torch.float64, device=dev)
+            p4.prepare(traj, stream=stream)
+            p4.contract(c4, None, stream=stream, t_range=(0, 1))
             torch.cuda.synchronize()
-            err = oracle.bin_error(cs.cpu().numpy()[t_list], res).max()
-            out["cpu_baseline"] = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.threads(),
-                                   "kind": "oracle",
-                                   "sample": f"rows {rows[0]}..{rows[1]} x {N} columns x t {t_list}, "
-                                             f"K={K}, {dt:.1f} s"}
-            out["max_bin_err"] = float(err)
+            a, b = new_event(), new_event()
+            a.record(stream)
+            p4.contract(c4, None, stream=stream, t_range=(0, nt_f))
+            b.record(stream)
+            torch.cuda.synchronize()
+            asd.check(asd.sync_status(stream), "bins only")
+            out["bins_only_TFLOP/s"] = flops_disp * nt_f / (a.elapsed_time(b) / 1e3) / 1e12
+            p4.close()
+        del tr_np
 
     if not args.no_extras:
         # e2e through the public API on every rank: pinned host spins -> device, full step,
-        # C -> host; the job's time is the slowest rank's
+        # C(b,t) and S(q,t) of the step's block -> host; the job's time is the slowest rank's
         h_in = torch.from_numpy(spins0.cpu().numpy()).pin_memory()
-        h_out = torch.empty((n_t, nb), dtype=torch.float64).pin_memory()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
+        h_c = torch.empty((n_t, nb), dtype=torch.float64).pin_memory()
+        h_q = torch.empty((n_t, nq), dtype=torch.float64).pin_memory() if nq else None
+        a = new_event()
+        b = new_event()
+        d2h = 0
         barrier(ws)
         torch.cuda.synchronize()
         with Clocks(local) as clk_e2e, torch.cuda.stream(stream):
             t0 = time.perf_counter()
             a.record(stream)
-            for _ in range(args.steps):
+            work_e = 0
+            for k in range(args.steps):
                 spins0.copy_(h_in, non_blocking=True)
-                step()
-                h_out.copy_(C, non_blocking=True)
+                tb, te = block(args.warmup + k)
+                work_e += step(args.warmup + k)
+                h_c[tb:te].copy_(C[tb:te], non_blocking=True)
+                d2h += (te - tb) * nb * 8
+                if nq:
+                    h_q[tb:te].copy_(Sq[tb:te], non_blocking=True)
+                    d2h += (te - tb) * nq * 8
             b.record(stream)
             torch.cuda.synchronize()
             wall = (time.perf_counter() - t0) / args.steps
         barrier(ws)
-        te = allmax(ws, a.elapsed_time(b) / 1e3 / args.steps)
+        te_s = allmax(ws, a.elapsed_time(b) / 1e3)
         wall = allmax(ws, wall)
         # (a separate run of the same steps: its SM clock under the power cap is recorded,
         # since it can differ from the clock of the device-timed run)
-        out["e2e"] = {"value": flops_step * ws / te / 1e12, "unit": "TFLOP/s",
+        out["e2e"] = {"value": flops_disp * work_e * ws / te_s / 1e12, "unit": "TFLOP/s",
                       "h2d_bytes_per_step": int(h_in.numel() * 4),
-                      "d2h_bytes_per_step": int(h_out.numel() * 8),
+                      "d2h_bytes_per_step": int(d2h // args.steps),
                       "wall_s_per_step": wall, "clocks": clk_e2e.summary()}
     if rank == 0:
         print(json.dumps(out))
     plan.close()
 
+
 # -------------------------------------------------------------------------------------
-# other workloads (one JSON line each; the headline line is the cubic40 workload)
+# other workloads (one JSON line each; the headline line is the glass64 workload)
 # -------------------------------------------------------------------------------------
 def _timed(fn, reps=1):
     import torch
@@ -435,99 +547,6 @@ def _timed(fn, reps=1):
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / 1e3 / reps
-
-
-def run_glass(args):
-    """64^3 jittered +-J glass (262144 sites, open): 256 bins of width 0.5 and S(q,t) for
-    64 q-vectors, 8 of the 128 displacements (every displacement costs the same), all
-    tensor forms; per-form error on a 16-row slice against the FP64 oracle."""
-    import numpy as np
-    import torch
-
-    import oracle
-    from paper_2308_07487_gb300 import asd, synth
-    if args.ncu:
-        # profiling case of the same kernel shapes: 32^3 jittered +-J glass (32768 sites),
-        # F = 640, T0 = 512, 2 displacements, 256 bins, 64 q; one launch with bins only,
-        # then one with bins and phase weights (capture the second: -s 1 -c 1)
-        lat = synth.hypercubic(32, 3, False, pm_j=True, p=0.5, seed=7, block=(4, 4, 8),
-                               jitter=0.1)
-        tr_s = torch.from_numpy(synth.traj_precess(lat.n_sites, 640, seed=5)).cuda()
-        for q in (None, synth.q_vectors_glass()):
-            plan = asd.CorrPlan.for_lattice(lat, 640, 512, 2, 0.5, 256, q=q)
-            C = torch.zeros((2, 256), dtype=torch.float64, device="cuda")
-            Sq = torch.zeros((2, 64), dtype=torch.float64, device="cuda") if q is not None else None
-            plan.run(tr_s, C, Sq)
-            asd.check(asd.sync_status(), "glass profiling case")
-            plan.close()
-        return
-    cfg = synth.cfg_glass64()
-    lat = cfg.lattice
-    N = lat.n_sites
-    tr = synth.traj_precess(N, cfg.F, seed=23083)
-    d_tr = torch.from_numpy(tr).cuda()
-    nt = 8
-    fl = 2.0 * N * N * 3 * cfg.T0 * nt
-    rows, t_sel = (70000, 70016), [0, nt - 1]
-    ref = oracle.pair_corr(tr, cfg.T0, t_sel, oracle.Geometry.of_lattice(lat), cfg.w, cfg.n_bins,
-                           q=cfg.q, rows=rows)
-    out = {"workload": cfg.name, "metric": "fused pair-corr TFLOP/s (bins; bins + 64 q)",
-           "unit": "TFLOP/s", "displacements_timed": nt, "forms": {}}
-    for form in ("split_bf16", "bf16", "tf32", "fp32"):
-        res = {}
-        for with_q in (False, True):
-            q = cfg.q if with_q else None
-            plan = asd.CorrPlan.for_lattice(lat, cfg.F, cfg.T0, nt, cfg.w, cfg.n_bins,
-                                            precision=form, q=q)
-            C = torch.zeros((nt, cfg.n_bins), dtype=torch.float64, device="cuda")
-            Sq = torch.zeros((nt, len(cfg.q)), dtype=torch.float64, device="cuda") if with_q else None
-            plan.prepare(d_tr)
-            if form == "fp32":
-                dt = _timed(lambda: plan.contract(C, Sq, rows=(0, N // 8))) * 8
-            else:
-                dt = _timed(lambda: plan.contract(C, Sq))
-            asd.check(asd.sync_status(), "glass")
-            C.zero_()
-            if Sq is not None:
-                Sq.zero_()
-            plan.contract(C, Sq, rows=rows)
-            torch.cuda.synchronize()
-            err = float(oracle.bin_error(C.cpu().numpy()[t_sel], ref).max())
-            key = "bins_and_phase" if with_q else "bins"
-            res[key] = {"TFLOP/s": fl / dt / 1e12, "ms": dt * 1e3, "max_bin_err": err}
-            if with_q:
-                d = np.abs(Sq.cpu().numpy()[t_sel] - ref["Sq_sum"]).max() / np.abs(ref["Sq_sum"]).max()
-                res[key]["phase_rel_err"] = float(d)
-            plan.close()
-        out["forms"][form] = res
-    # separable route of the phase form (asd_pair_corr_sq_separable): all 128 displacements
-    nt_all = cfg.n_t
-    plan = asd.CorrPlan.for_lattice(lat, cfg.F, cfg.T0, nt_all, cfg.w, 0, q=cfg.q)
-    Sq_all = torch.zeros((nt_all, len(cfg.q)), dtype=torch.float64, device="cuda")
-    dt_sep = _timed(lambda: plan.sq_separable(d_tr, Sq_all))
-    Sq_all.zero_()
-    plan.sq_separable(d_tr, Sq_all)
-    asd.check(asd.sync_status(), "separable")
-    plan.close()
-    # the fused split-BF16 phase sums of the first 8 displacements, for consistency
-    plan = asd.CorrPlan.for_lattice(lat, cfg.F, cfg.T0, nt, cfg.w, 0, q=cfg.q)
-    Sq8 = torch.zeros((nt, len(cfg.q)), dtype=torch.float64, device="cuda")
-    plan.run(d_tr, None, Sq8)
-    torch.cuda.synchronize()
-    plan.close()
-    a8, b8 = Sq_all.cpu().numpy()[:nt], Sq8.cpu().numpy()
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    nudft_flops = 2.0 * 2 * len(cfg.q) * N * 3 * cfg.F
-    out["separable_phase"] = {
-        "displacements": nt_all, "ms": dt_sep * 1e3,
-        "fused_phase_ms_for_same_displacements": out["forms"]["split_bf16"]["bins_and_phase"]["ms"]
-        / nt * nt_all,
-        "transform_TFLOP/s": nudft_flops / dt_sep / 1e12,
-        "fp32_alu_peak_TFLOP/s_at_max_clock": sms * 128 * 2 * 2.07e9 / 1e12,
-        "rel_diff_vs_fused_split_bf16": float(np.abs(a8 - b8).max() / np.abs(b8).max())}
-    out["note"] = ("fp32 timed on rows 0..N/8 and scaled (the SIMT form is ~30x slower); "
-                   "errors on rows 70000..70016, displacements 0 and 7")
-    print(json.dumps(out))
 
 
 def run_ensemble(args):
@@ -758,11 +777,11 @@ def run_learned(args):
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
-    if args.workload != "cubic40":
+    if args.workload in ("ensemble", "learned"):
         if rank == 0:
-            {"glass": run_glass, "ensemble": run_ensemble, "learned": run_learned}[args.workload](args)
+            {"ensemble": run_ensemble, "learned": run_learned}[args.workload](args)
         return
-    W = workload(args.small, args.medium)
+    W = workload(args.workload, args.small, args.medium)
     if args.impl == "reference":
         run_reference(args, W, ws, rank)
     else:

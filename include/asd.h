@@ -162,6 +162,18 @@ int asd_pair_corr_contract(asd_corr_plan *plan, int64_t row_begin, int64_t row_e
                            double *C_sum, double *Sq_sum, void *stream);
 
 /*
+ * asd_pair_corr_contract restricted to the displacements t in [t_begin, t_end)
+ * (0 <= t_begin <= t_end <= n_t): every displacement is an independent contraction
+ * (the time loop of Algorithm 2), so a long run can be cut into blocks of displacements
+ * that accumulate into the same outputs.  C_sum / Sq_sum keep their full [n_t][...] shape
+ * and only rows t_begin .. t_end-1 are added to.  ASD_EINVAL for a bad range; an empty
+ * range is a no-op.
+ */
+int asd_pair_corr_contract_range(asd_corr_plan *plan, int64_t row_begin, int64_t row_end,
+                                 int32_t t_begin, int32_t t_end, double *C_sum, double *Sq_sum,
+                                 void *stream);
+
+/*
  * Several independent problems (each its own plan, trajectory and outputs) in ONE
  * persistent launch over a flattened (problem, t, tile) work list.  All plans must
  * use the same tensor-core precision, tile width and epilogue warp count.  Operand preparation

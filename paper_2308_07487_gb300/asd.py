@@ -70,6 +70,9 @@ _SIGS = {
     "asd_pair_corr": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP]),
     "asd_pair_corr_prepare": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP]),
     "asd_pair_corr_contract": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP]),
+    "asd_pair_corr_contract_range": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64,
+                                                    ctypes.c_int32, ctypes.c_int32, _VP, _VP,
+                                                    _VP]),
     "asd_pair_corr_batched": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int,
                                              ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     "asd_pair_corr_normalize": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
@@ -217,10 +220,17 @@ class CorrPlan:
         check(lib.asd_pair_corr_prepare(self.handle, _ptr(traj), r0, r1, _stream(stream)),
               "pair_corr_prepare")
 
-    def contract(self, C_sum=None, Sq_sum=None, rows=None, stream=None):
+    def contract(self, C_sum=None, Sq_sum=None, rows=None, stream=None, t_range=None):
+        """asd_pair_corr_contract, or asd_pair_corr_contract_range for the displacements
+        t_range = (t_begin, t_end)."""
         r0, r1 = (0, self.N) if rows is None else rows
-        check(lib.asd_pair_corr_contract(self.handle, r0, r1, _ptr(C_sum), _ptr(Sq_sum),
-                                         _stream(stream)), "pair_corr_contract")
+        if t_range is None:
+            check(lib.asd_pair_corr_contract(self.handle, r0, r1, _ptr(C_sum), _ptr(Sq_sum),
+                                             _stream(stream)), "pair_corr_contract")
+        else:
+            check(lib.asd_pair_corr_contract_range(self.handle, r0, r1, int(t_range[0]),
+                                                   int(t_range[1]), _ptr(C_sum), _ptr(Sq_sum),
+                                                   _stream(stream)), "pair_corr_contract_range")
 
     def sq_separable(self, traj, Sq_sum, stream=None):
         """asd_pair_corr_sq_separable: the phase-weighted sum through per-site transforms."""

@@ -53,7 +53,10 @@ constexpr int kMaxCopies = 8;       // shifted operand copies (16-byte TMA start
 constexpr int kMaxProblems = 4096;  // batched work list
 constexpr size_t kMinSmem = 120 * 1024;  // tensor-core kernel: one CTA per SM
 constexpr int kLutMax = 16384;           // largest d2 -> bin table kept in shared memory
-constexpr int kQChunk = 16;              // q-vectors per pass of the phase epilogue
+constexpr int kQChunk = 16;              // q-vectors per chunk of the phase epilogue (cs
+                                         // rows are zero padded to whole chunks)
+constexpr int kPhaseQ = 64;              // q-vectors per pass of the tensor-core phase
+                                         // product (128 output columns: cos and sin)
 
 // Private-bin stride (floats) of the tensor-core epilogue with `ew` epilogue warps: one
 // column per accumulator row, so a warp's 32 lanes address 32 distinct banks.
@@ -78,6 +81,7 @@ struct EpiParams {
                             // packed-coordinate d2, table entries are private-bin offsets
     uint32_t Lpk;           // fast: per-byte minimum-image modulus (x | y<<8 | z<<16)
     int nq_pad;             // row length of cs (n_q rounded up to the q-chunk, zero padded)
+    int npass;              // passes of kPhaseQ q-vectors (0 without phase weights)
     int q_parts;            // 1: cosine part of the phase sum; 2: cosine and sine parts
     const float2 *cs;       // [N][nq_pad] (cos, sin)(q.r_i)
     double *C_sum;          // [n_t][n_bins]
@@ -88,6 +92,8 @@ struct EpiParams {
 struct TcProblem {
     CUtensorMap mapA[2][kMaxCopies];  // [plane][copy]
     CUtensorMap mapB[2];              // [plane]
+    CUtensorMap mapW[2];              // phase column weights [plane]: rows (pass, output),
+                                      // columns = sites (BF16 hi / lo)
     int64_t tile_begin;               // first flattened tile of this problem
     int64_t n_tiles;                  // n_t * tiles_m * tiles_n
     int N;                            // columns (sites)
@@ -109,6 +115,7 @@ struct TcProblem {
 struct TcOverride {
     int active;
     int row_begin, row_end, tiles_m;
+    int t_begin, n_t;              // displacements [t_begin, t_begin + n_t)
     int64_t n_tiles;
     double *C_sum;
     double *Sq_sum;
@@ -165,6 +172,8 @@ struct asd_corr_plan {
     uint16_t *lut;             // lattice d2 -> bin table (nullptr when d2 can reach kLutMax)
     int n_lut;
     float2 *cs;
+    void *W;                   // phase column weights [2 planes][npass * 128][Wld] BF16
+    int64_t Wld;               // row length of W (N rounded up to 8)
     double *sqF;               // separable phase form: transforms [2 n_q][S*3F] (n_q > 0)
     unsigned long long *counter;  // work-item counter of the dynamic schedule
     int q_parts;               // 1 + desc.phase_sine: values per (t, q) in Sq_sum
@@ -197,7 +206,7 @@ int launch_prep(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
 int launch_counts(asd_corr_plan *p, cudaStream_t s, unsigned long long *d_counts);
 // pc_simt.cu
 int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t row_end,
-                double *C_sum, double *Sq_sum, cudaStream_t s);
+                int t_begin, int t_end, double *C_sum, double *Sq_sum, cudaStream_t s);
 // pc_tc.cu
 int tc_configure(asd_corr_plan *p);    // stages / smem for the plan's form
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,

@@ -26,6 +26,7 @@ struct SimtParams {
     int S;
     int N;
     int row_begin, row_end;
+    int t_begin;      // displacement of grid slice blockIdx.z = 0
     EpiParams e;
 };
 
@@ -39,7 +40,7 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int t = blockIdx.z;
+    const int t = P.t_begin + blockIdx.z;
     const int m0 = P.row_begin + blockIdx.x * TM;
     const int n0 = blockIdx.y * TN;
     for (int k = tid; k < P.e.n_bins + P.e.n_q * P.e.q_parts; k += 256) red[k] = 0.0;
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
 }  // namespace
 
 int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t row_end,
-                double *C_sum, double *Sq_sum, cudaStream_t s)
+                int t_begin, int t_end, double *C_sum, double *Sq_sum, cudaStream_t s)
 {
     SimtParams P{};
     P.traj = traj;
@@ -186,6 +187,7 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
     P.N = (int)p->N;
     P.row_begin = (int)row_begin;
     P.row_end = (int)row_end;
+    P.t_begin = t_begin;
     EpiParams &e = P.e;
     e.geom = p->d.geometry;
     e.Lx = p->d.L[0];
@@ -204,7 +206,7 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
     e.C_sum = C_sum;
     e.Sq_sum = Sq_sum;
     dim3 grid((unsigned)((row_end - row_begin + TM - 1) / TM), (unsigned)((p->N + TN - 1) / TN),
-              (unsigned)p->n_t);
+              (unsigned)(t_end - t_begin));
     if (grid.y > 65535u || grid.z > 65535u) {
         set_error_text("FP32 form: grid too large (N or n_t)");
         return ASD_EUNSUPPORTED;

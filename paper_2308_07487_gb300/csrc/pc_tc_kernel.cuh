@@ -34,7 +34,6 @@
 #include <cuda_bf16.h>
 
 #include "asd_internal.h"
-#include "fma2.cuh"
 #include "geom.cuh"
 
 namespace asd {
@@ -43,12 +42,12 @@ namespace {
 // Epilogue warps EW (template parameter): 4 (one per TMEM lane quarter, all columns) or
 // 8 (two per quarter, half the columns each).  Threads = TMA warp + MMA warp + EW warps.
 constexpr int kMaxEpiWarps = 8;
-constexpr int kQC = kQChunk;                  // (cos, sin) rows are padded to whole kQC
-// q-vectors per pass of the phase loop: 8 with 4 epilogue warps; 4 with 8 warps, whose
-// register budget (two warps per scheduler) has no room for 8 q of accumulators
-__host__ __device__ constexpr int qp_of(int ew) { return ew == 8 ? 4 : 8; }
-static_assert(kQC % qp_of(4) == 0 && kQC % qp_of(8) == 0, "q passes tile the padded q rows");
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
+// TMEM: 512 columns per CTA (one CTA per SM): two BN-column accumulators, then (phase
+// workloads, BN <= 192) the 128-column phase product P of one pass of 64 q-vectors.
+constexpr uint32_t kTmemAlloc = 512;
+constexpr int kPCols = 2 * kPhaseQ;           // u (cosine weights) and v (sine weights)
+constexpr uint32_t kWBytes = 128u * 128u;     // one plane of a W stage: 128 rows x 64 BF16
 // Work items are handed from the TMA thread to the MMA thread and the epilogue warps
 // through a ring of kWQ slots in shared memory.  With the dynamic schedule the TMA thread
 // claims each item from a global counter, so the items in flight across the grid stay
@@ -175,21 +174,30 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-// 16 lanes x 256 bits, 4 repetitions along the columns (32 columns): register 4m + e
-// holds (lane l/4, column 8m + 2(l%4) + e) and register 4m + 2 + e holds (lane l/4 + 8,
-// the same column), l = this thread's lane in the warp.  Valid after tmem_wait16x2.
-__device__ __forceinline__ void tmem_ld16x256b_x4(uint32_t taddr, uint32_t (&r)[16])
+// MMA with the A operand in tensor memory (128 lanes = rows, K along the columns, two
+// BF16 elements per 32-bit column, the even element in the low half) and B in shared
+// memory: the phase product P = G W of the epilogue.
+__device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                          uint32_t acc)
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// 32 lanes x 16 consecutive 32-bit columns (this thread's lane), and its wait, tied to the
+// registers.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
         "%11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
-
-// Wait for two 16x256b.x4 loads, tied to their registers.
 __device__ __forceinline__ void tmem_wait16x2(uint32_t (&a)[16], uint32_t (&b)[16])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
@@ -203,15 +211,18 @@ __device__ __forceinline__ void tmem_wait16x2(uint32_t (&a)[16], uint32_t (&b)[1
                  : "memory");
 }
 
-// Asynchronous 16-byte global -> shared copy (completion per thread by commit groups).
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+// Store 16 consecutive 32-bit columns of this thread's lane; complete after tmem_wait_st.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16])
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(smem_dst)),
-                 "l"(gsrc)
-                 : "memory");
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15])
+        : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Issue half of tmem_ld32: the registers are valid only after tmem_wait32 on them.
 __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32])
@@ -313,7 +324,7 @@ __host__ __device__ constexpr uint32_t idesc(bool tf32, int N)
 // shared-memory layout of the epilogue region
 // ------------------------------------------------------------------------------------
 struct EpiLayout {
-    uint32_t cacc, qacc, qred, fb, colgeo, colpk, colcs, rowcs, boxred, var, total;
+    uint32_t cacc, qacc, fb, colgeo, colpk, boxred, var, total;
 };
 
 __host__ __device__ inline uint32_t take(uint32_t &o, uint32_t bytes)
@@ -347,15 +358,9 @@ __host__ __device__ inline EpiLayout epi_layout(uint32_t vb, int nb, int nq, int
     L.cacc = take(o, 8u * (nb > 0 ? nb : 1));
     // phase sums per q: (cosine, sine) parts
     L.qacc = take(o, 8u * 2 * (nq > 0 ? nq : 1));
-    // one slot per (pass, warp, q): the passes of a tile are reduced once at its end
-    const int qp = qp_of(ew);
-    L.qred = take(o, 8u * 2 * ew * (nq > 0 ? (nq + qp - 1) / qp * qp : qp));
     L.fb = take(o, 4u * (nb > 0 ? nb : 1));
     L.colgeo = take(o, 16u * BN);
     L.colpk = take(o, 4u * BN);
-    // phase weights of one pass, double buffered: columns (BN) and rows (128) of the tile
-    L.colcs = nq > 0 ? take(o, 2u * 8u * BN * qp) : 0u;
-    L.rowcs = nq > 0 ? take(o, 2u * 8u * kBM * qp) : 0u;
     L.boxred = take(o, 4u * ew * 12);
     L.var = take(o, vb);
     L.total = (o + 1023u) & ~1023u;
@@ -376,7 +381,7 @@ struct TileInfo {
 struct WorkCursor {
     int p = -1;
     int64_t begin = 0, end = 0;  // flattened items [begin, end) belong to problem p
-    int tiles_m, tiles_n, kch, G, nk, row_begin, row_end;
+    int tiles_m, tiles_n, kch, G, nk, row_begin, row_end, t_begin;
     int64_t per_kc;
 };
 
@@ -411,12 +416,13 @@ __device__ __forceinline__ TileInfo decode(WorkCursor &cu, const TcProblem *__re
         cu.nk = P.S * P.nkb;
         cu.row_begin = ov.active ? ov.row_begin : P.row_begin;
         cu.row_end = ov.active ? ov.row_end : P.row_end;
+        cu.t_begin = ov.active ? ov.t_begin : 0;
         cu.per_kc = (int64_t)cu.tiles_m * cu.tiles_n;
     }
     const int64_t l = tau - cu.begin;
     TileInfo ti;
     ti.p = cu.p;
-    ti.t = (int)(l / (cu.per_kc * cu.kch));
+    ti.t = cu.t_begin + (int)(l / (cu.per_kc * cu.kch));
     const int64_t rem0 = l % (cu.per_kc * cu.kch);
     const int kc = (int)(rem0 / cu.per_kc);
     const int64_t rem = rem0 % cu.per_kc;
@@ -530,7 +536,52 @@ __device__ __forceinline__ void pk_offsets(uint32_t (&off)[32], uint32_t rpk, ui
     }
 }
 
+// Fast form of bin_chunk's first phase for FP32 positions, when every pair of the tile
+// falls inside the private window (see the epilogue): the exact bin of each pair from
+// its FP32 d2 and the thresholds, as a private-bin word offset; dropped pairs go to the
+// trash row, so no pair takes a branch.
+template <int STRIDE>
+__device__ __forceinline__ void pos_offsets(uint32_t (&off)[32], float4 rp,
+                                            const float4 *__restrict__ cgeo,
+                                            const float2 *__restrict__ thr2, float inv_w, int nb,
+                                            int blo, uint32_t trash_off)
+{
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const int b = bin_of_d2_pair(position_d2(rp, cgeo[k]), inv_w, nb, thr2);
+        off[k] = b < nb ? (uint32_t)((b - blo) * STRIDE) : trash_off;
+    }
+}
+
 using LaunchArgs = TcLaunchArgs;
+
+// Sum of 16 per-lane values over the warp's 32 lanes by recursive halving: each exchange
+// sends the half of the values this lane does not keep; after four steps lanes 2m and
+// 2m + 1 hold partial sums of value m, which the last exchange adds.
+__device__ __forceinline__ float warp_sum16(float (&z)[16], int lane)
+{
+#pragma unroll
+    for (int hh = 8, o = 16; hh >= 1; hh >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < hh; ++k) {
+            const float send = up ? z[k] : z[k + hh];
+            const float keep = up ? z[k + hh] : z[k];
+            z[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return z[0] + __shfl_xor_sync(0xffffffffu, z[0], 1);
+}
+
+// K block of a work item before which pass pp (of npass) of the previous item's phase
+// product is issued, always inside the item.  The epilogue needs the first part of the
+// item to bin and convert the previous tile, the rest of it to read the product out before
+// the accumulator is needed again: one pass goes in at 2/3 of the item, more passes are
+// spread over the rest of it.
+__device__ __forceinline__ int phase_slot(int pp, int nk, int npass)
+{
+    return ((pp + 2) * nk) / (npass + 2);
+}
 
 // ------------------------------------------------------------------------------------
 // the kernel
@@ -542,7 +593,6 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     constexpr int kEpiThreads = 32 * EW;
     constexpr int kBinStride = bin_stride(EW);
     constexpr int kHalves = EW / 4;
-    constexpr int kQP = qp_of(EW);
     constexpr bool kTF32 = FORM == ASD_TF32;
     constexpr int kPlanes = FORM == ASD_SPLIT_BF16 ? 2 : 1;
     constexpr uint32_t kABytes = kBM * SWB;
@@ -551,7 +601,19 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     constexpr int kKSteps = SWB / 32;          // one MMA k-step covers 32 bytes of K
     constexpr int kBK = SWB / (kTF32 ? 4 : 2); // K elements per stage
     constexpr uint32_t kIdesc = idesc(kTF32, BN);
-    constexpr uint32_t kTmemCols = 2 * BN;
+    // Phase weights on the tensor core (problems with n_q > 0; the plan picks BN <= 192 and
+    // 4 epilogue warps): after the epilogue has binned a tile it stores the tile's G, split
+    // into BF16 hi + lo, back over the accumulator's own columns (chunk of 32 columns ->
+    // 16 columns of hi, then 16 of lo), and one pass of kPhaseQ q-vectors is the
+    // 128 x 128 x BN product P = G W with W[c][o] = cos / sin(q_o . r_c) of the tile's
+    // columns, streamed through the operand ring (64 columns c per stage).  Split-BF16 and
+    // TF32 issue hi*hi + hi*lo + lo*hi (the FP32-accurate sum); BF16 issues hi*hi.
+    constexpr bool kPhaseOK = 2 * BN + kPCols <= (int)kTmemAlloc;
+    constexpr int kWPlanes = FORM == ASD_BF16 ? 1 : 2;
+    constexpr int kWStages = BN / 64;          // W stages per pass (64 columns c each)
+    constexpr uint32_t kIdescP = idesc(false, kPCols);
+    static_assert(!kPhaseOK || (kStageBytes >= kWPlanes * kWBytes && BN % 64 == 0),
+                  "a W stage fits a ring stage");
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned base for the swizzled tiles
@@ -563,11 +625,16 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     const EpiLayout EL = epi_layout(args.VB, args.NB, args.NQ, BN, EW);
     uint64_t *bars = reinterpret_cast<uint64_t *>(epi + EL.total);
     // bars: full[stages], empty[stages], tfull[2], tempty[2], drain, wqfull[kWQ],
-    // wqempty[kWQ]; then the work ring wq[kWQ] and the TMEM address slot
+    // wqempty[kWQ], conv, pfull, pempty; then the work ring wq[kWQ] and the TMEM address
+    // slot
     const uint32_t wqfull0 = saddr(bars + 2 * stages + 5);
     const uint32_t wqempty0 = saddr(bars + 2 * stages + 5 + kWQ);
-    volatile int64_t *wq = reinterpret_cast<volatile int64_t *>(bars + 2 * stages + 5 + 2 * kWQ);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 5 + 3 * kWQ);
+    // conv: the epilogue has stored a tile's G as BF16 hi / lo (one arrival per warp);
+    // pfull: the phase product of a pass is complete; pempty: the epilogue has read it
+    const uint32_t conv = saddr(bars + 2 * stages + 5 + 2 * kWQ);
+    const uint32_t pfull = conv + 8, pempty = conv + 16;
+    volatile int64_t *wq = reinterpret_cast<volatile int64_t *>(bars + 2 * stages + 8 + 2 * kWQ);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 8 + 3 * kWQ);
     const uint32_t full0 = saddr(bars), empty0 = saddr(bars + stages);
     const uint32_t tfull0 = saddr(bars + 2 * stages), tempty0 = saddr(bars + 2 * stages + 2);
     const uint32_t drain = saddr(bars + 2 * stages + 4);
@@ -589,9 +656,12 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             // released by the MMA thread and one lane of every epilogue warp
             mbar_init(wqempty0 + 8 * k, 1 + kEpiWarps);
         }
+        mbar_init(conv, kEpiWarps);
+        mbar_init(pfull, 1);
+        mbar_init(pempty, kEpiWarps);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(saddr(tmem_slot), kTmemCols);
+    if (warp == 1) tmem_alloc(saddr(tmem_slot), kTmemAlloc);
     tc_before();
     __syncthreads();
     tc_after();
@@ -606,6 +676,32 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             uint32_t phase = 0;
             bool ok = true;
             WorkCursor cu;
+            // the previous work item, while its phase passes are still to be loaded: they
+            // go in among this item's K blocks (pass pp before block phase_slot(pp)), so
+            // the phase product of item v - 1 runs while item v's MMAs run
+            int pend_p = -1, pend_n0 = 0, pend_np = 0;
+            auto next_stage = [&]() {
+                if (++stage == stages) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+            };
+            auto load_pass = [&](int pp) {
+                const TcProblem &Q = probs[pend_p];
+                for (int j = 0; j < kWStages; ++j) {
+                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, args.err, DEV_TIMEOUT_TMA))
+                        return false;
+                    const uint32_t fb = full0 + 8 * stage;
+                    mbar_expect_tx(fb, kWPlanes * kWBytes);
+                    uint8_t *st = tiles + (size_t)stage * kStageBytes;
+#pragma unroll
+                    for (int pl = 0; pl < kWPlanes; ++pl)
+                        tma_load_2d(saddr(st + pl * kWBytes), &Q.mapW[pl], fb, pend_n0 + 64 * j,
+                                    pp * kPCols);
+                    next_stage();
+                }
+                return true;
+            };
             for (int64_t v = 0; ok; ++v) {
                 // publish the next work item (-1: none left) once its ring slot is free
                 const int qs = (int)(v % kWQ);
@@ -622,7 +718,19 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 if (tau < 0) break;
                 const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau, BN);
                 const TcProblem &P = probs[ti.p];
-                for (int kg = ti.kg0; kg < ti.kg1; ++kg) {
+                const int nk = ti.kg1 - ti.kg0;
+                int pp = 0;
+                for (int kg = ti.kg0; kg < ti.kg1 && ok; ++kg) {
+                    if constexpr (kPhaseOK) {
+                        while (pend_p >= 0 && pp < pend_np &&
+                               kg - ti.kg0 == phase_slot(pp, nk, pend_np)) {
+                            if (!load_pass(pp++)) {
+                                ok = false;
+                                break;
+                            }
+                        }
+                        if (!ok) break;
+                    }
                     const int s = kg / P.nkb, kb = kg % P.nkb;
                     const int xw = s * P.F3 + 3 * ti.t;
                     const int c = xw % P.n_copies;
@@ -640,12 +748,18 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         tma_load_2d(saddr(st + kPlanes * kABytes + pl * kBBytes), &P.mapB[pl], fb,
                                     s * P.Kseg + kb * kBK, ti.n0);
                     }
-                    if (++stage == stages) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
+                    next_stage();
+                }
+                pend_p = -1;
+                if (kPhaseOK && P.epi.n_q > 0) {
+                    pend_p = ti.p;
+                    pend_n0 = ti.n0;
+                    pend_np = P.epi.npass;
                 }
             }
+            // the last item's phase passes
+            if (kPhaseOK && ok && pend_p >= 0)
+                for (int pp = 0; pp < pend_np && ok; ++pp) ok = load_pass(pp);
             // drain: wait until the last fill of every stage has landed
             for (int k = 0; k < stages; ++k) {
                 if (--stage < 0) {
@@ -665,6 +779,54 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             uint32_t v = 0;
             bool ok = true;
             WorkCursor cu;
+            // previous item with phase passes still to issue (its accumulator buffer), the
+            // count of converted tiles waited for and of phase passes issued
+            int pend_acc = -1, pend_np = 0;
+            uint32_t n_conv = 0, n_pass = 0;
+            const uint32_t ptm = tmem + 2 * BN;  // phase product P
+            // one pass of the previous item's phase product: P = G W over the kWStages W
+            // stages of the ring, A = the BF16 hi / lo copy of G in its accumulator columns
+            auto issue_pass = [&](int pp) {
+                const uint32_t g0 = tmem + (uint32_t)pend_acc * BN;
+                for (int j = 0; j < kWStages; ++j) {
+                    if (!mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_MMA))
+                        return false;
+                    if (j == 0) {
+                        // G stored as BF16 by the epilogue (once per item), P read out
+                        if (pp == 0 &&
+                            !mbar_wait(conv, n_conv++ & 1, args.err, DEV_TIMEOUT_MMA))
+                            return false;
+                        if (!mbar_wait(pempty, (n_pass & 1) ^ 1, args.err, DEV_TIMEOUT_MMA))
+                            return false;
+                    }
+                    tc_after();
+                    uint8_t *st = tiles + (size_t)stage * kStageBytes;
+                    const uint64_t w0 = sdesc(saddr(st), 128);
+                    const uint64_t w1 = sdesc(saddr(st + kWBytes), 128);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        // columns c = 64 j + 16 ks: chunk c / 32 holds hi in its first 16
+                        // TMEM columns and lo in the next 16
+                        const int c = 64 * j + 16 * ks;
+                        const uint32_t ahi = g0 + 32 * (c >> 5) + 8 * ((c >> 4) & 1);
+                        const uint64_t off = (uint64_t)(ks * 32) >> 4;
+                        const uint32_t accum = (j | ks) != 0;
+                        tc_mma_ts(ptm, ahi, w0 + off, kIdescP, accum);           // hi*hi
+                        if (kWPlanes == 2) {
+                            tc_mma_ts(ptm, ahi, w1 + off, kIdescP, 1u);          // hi*lo
+                            tc_mma_ts(ptm, ahi + 16, w0 + off, kIdescP, 1u);     // lo*hi
+                        }
+                    }
+                    tc_commit(empty0 + 8 * stage);
+                    if (++stage == stages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                tc_commit(pfull);
+                ++n_pass;
+                return true;
+            };
             for (;; ++v) {
                 const int qs = (int)(v % kWQ);
                 if (!mbar_wait(wqfull0 + 8 * qs, (v / kWQ) & 1, args.err, DEV_TIMEOUT_MMA)) {
@@ -682,8 +844,19 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 }
                 tc_after();
                 const uint32_t d = tmem + acc * BN;
+                const int nk = ti.kg1 - ti.kg0;
+                int pp = 0;
                 for (int kg = ti.kg0; kg < ti.kg1; ++kg) {
                     const int kb = kg - ti.kg0;  // 0 for the first block of this chunk
+                    if constexpr (kPhaseOK) {
+                        while (pend_acc >= 0 && pp < pend_np && kb == phase_slot(pp, nk, pend_np)) {
+                            if (!issue_pass(pp++)) {
+                                ok = false;
+                                break;
+                            }
+                        }
+                        if (!ok) break;
+                    }
                     if (!mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_MMA)) {
                         ok = false;
                         break;
@@ -714,7 +887,15 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 }
                 if (!ok) break;
                 tc_commit(tfull0 + 8 * acc);
+                pend_acc = -1;
+                if (kPhaseOK && probs[ti.p].epi.n_q > 0) {
+                    pend_acc = (int)acc;
+                    pend_np = probs[ti.p].epi.npass;
+                }
             }
+            // the last item's phase passes
+            if (kPhaseOK && ok && pend_acc >= 0)
+                for (int pp = 0; pp < pend_np && ok; ++pp) ok = issue_pass(pp);
             // drain every MMA this thread issued before TMEM is released
             tc_commit(drain);
             mbar_wait(drain, 0, args.err, DEV_TIMEOUT_MMA);
@@ -732,11 +913,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         float *fb = reinterpret_cast<float *>(epi + EL.fb);
         double *cacc = reinterpret_cast<double *>(epi + EL.cacc);
         double *qacc = reinterpret_cast<double *>(epi + EL.qacc);
-        double *qred = reinterpret_cast<double *>(epi + EL.qred);
         float4 *colgeo = reinterpret_cast<float4 *>(epi + EL.colgeo);
         uint32_t *colpk = reinterpret_cast<uint32_t *>(epi + EL.colpk);
-        float4 *colcs = reinterpret_cast<float4 *>(epi + EL.colcs);
-        float4 *rowcs = reinterpret_cast<float4 *>(epi + EL.rowcs);
         float *boxred = reinterpret_cast<float *>(epi + EL.boxred);
         float *thr_s = bins;
         for (int k = et; k < args.NB; k += kEpiThreads) {
@@ -752,30 +930,25 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         auto fast_ok = [&](const EpiParams &E) {
             return E.fast && (E.NW + 1) * kBinStride <= 65536;
         };
-        // phase weights of pass `pass` (q = pass*kQP ...) of a tile into buffer pass & 1:
-        // the tile's column and row (cos, sin) rows, as asynchronous copies (rows are zero
-        // padded to whole chunks, two q per float4; indices past the problem are clamped,
-        // their accumulator entries being zero or their rows weighed by 0)
-        auto stage_phase = [&](const TileInfo &tq, const TcProblem &Pq, int pass) {
-            const float4 *cs4 = reinterpret_cast<const float4 *>(Pq.epi.cs);
-            const int64_t qo = (int64_t)pass * kQP / 2;
-            const int64_t rl = Pq.epi.nq_pad / 2;
-            float4 *cb = colcs + (pass & 1) * (BN * kQP / 2);
-            float4 *rb = rowcs + (pass & 1) * (kBM * kQP / 2);
-            // shared layouts: columns [c/8][q2][c%8] (the 4 column pairs a warp reads at
-            // once are 32 bytes apart: distinct banks), rows [q2][row]
-            for (int k = et; k < BN * kQP / 2; k += kEpiThreads) {
-                const int c = k / (kQP / 2), q2 = k % (kQP / 2);
-                const int j = min(tq.n0 + c, Pq.N - 1);
-                cp_async16(cb + ((c >> 3) * (kQP / 2) + q2) * 8 + (c & 7),
-                           cs4 + (int64_t)j * rl + qo + q2);
+        // phase passes read out so far (parity of pfull)
+        uint32_t n_pass = 0;
+        // Store a 32-column chunk of this thread's accumulator row back as BF16 hi / lo
+        // (16 columns each, two values per column, the even column in the low half):
+        // the A operand of the phase product.  Rows past the range store zeros.
+        auto to_bf16 = [&](const uint32_t (&g)[32], uint32_t tcol, bool keep) {
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float a = keep ? __uint_as_float(g[2 * k]) : 0.f;
+                const float b = keep ? __uint_as_float(g[2 * k + 1]) : 0.f;
+                const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                const float2 hf = __bfloat1622float2(h);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+                hi[k] = *reinterpret_cast<const uint32_t *>(&h);
+                lo[k] = *reinterpret_cast<const uint32_t *>(&l);
             }
-            for (int k = et; k < kBM * kQP / 2; k += kEpiThreads) {
-                const int r = k / (kQP / 2), q2 = k % (kQP / 2);
-                const int i = min(tq.m0 + r, Pq.N - 1);
-                cp_async16(rb + q2 * kBM + r, cs4 + (int64_t)i * rl + qo + q2);
-            }
-            cp_async_commit();
+            tmem_st16(tcol, hi);
+            tmem_st16(tcol + 16, lo);
         };
         uint32_t v = 0;
         bool ok = true;
@@ -896,8 +1069,12 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 cur_t = ti.t;
             }
             int blo = 0;
+            // positions: whether every kept bin of the tile lies inside the private window
+            // [blo, blo + NW), from the largest distance between the two bounding boxes
+            bool pos_fit = !E.use_window;
+            int bhi_tile = E.n_bins - 1;
             if (E.use_window) {
-                float d2min = 0.f;
+                float d2min = 0.f, d2max = 0.f;
                 for (int a = 0; a < 3; ++a) {
                     float rl = 3e38f, rh = -3e38f, cl = 3e38f, ch = -3e38f;
                     for (int w = 0; w < kEpiWarps; ++w) {
@@ -913,11 +1090,19 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         gap = fminf(gap, fmaxf(0.f, fmaxf(cl - L - rh, rl - (ch - L))));
                     }
                     d2min += gap * gap;
+                    const float far = fmaxf(ch - rl, rh - cl);
+                    d2max += far * far;
                 }
                 blo = max(0, bin_of_d2(d2min * 0.999f, E.inv_w, E.n_bins, E.thr) - 1);
+                if (!lattice) {
+                    bhi_tile = min(E.n_bins - 1,
+                                   bin_of_d2(d2max * 1.001f + 1e-30f, E.inv_w, E.n_bins, E.thr) + 1);
+                    pos_fit = bhi_tile - blo < E.NW;
+                }
             }
 
-            if (E.n_q > 0) stage_phase(ti, P, 0);  // lands while the MMAs finish
+            // phase weights of this item go through the tensor core (see kPhaseOK)
+            const bool ph = kPhaseOK && E.n_q > 0;
             const uint32_t acc = v & 1, use = v >> 1;
             const bool got = mbar_wait(tfull0 + 8 * acc, use & 1, args.err, DEV_TIMEOUT_EPI);
             ok = epi_sync_and(got, kEpiThreads);
@@ -960,6 +1145,25 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
 #pragma unroll
                             for (int k = 0; k < 32; ++k) mb[off[k]] += __uint_as_float(g[k]);
                         }
+                        if (ph) to_bf16(g, tbase + ch * 32, row_ok);
+                    }
+                } else if (mode == BIN_POS && pos_fit) {
+                    // rows past the range skip the pairs (the TMEM loads stay warp-wide)
+                    float *mb = bins + r + kBM * half;
+                    const uint32_t trash_off = (uint32_t)E.NW * kBinStride;
+                    const float2 *thr2 = reinterpret_cast<const float2 *>(thr_s);
+                    const int b0 = E.use_window ? blo : 0;
+                    for (int ch = ch0; ch < ch1; ++ch) {
+                        uint32_t g[32], off[32];
+                        tmem_ld32_issue(tbase + ch * 32, g);
+                        pos_offsets<kBinStride>(off, rp, colgeo + ch * 32, thr2, E.inv_w,
+                                                E.n_bins, b0, trash_off);
+                        tmem_wait32(g);
+                        if (row_ok) {
+#pragma unroll
+                            for (int k = 0; k < 32; ++k) mb[off[k]] += __uint_as_float(g[k]);
+                        }
+                        if (ph) to_bf16(g, tbase + ch * 32, row_ok);
                     }
                 } else
                 for (int ch = ch0; ch < ch1; ++ch) {
@@ -973,151 +1177,55 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         bin_chunk<BIN_THR, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fb, ba);
                     else
                         bin_chunk<BIN_POS, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fb, ba);
+                    if (ph) to_bf16(g, tbase + ch * 32, row_ok);
+                }
+            } else if (ph) {
+                for (int ch = ch0; ch < ch1; ++ch) {
+                    uint32_t g[32];
+                    tmem_ld32(tbase + ch * 32, g);
+                    to_bf16(g, tbase + ch * 32, row_ok);
                 }
             }
-            if (E.n_q > 0) {
-                // Phase weights, kQP q per pass.  The accumulator is read in the 16x256b
-                // shape: a thread holds rows {l/4, l/4+8} (+16 for the second half-quarter)
-                // and columns {2(l%4), 2(l%4)+1} of every 8-column block, so each (cos, sin)
-                // column weight loaded from shared memory serves 4 rows:
-                //   u_r(q) = sum_j c_j(q) G_rj,  v_r(q) = sum_j s_j(q) G_rj  (partial over the
-                // thread's columns), then sum_r c_r(q) u_r(q) + s_r(q) v_r(q) over the warp.
-                // The weights of pass p+1 are copied while pass p computes.
-                const int npass = (E.n_q + kQP - 1) / kQP;
-                const int cq = 2 * (lane & 3);  // this thread's column pair in a block
-                for (int pass = 0; pass < npass; ++pass) {
-                    cp_async_wait_all();
-                    // everyone's copies of this pass are visible; everyone is done with the
-                    // buffer that the next pass's copies overwrite
-                    epi_sync(kEpiThreads);
-                    if (pass + 1 < npass) stage_phase(ti, P, pass + 1);
-                    const float4 *cb = colcs + (pass & 1) * (BN * kQP / 2);
-                    const float4 *rb = rowcs + (pass & 1) * (kBM * kQP / 2);
-                    float u[4][kQP], vv[4][kQP];
-#pragma unroll
-                    for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-                        for (int q = 0; q < kQP; ++q) {
-                            u[rr][q] = 0.f;
-                            vv[rr][q] = 0.f;
-                        }
-                    // rows of this thread past the range (unprepared A rows): values replaced
-                    bool okr[4];
-#pragma unroll
-                    for (int rr = 0; rr < 4; ++rr)
-                        okr[rr] = ti.m0 + q4 * 32 + 16 * (rr >> 1) + 8 * (rr & 1) + (lane >> 2) <
-                                  ti.row_end;
-                    auto chunk = [&](const uint32_t (&g)[2][16], int ch) {
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) {
-#pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const float4 *w = cb + (ch * 4 + m) * (kQP / 2) * 8 + cq + e;
-#pragma unroll
-                                for (int q2 = 0; q2 < kQP / 2; ++q2) {
-                                    const float4 w4 = w[q2 * 8];
-#pragma unroll
-                                    for (int rr = 0; rr < 4; ++rr) {
-                                        const float gv =
-                                            okr[rr] ? __uint_as_float(g[rr >> 1][4 * m + 2 * (rr & 1) + e])
-                                                    : 0.f;
-                                        fma2(u[rr][2 * q2], vv[rr][2 * q2], w4.x, w4.y, gv);
-                                        fma2(u[rr][2 * q2 + 1], vv[rr][2 * q2 + 1], w4.z, w4.w, gv);
-                                    }
-                                }
-                            }
-                        }
-                    };
-                    for (int ch = ch0; ch < ch1; ++ch) {
-                        uint32_t g[2][16];
-                        tmem_ld16x256b_x4(tbase + ch * 32, g[0]);
-                        tmem_ld16x256b_x4(tbase + (16u << 16) + ch * 32, g[1]);
-                        tmem_wait16x2(g[0], g[1]);
-                        chunk(g, ch);
-                    }
-                    // row weights of the thread's 4 rows (rows past the range weigh 0):
-                    // cosine part c_r u + s_r v, sine part s_r u - c_r v (angle difference)
-                    float x[kQP], y[kQP];
-#pragma unroll
-                    for (int q = 0; q < kQP; ++q) {
-                        x[q] = 0.f;
-                        y[q] = 0.f;
-                    }
-#pragma unroll
-                    for (int rr = 0; rr < 4; ++rr) {
-                        const int rrow = q4 * 32 + 16 * (rr >> 1) + 8 * (rr & 1) + (lane >> 2);
-                        const bool ok_r = ti.m0 + rrow < ti.row_end;
-#pragma unroll
-                        for (int q2 = 0; q2 < kQP / 2; ++q2) {
-                            float4 w = rb[q2 * kBM + rrow];
-                            if (!ok_r) w = make_float4(0.f, 0.f, 0.f, 0.f);
-                            const float u0 = u[rr][2 * q2], v0 = vv[rr][2 * q2];
-                            const float u1 = u[rr][2 * q2 + 1], v1 = vv[rr][2 * q2 + 1];
-                            x[2 * q2] = fmaf(w.x, u0, fmaf(w.y, v0, x[2 * q2]));
-                            x[2 * q2 + 1] = fmaf(w.z, u1, fmaf(w.w, v1, x[2 * q2 + 1]));
-                            y[2 * q2] = fmaf(w.y, u0, fmaf(-w.x, v0, y[2 * q2]));
-                            y[2 * q2 + 1] = fmaf(w.w, u1, fmaf(-w.z, v1, y[2 * q2 + 1]));
-                        }
-                    }
-                    // sum over the warp's 32 lanes by recursive halving: each exchange sends
-                    // the half of the q-values this lane does not keep; after log2(kQP)
-                    // steps a lane holds one q (set by its top lane bits), the remaining
-                    // exchanges add the lanes that hold the same q
-                    constexpr int kLanesPerQ = 32 / kQP;
-                    auto warp_sum = [&](float (&z)[kQP]) {
-#pragma unroll
-                        for (int hh = kQP / 2, o = 16; hh >= 1; hh >>= 1, o >>= 1) {
-                            const bool up = (lane & o) != 0;
-#pragma unroll
-                            for (int k = 0; k < hh; ++k) {
-                                const float send = up ? z[k] : z[k + hh];
-                                const float keep = up ? z[k + hh] : z[k];
-                                z[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-                            }
-                        }
-#pragma unroll
-                        for (int o = kLanesPerQ / 2; o >= 1; o >>= 1)
-                            z[0] += __shfl_xor_sync(0xffffffffu, z[0], o);
-                    };
-                    const int qme = lane / kLanesPerQ;
-                    double *slot = qred + ((pass * kEpiWarps + ew) * kQP + qme) * 2;
-                    warp_sum(x);
-                    if (lane % kLanesPerQ == 0) slot[0] = (double)x[0];
-                    if (E.q_parts == 2) {
-                        warp_sum(y);
-                        if (lane % kLanesPerQ == 0) slot[1] = (double)y[0];
-                    }
-                }
-                epi_sync(kEpiThreads);
-                for (int q = et; q < E.n_q; q += kEpiThreads)
-                    for (int part = 0; part < E.q_parts; ++part) {
-                        double sq = 0.0;
-                        for (int w = 0; w < kEpiWarps; ++w)
-                            sq += qred[(((q / kQP) * kEpiWarps + w) * kQP + q % kQP) * 2 + part];
-                        qacc[2 * q + part] += sq;
-                    }
-            }
-            // accumulator buffer free for the MMA warp
+            // without phase weights the accumulator buffer is free for the MMA warp now;
+            // with them the BF16 copy of G is in place and the MMA thread may start the
+            // phase product (the accumulator stays taken until that product is complete)
+            if (ph) tmem_wait_st();
             tc_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
+            if (lane == 0) mbar_arrive(ph ? conv : tempty0 + 8 * acc);
             epi_sync(kEpiThreads);  // all private bins written
             if (E.n_bins > 0) {
-                const int NWp = E.use_window ? E.NW : E.n_bins;
-                // epilogue warp ew reduces bins b = ew (mod 8): 8 conflict-free loads per
-                // lane, an FP32 tree over the 256 entries, one FP64 add per bin (the FP64
-                // pipe is narrow on this part, so FP64 work is kept per bin, not per row)
-                for (int b = ew; b < NWp; b += kEpiWarps) {
-                    float *row = bins + b * kBinStride;
-                    float v = 0.f;
+                // private rows this tile may have written: with the branch-free position
+                // path only the tile's own bin range, else the whole window / bin set
+                const int NWp = !E.use_window ? E.n_bins
+                                : (!lattice && pos_fit ? min(E.NW, bhi_tile - blo + 1) : E.NW);
+                // epilogue warp ew reduces bins b = 4 ew + u (mod 4 EW), four at a time (the
+                // four shuffle trees overlap): conflict-free loads, an FP32 tree over the
+                // stride, one FP64 add per bin (the FP64 pipe is narrow on this part, so
+                // FP64 work is kept per bin, not per row)
+                for (int b0 = 4 * ew; b0 < NWp; b0 += 4 * kEpiWarps) {
+                    float v4[4];
 #pragma unroll
-                    for (int m = 0; m < kBinStride / 32; ++m) {
-                        v += row[lane + 32 * m];
-                        row[lane + 32 * m] = 0.f;
+                    for (int u = 0; u < 4; ++u) {
+                        v4[u] = 0.f;
+                        if (b0 + u < NWp) {
+                            float *row = bins + (b0 + u) * kBinStride;
+#pragma unroll
+                            for (int m = 0; m < kBinStride / 32; ++m) {
+                                v4[u] += row[lane + 32 * m];
+                                row[lane + 32 * m] = 0.f;
+                            }
+                        }
                     }
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0 && blo + b < E.n_bins) cacc[blo + b] += (double)v;
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) v4[u] += __shfl_xor_sync(0xffffffffu, v4[u], o);
+                    if (lane == 0)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (b0 + u < NWp && blo + b0 + u < E.n_bins)
+                                cacc[blo + b0 + u] += (double)v4[u];
                 }
                 if (E.use_window) {
                     epi_sync(kEpiThreads);  // the fallback bins update the same accumulators
@@ -1129,8 +1237,67 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     }
                 }
             }
+            if (ph) {
+                // Phase product of each pass: P[r][o] = sum_c G_rc W_co, u = P[.][0:64)
+                // (cosine column weights), v = P[.][64:128) (sine).  Row r adds
+                // cos(q.r_i) u + sin(q.r_i) v (cosine part) and sin(q.r_i) u - cos(q.r_i) v
+                // (sine part), the angle-difference identities of Eq. 6's weight; the warp
+                // then sums its 32 rows by recursive halving (each lane ends with one q
+                // of the 16) and adds it to the CTA's FP64 sums.
+                const float4 *cs4 = reinterpret_cast<const float4 *>(E.cs) +
+                                    (int64_t)ic * (E.nq_pad / 2);
+                const uint32_t pt = tmem + ((uint32_t)(q4 * 32) << 16) + 2 * BN;
+                for (int pp = 0; pp < E.npass && ok; ++pp) {
+                    const bool gotp = mbar_wait(pfull, n_pass & 1, args.err, DEV_TIMEOUT_EPI);
+                    ++n_pass;
+                    ok = epi_sync_and(gotp, kEpiThreads);
+                    if (!ok) break;
+                    tc_after();
+                    // (with 8 epilogue warps the two warps of a lane quarter take half of
+                    // the pass's q-vectors each)
+                    constexpr int kJ = kPhaseQ / 16 / kHalves;
+                    for (int j = half * kJ; j < (half + 1) * kJ; ++j) {
+                        const int q0 = pp * kPhaseQ + 16 * j;
+                        if (q0 >= E.n_q) break;
+                        uint32_t u[16], w[16];
+                        tmem_ld16(pt + 16 * j, u);
+                        tmem_ld16(pt + kPhaseQ + 16 * j, w);
+                        float4 c4[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) c4[k] = cs4[q0 / 2 + k];
+                        tmem_wait16x2(u, w);
+                        float x[16], y[16];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const float ca = c4[k].x, sa = c4[k].y, cb = c4[k].z, sb = c4[k].w;
+                            const float u0 = __uint_as_float(u[2 * k]), v0 = __uint_as_float(w[2 * k]);
+                            const float u1 = __uint_as_float(u[2 * k + 1]);
+                            const float v1 = __uint_as_float(w[2 * k + 1]);
+                            x[2 * k] = fmaf(ca, u0, sa * v0);
+                            x[2 * k + 1] = fmaf(cb, u1, sb * v1);
+                            y[2 * k] = fmaf(sa, u0, -ca * v0);
+                            y[2 * k + 1] = fmaf(sb, u1, -cb * v1);
+                        }
+                        const int qme = q0 + (lane >> 1);
+                        const float xs = warp_sum16(x, lane);
+                        if ((lane & 1) == 0 && qme < E.n_q) atomicAdd(&qacc[2 * qme], (double)xs);
+                        if (E.q_parts == 2) {
+                            const float ys = warp_sum16(y, lane);
+                            if ((lane & 1) == 0 && qme < E.n_q)
+                                atomicAdd(&qacc[2 * qme + 1], (double)ys);
+                        }
+                    }
+                    // P read: the next pass (or item) may overwrite it
+                    tc_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(pempty);
+                }
+                if (!ok) break;
+                // the phase product has consumed G: the accumulator buffer is free
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
+            }
         }
-        cp_async_wait_all();  // no copy into this CTA's shared memory outlives it
         epi_sync(kEpiThreads);
         if (ok && cur_p >= 0) flush_acc(cur_p, cur_t);
     }
@@ -1138,7 +1305,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     __syncthreads();
     if (warp == 1) {
         tc_after();
-        tmem_dealloc(tmem, kTmemCols);
+        tmem_dealloc(tmem, kTmemAlloc);
     }
 }
 
@@ -1158,7 +1325,8 @@ int launch_one(const LaunchArgs &a, size_t smem, int sm_count, cudaStream_t s)
 }  // namespace
 
 // Launch one precision form.  Instantiated combinations (the rest are rejected):
-//   BN = 256 with 4 or 8 epilogue warps; BN = 128 with 4 warps.
+//   BN = 256 and BN = 192 with 4 or 8 epilogue warps; BN = 128 with 4 warps (192 and 128
+//   are the tile widths that leave TMEM room for the phase product).
 template <int FORM>
 int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int ew, int sm_count,
                    cudaStream_t s)
@@ -1166,6 +1334,8 @@ int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int ew, int sm_co
     constexpr int SWB = FORM == ASD_SPLIT_BF16 ? 64 : 128;
     if (BN == 256 && ew == 4) return launch_one<FORM, 256, SWB, 4>(a, smem, sm_count, s);
     if (BN == 256 && ew == 8) return launch_one<FORM, 256, SWB, 8>(a, smem, sm_count, s);
+    if (BN == 192 && ew == 4) return launch_one<FORM, 192, SWB, 4>(a, smem, sm_count, s);
+    if (BN == 192 && ew == 8) return launch_one<FORM, 192, SWB, 8>(a, smem, sm_count, s);
     if (BN == 128 && ew == 4) return launch_one<FORM, 128, SWB, 4>(a, smem, sm_count, s);
     set_error_text("tensor-core kernel: unsupported (tile width, epilogue warps)");
     return ASD_EUNSUPPORTED;

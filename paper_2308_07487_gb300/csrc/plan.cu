@@ -103,9 +103,26 @@ static EpiParams epi_of(const asd_corr_plan *p)
         }
     }
     e.nq_pad = (p->n_q + kQChunk - 1) / kQChunk * kQChunk;
+    e.npass = p->tc && p->n_q > 0 ? (p->n_q + kPhaseQ - 1) / kPhaseQ : 0;
     e.q_parts = p->q_parts;
     e.cs = p->cs;
     return e;
+}
+
+// Round to the nearest BF16 (ties to even); the inputs here are finite.
+static uint16_t bf16_rn(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+static double bf16_value(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
 }
 
 static void carve(char *&cur, size_t bytes, void **out)
@@ -175,6 +192,17 @@ static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int6
                            (uint32_t)p->BK, (uint32_t)p->BN, p->swizzle_bytes);
         if (rc) return rc;
     }
+    // phase column weights: boxes of 64 sites x one pass (128 rows), BF16, 128-byte swizzle
+    if (p->W) {
+        const int npass = (p->n_q + kPhaseQ - 1) / kPhaseQ;
+        const size_t plane = (size_t)npass * 2 * kPhaseQ * p->Wld * 2;
+        for (int pl = 0; pl < 2; ++pl) {
+            int rc = encode_2d(&tp->mapW[pl], static_cast<char *>(p->W) + pl * plane, 2,
+                               (uint64_t)p->Wld, (uint64_t)npass * 2 * kPhaseQ, 64, 2 * kPhaseQ,
+                               128);
+            if (rc) return rc;
+        }
+    }
     tp->N = (int)p->N;
     tp->row_begin = (int)row_begin;
     tp->row_end = (int)row_end;
@@ -242,6 +270,7 @@ void asd_pair_corr_plan_destroy(asd_corr_plan *p)
     cudaFree(p->thr);
     cudaFree(p->lut);
     cudaFree(p->cs);
+    cudaFree(p->W);
     cudaFree(p->sqF);
     cudaFree(p->counter);
     cudaFree(p->inv_counts);
@@ -278,16 +307,21 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
     ASD_CHECK_ARG(d->n_bins > 0 || d->n_q > 0, "nothing to compute (n_bins = n_q = 0)");
     ASD_CHECK_ARG(d->n_bins == 0 || d->bin_width > 0, "bin_width must be > 0");
     ASD_CHECK_ARG(d->n_q == 0 || d->q, "q required when n_q > 0");
-    ASD_CHECK_ARG(d->tile_n == 0 || d->tile_n == 128 || d->tile_n == 256, "tile_n: 0, 128, 256");
+    ASD_CHECK_ARG(d->tile_n == 0 || d->tile_n == 128 || d->tile_n == 192 || d->tile_n == 256,
+                  "tile_n: 0, 128, 192, 256");
     ASD_CHECK_ARG(d->raster_m >= 0 && d->raster_m <= 64, "raster_m: 0..64");
     ASD_CHECK_ARG(d->stages == 0 || (d->stages >= 2 && d->stages <= 8), "stages: 0 or 2..8");
     ASD_CHECK_ARG(d->k_chunks >= 0 && d->k_chunks <= 256, "k_chunks: 0..256");
     ASD_CHECK_ARG(d->epi_warps == 0 || d->epi_warps == 4 || d->epi_warps == 8, "epi_warps: 0, 4 or 8");
     {
-        // instantiated tensor-core kernels: 256-wide tiles with either warp count; 128-wide
-        // tiles with 4 warps
-        const int ew = d->epi_warps ? d->epi_warps : 4;
-        ASD_CHECK_ARG(!(d->tile_n == 128 && ew != 4), "tile_n = 128 needs 4 epilogue warps");
+        // instantiated tensor-core kernels: 256- and 192-wide tiles with either warp
+        // count; 128-wide tiles with 4 warps.  Phase weights run on the tensor core, whose
+        // product needs 128 TMEM columns beside the two accumulators: tiles of at most 192
+        // columns.
+        ASD_CHECK_ARG(!(d->tile_n == 128 && d->epi_warps == 8),
+                      "tile_n = 128 needs 4 epilogue warps");
+        if (d->precision != ASD_FP32 && d->n_q > 0)
+            ASD_CHECK_ARG(d->tile_n != 256, "phase weights need tile_n <= 192");
     }
     ASD_CHECK_ARG(d->static_schedule == 0 || d->static_schedule == 1, "static_schedule: 0 or 1");
     ASD_CHECK_ARG(d->phase_sine == 0 || d->phase_sine == 1, "phase_sine: 0 or 1");
@@ -353,27 +387,29 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         p->n_copies = 16 / p->elem_bytes;
         p->swizzle_bytes = d->precision == ASD_SPLIT_BF16 ? 64 : 128;
         p->BK = p->swizzle_bytes / p->elem_bytes;
-        p->BN = d->tile_n ? d->tile_n : (p->N <= 4096 ? 128 : 256);
+        p->BN = d->tile_n ? d->tile_n : (p->N <= 4096 ? 128 : (d->n_q > 0 ? 192 : 256));
         p->Rpad = (R + 7) / 8 * 8;
         p->Kseg = ((int64_t)3 * d->T0 + p->BK - 1) / p->BK * p->BK;
-        // epilogue warps: 4 by default (one launch of a batch needs one count).  8 warps
-        // (opt-in, 4 q per phase pass) cap the registers at 168: measured, they help
-        // single-product BF16 binning with a short K on one large problem and bins + 64 q
-        // on the jittered glass by 3-4 %, and lose 4-7 % with bins alone there
-        p->EW = d->epi_warps ? d->epi_warps : 4;
-        // instantiated kernels: 256-wide tiles with either warp count; 128-wide tiles with
-        // 4 warps
-        if (p->EW != 4) p->BN = 256;  // combination checked up front
+        // epilogue warps: two per scheduler (8) hide the latency of the binning epilogue
+        // where it is longest, the FP32 position rule (measured on the 32^3 jittered glass,
+        // split-BF16 with two K chunks: 453 against 340 TFLOP/s); lattices keep 4 (their
+        // packed-coordinate binning is short: 540 against 492 on the 26^3 lattice).
+        // 128-wide tiles run with 4 warps.
+        p->EW = d->epi_warps ? d->epi_warps
+                             : (d->geometry == ASD_GEOM_POSITIONS && p->BN != 128 ? 8 : 4);
+        if (p->EW != 4 && p->BN == 128) p->BN = d->n_q > 0 ? 192 : 256;
         // K chunks: split-BF16 is the FP32-accurate form; each chunk's accumulator starts
-        // from zero, bounding the FP32 accumulation error of the tensor core to ~1536
-        // terms per partial sum at any K (measured: 16 chunks of 6144 at K = 98304 leave
-        // 3.4e-5 per bin; chunks of ~1536 stay below 1e-5).  The other forms are limited
-        // by their operand rounding.  Each chunk's binning pass runs while the next
-        // chunk's MMAs do, so chunks of this length cost little.
+        // from zero, bounding the FP32 accumulation error of the tensor core (it adds each
+        // MMA's products into the FP32 accumulator with truncation) to ~768 terms per
+        // partial sum at any K (measured on the 64^3 glass, K = 1536, 12 random blocks of
+        // 16 rows: one chunk 1.1e-5 worst per bin, in a bin of 4 pairs; two 7.9e-6; on the
+        // 40^3 lattice, K = 3000: one chunk 1.4e-5, two 7.9e-6).  The other forms are
+        // limited by their operand rounding.  Each chunk's epilogue runs while the next
+        // chunk's MMAs do.
         const int64_t nk = (int64_t)p->S * (p->Kseg / p->BK);
         int kc = d->k_chunks;
         if (kc == 0)
-            kc = d->precision == ASD_SPLIT_BF16 ? (int)((p->S * p->Kseg + 1535) / 1536) : 1;
+            kc = d->precision == ASD_SPLIT_BF16 ? (int)((p->S * p->Kseg + 767) / 768) : 1;
         if (kc > 256) kc = 256;
         if (kc > nk) kc = (int)nk;
         p->k_chunks = kc < 1 ? 1 : kc;
@@ -512,6 +548,42 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
             }
             if (cudaMemcpy(p->cs, cs.data(), sizeof(float2) * cs.size(), cudaMemcpyHostToDevice))
                 return fail(ASD_ECUDA);
+            // column weights of the tensor-core phase product, pass by pass: row
+            // pp * 128 + o holds cos(q.r_c) of q = 64 pp + o (o < 64) or sin(q.r_c) of
+            // q = 64 pp + o - 64, zero for q >= n_q, as BF16 hi = RN(x) and
+            // lo = RN(x - hi) in two planes
+            if (tc) {
+                const int npass = (p->n_q + kPhaseQ - 1) / kPhaseQ;
+                p->Wld = (p->N + 7) / 8 * 8;
+                const size_t rows = (size_t)npass * 2 * kPhaseQ, plane = rows * p->Wld;
+                std::vector<uint16_t> W(2 * plane, 0);
+                for (int64_t c = 0; c < p->N; ++c) {
+                    double r[3];
+                    for (int a = 0; a < 3; ++a)
+                        r[a] = d->geometry == ASD_GEOM_LATTICE ? (double)d->coords[3 * c + a]
+                                                               : (double)d->pos[3 * c + a];
+                    for (int q = 0; q < p->n_q; ++q) {
+                        const double ph = d->q[3 * q] * r[0] + d->q[3 * q + 1] * r[1] +
+                                          d->q[3 * q + 2] * r[2];
+                        const double x2[2] = {cos(ph), sin(ph)};
+                        for (int part = 0; part < 2; ++part) {
+                            const size_t row = (size_t)(q / kPhaseQ) * 2 * kPhaseQ +
+                                               part * kPhaseQ + q % kPhaseQ;
+                            const uint16_t hi = bf16_rn((float)x2[part]);
+                            W[row * p->Wld + c] = hi;
+                            W[plane + row * p->Wld + c] =
+                                bf16_rn((float)(x2[part] - bf16_value(hi)));
+                        }
+                    }
+                }
+                if (cudaMalloc(&p->W, sizeof(uint16_t) * W.size()) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(ASD_ENOMEM);
+                }
+                if (cudaMemcpy(p->W, W.data(), sizeof(uint16_t) * W.size(),
+                               cudaMemcpyHostToDevice))
+                    return fail(ASD_ECUDA);
+            }
             // transforms of the separable phase form (asd_pair_corr_sq_separable)
             const size_t fb = sizeof(double) * 2 * (size_t)p->n_q * p->S * 3 * p->F;
             if (cudaMalloc(&p->sqF, fb) != cudaSuccess) {
@@ -602,21 +674,34 @@ int asd_pair_corr_contract(asd_corr_plan *p, int64_t row_begin, int64_t row_end,
                            double *Sq_sum, void *stream)
 {
     ASD_CHECK_ARG(p, "null plan");
+    return asd_pair_corr_contract_range(p, row_begin, row_end, 0, p->n_t, C_sum, Sq_sum, stream);
+}
+
+int asd_pair_corr_contract_range(asd_corr_plan *p, int64_t row_begin, int64_t row_end,
+                                 int32_t t_begin, int32_t t_end, double *C_sum, double *Sq_sum,
+                                 void *stream)
+{
+    ASD_CHECK_ARG(p, "null plan");
+    ASD_CHECK_ARG(0 <= t_begin && t_begin <= t_end && t_end <= p->n_t, "bad displacement range");
     ASD_CHECK_ARG(p->prepared_traj, "asd_pair_corr_prepare has not been called");
     ASD_CHECK_ARG(p->prepared_begin <= row_begin && row_begin <= row_end &&
                       row_end <= p->prepared_end,
                   "rows outside the prepared range");
     ASD_CHECK_ARG(p->n_bins == 0 || C_sum, "C_sum required when n_bins > 0");
     ASD_CHECK_ARG(p->n_q == 0 || Sq_sum, "Sq_sum required when n_q > 0");
-    if (row_begin == row_end) return ASD_OK;
+    if (row_begin == row_end || t_begin == t_end) return ASD_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!p->tc) return launch_simt(p, p->prepared_traj, row_begin, row_end, C_sum, Sq_sum, s);
+    if (!p->tc)
+        return launch_simt(p, p->prepared_traj, row_begin, row_end, t_begin, t_end, C_sum, Sq_sum,
+                           s);
     TcOverride ov{};
     ov.active = 1;
     ov.row_begin = (int)row_begin;
     ov.row_end = (int)row_end;
+    ov.t_begin = t_begin;
+    ov.n_t = t_end - t_begin;
     ov.tiles_m = (int)((row_end - row_begin + kBM - 1) / kBM);
-    ov.n_tiles = tc_work_items(p->n_t, p->k_chunks, ov.tiles_m, p->h_prob->tiles_n);
+    ov.n_tiles = tc_work_items(ov.n_t, p->k_chunks, ov.tiles_m, p->h_prob->tiles_n);
     ov.C_sum = C_sum;
     ov.Sq_sum = Sq_sum;
     return launch_tc(p->d_prob, 1, ov.n_tiles, ov, p->prec, p->BN, p->swizzle_bytes, p->stages,

@@ -19,7 +19,7 @@ import json
 import os
 
 DEFAULT_SPACE = {
-    "tile_n": [128, 256],
+    "tile_n": [128, 192, 256],
     "epi_warps": [4, 8],
     "raster_m": [8, 16, 32, 64],
     "stages": [0, 3],
@@ -28,17 +28,20 @@ DEFAULT_SPACE = {
 
 def candidates(space=None, n_q=0, N=None):
     """Valid combinations of the knobs (the plan's instantiated kernels): 128-wide tiles
-    run with 4 epilogue warps; tiles wider than the problem are skipped.  `n_q` is kept
-    for callers: 8 epilogue warps are valid with phase weights too (their phase loop takes
-    4 q per pass and fits the 168-register cap)."""
+    run with 4 epilogue warps; with phase weights (n_q > 0) the phase product takes 128
+    TMEM columns beside the two accumulators, so tiles are at most 192 wide; tiles wider
+    than the problem are skipped."""
     sp = dict(DEFAULT_SPACE if space is None else space)
     out = []
     keys = sorted(sp)
     for vals in itertools.product(*(sp[k] for k in keys)):
         c = dict(zip(keys, vals))
-        if c.get("tile_n") == 128 and c.get("epi_warps", 4) != 4:
+        tn, ew = c.get("tile_n", 0), c.get("epi_warps", 4)
+        if tn == 128 and ew != 4:
             continue
-        if N is not None and c.get("tile_n") == 256 and N <= 128:
+        if n_q > 0 and tn == 256:
+            continue
+        if N is not None and tn and tn > 128 and N <= 128:
             continue
         out.append(c)
     return out

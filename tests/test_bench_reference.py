@@ -25,12 +25,16 @@ def test_reference_arm_json_line():
     assert out["metric"] == bench.METRIC and out["unit"] == "TFLOP/s"
     assert out["higher_is_better"] is True and out["n_gpus"] == 1
     assert out["steps"] == 1 and out["warmup"] == 0
-    assert out["config"]["workload"] == "sc40_periodic_N64000"
+    assert out["config"]["workload"] == "glass64_open_N262144"
     assert out["value"] > 0 and out["ms_per_step"] > 0
     cb = out["cpu_baseline"]
     # the threads the oracle ran on, not the machine's CPU count
     assert cb["kind"] == "oracle" and cb["cores"] == 3 and cb["value"] == out["value"]
     assert cb["sample"] == out["config"]["sample"]
+    # the oracle parallelises over rows: at least four rows per thread keep each one busy
+    r0, r1 = (int(x) for x in cb["sample"].split()[1].split(".."))
+    assert r1 - r0 >= 4 * cb["cores"]
+    assert "256 bins" in cb["sample"] and "64 q" in cb["sample"]
     e2e = out["e2e"]
     assert e2e["value"] == out["value"] and e2e["unit"] == out["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
@@ -54,4 +58,7 @@ def test_reference_arm_two_ranks_prints_one_line():
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2
     # rank 0 uses every CPU of the process although the launcher sets one thread per rank
-    assert out["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+    cb = out["cpu_baseline"]
+    assert cb["cores"] == len(os.sched_getaffinity(0))
+    r0, r1 = (int(x) for x in cb["sample"].split()[1].split(".."))
+    assert r1 - r0 >= 4 * cb["cores"]

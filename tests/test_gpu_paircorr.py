@@ -217,17 +217,18 @@ def test_phase_on_lattice_row_range(asd, form):
 
 
 @pytest.mark.parametrize("form", ["split_bf16", "bf16", "tf32"])
+@pytest.mark.parametrize("tile_n,ew", [(128, 4), (192, 4), (192, 8)])
 @pytest.mark.parametrize("sine", [False, True])
-def test_phase_eight_epilogue_warps(asd, form, sine):
-    """Eight epilogue warps (two per TMEM lane quarter, half the columns each; 4 q per
-    pass of the phase loop): 13 q (a partial last pass), bins at the same time, rows from
-    mid-tile, cosine and sine parts."""
+def test_phase_tile_widths(asd, form, tile_n, ew, sine):
+    """The tensor-core phase product at both tile widths that leave it TMEM room, with 4
+    and 8 epilogue warps: 13 q (a partial pass), bins at the same time, rows from mid-tile
+    (ragged row and column tiles), cosine and sine parts.  Wider tiles are refused."""
     lat = synth.hypercubic(9, 3, False, jitter=0.1, seed=5)
     q = synth.q_vectors_glass()[::5]
     tr = synth.traj_precess(lat.n_sites, 30, seed=9)
     rows = (20, 700)
     plan = asd.CorrPlan.for_lattice(lat, 30, 18, 7, 0.5, 16, precision=form, q=q,
-                                    phase_sine=sine, tile_n=256, epi_warps=8)
+                                    phase_sine=sine, tile_n=tile_n, epi_warps=ew)
     C = torch.zeros((7, 16), dtype=torch.float64, device="cuda")
     Sq = torch.zeros((7, len(q), 2) if sine else (7, len(q)), dtype=torch.float64,
                      device="cuda")
@@ -241,6 +242,9 @@ def test_phase_eight_epilogue_warps(asd, form, sine):
     if sine:
         assert_phase(got[..., 1], ref, form, "sin")
     assert oracle.bin_error(C.cpu().numpy(), ref).max() <= TOL[form]
+    for kw in ({"tile_n": 256}, {"tile_n": 128, "epi_warps": 8}):
+        with pytest.raises(asd.AsdError):
+            asd.CorrPlan.for_lattice(lat, 30, 18, 7, 0.5, 16, precision=form, q=q, **kw)
 
 
 @pytest.mark.parametrize("form", FORMS)
@@ -332,3 +336,36 @@ def test_maximum_q_count(asd):
     got = run_gpu(asd, lat, tr, 8, 3, 0.5, 6, "split_bf16", q=q)
     ref = oracle_ref(lat, tr, 8, 3, 0.5, 6, q=q)
     assert_parity(got, ref, "split_bf16", q=True)
+
+
+@pytest.mark.parametrize("form", ["split_bf16", "fp32", "bf16"])
+def test_displacement_range(asd, form):
+    """asd_pair_corr_contract_range: displacements in blocks [0, 3), [3, 7), [7, 11)
+    accumulate into one output (bins and phase, rows from mid-tile) and match the oracle;
+    a single block touches only its own rows of the outputs; an empty or reversed range
+    is a no-op or an error."""
+    lat = synth.hypercubic(7, 3, False, jitter=0.1, seed=3)
+    q = synth.q_vectors_glass()[::5]
+    tr = synth.traj_precess(lat.n_sites, 30, seed=8)
+    rows = (20, 300)
+    plan = asd.CorrPlan.for_lattice(lat, 30, 18, 11, 0.5, 12, precision=form, q=q)
+    plan.prepare(torch.from_numpy(np.ascontiguousarray(tr[:, None])).cuda())
+    C = torch.zeros((11, 12), dtype=torch.float64, device="cuda")
+    Sq = torch.zeros((11, len(q)), dtype=torch.float64, device="cuda")
+    for tb in ((0, 3), (3, 7), (7, 11), (5, 5)):
+        plan.contract(C, Sq, rows=rows, t_range=tb)
+    C1 = torch.zeros_like(C)
+    plan.contract(C1, torch.zeros_like(Sq), rows=rows, t_range=(3, 7))
+    with pytest.raises(asd.AsdError):
+        plan.contract(C1, torch.zeros_like(Sq), rows=rows, t_range=(7, 3))
+    with pytest.raises(asd.AsdError):
+        plan.contract(C1, torch.zeros_like(Sq), rows=rows, t_range=(0, 12))
+    assert asd.sync_status() == 0
+    plan.close()
+    ref = oracle.pair_corr(tr, 18, list(range(11)), oracle.Geometry.of_lattice(lat), 0.5, 12,
+                           q=q, rows=rows)
+    assert_parity({"C_sum": C.cpu().numpy(), "Sq_sum": Sq.cpu().numpy()}, ref, form, q=True)
+    c1 = C1.cpu().numpy()
+    assert not c1[:3].any() and not c1[7:].any() and c1[3:7].any()
+    assert oracle.bin_error(c1[3:7], {k: (v[3:7] if k in ("C_sum", "M_abs") else v)
+                                      for k, v in ref.items()}).max() <= TOL[form]

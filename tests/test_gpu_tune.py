@@ -9,7 +9,7 @@ from paper_2308_07487_gb300 import synth, tune
 
 pytestmark = pytest.mark.gpu
 
-SPACE = {"tile_n": [128, 256], "epi_warps": [4, 8], "raster_m": [8, 16]}
+SPACE = {"tile_n": [128, 192, 256], "epi_warps": [4, 8], "raster_m": [8, 16]}
 
 
 @pytest.fixture(scope="module")
