@@ -226,6 +226,15 @@ def bin_error(C_sum_test, res):
     return np.where(M > 0, d / np.where(M > 0, M, 1.0), d)
 
 
+def sampled_bin_error(C_sum_test, res, min_pairs=16):
+    """bin_error over the bins that hold at least `min_pairs` ordered pairs of the sample,
+    0 elsewhere.  A row sample of a large problem leaves its far bins with a handful of
+    pairs, where the per-bin error is the error of single pair terms; those bins are
+    held to the rounding scale instead (rounding_ratio)."""
+    e = bin_error(C_sum_test, res)
+    return np.where(np.asarray(res["counts"])[None, :] >= min_pairs, e, 0.0)
+
+
 def phase_error(Sq_test, res, part="cos"):
     """Per-(t, q) error of a tested phase sum against the oracle, scaled by that q's
     magnitude sum: |Sq_test - Sq_ref| / Sq_abs (cosine part) or against Sq_im with

@@ -64,6 +64,10 @@ def test_two_site_mixed_signs_hand_computed():
     np.testing.assert_allclose(oracle.phase_error(r["Sq_sum"] + 0.7, r)[1],
                                0.7 / np.array(g["Sq_abs"][1]))
     np.testing.assert_allclose(oracle.phase_error(r["Sq_im"] + 0.2, r, "sin")[1, 0], 0.2 / 4)
+    # the sampled per-bin error keeps bins with enough pairs and zeroes the others
+    np.testing.assert_array_equal(oracle.sampled_bin_error(bumped, r, min_pairs=2),
+                                  oracle.bin_error(bumped, r))
+    assert not oracle.sampled_bin_error(bumped, r, min_pairs=3).any()
 
 
 def test_bin_rule_golden():
