@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--medium", action="store_true", help="profiling workload (ncu)")
     ap.add_argument("--no-extras", action="store_true", help="skip form sweep, CPU baseline, e2e")
     ap.add_argument("--ncu", action="store_true", help="one step, nothing else (for ncu)")
+    ap.add_argument("--mlp-depth", type=int, default=2, choices=[2, 3],
+                    help="learned workload: hidden layers of the proposal network")
     ap.add_argument("--nt-per-step", type=int, default=0,
                     help="displacements per step (0: the workload's default)")
     ap.add_argument("--workload", default="glass64",
@@ -657,7 +659,7 @@ def run_learned(args):
     X, Y = torch.cat(xs), torch.cat(ys)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
-    net = asd.Mlp(12, seed=5)
+    net = asd.Mlp(12, seed=5, depth=args.mlp_depth)
     gen = torch.Generator(device="cuda").manual_seed(0)
     B, steps = 16384, 1500
     t0 = time.perf_counter()
@@ -771,7 +773,7 @@ def run_learned(args):
         plan.close()
     dC = np.abs(res["learned"]["C"] - res["metropolis"]["C"])[:, :40].max()
     print(json.dumps({
-        "workload": "sq128_learned_proposal", "T": T, "starts": S,
+        "workload": "sq128_learned_proposal", "T": T, "starts": S, "mlp_depth": args.mlp_depth,
         "training": {"pairs": int(X.shape[0]), "steps": steps, "batch": B,
                      "data_s": t_data, "train_s": t_train, "nll_per_site": nll,
                      "nll_uniform": math.log(4 * math.pi)},

@@ -318,6 +318,10 @@ typedef struct asd_mlp {
     int32_t n_in, n_hidden;       /* n_in = 3 * z                                     */
     const uint16_t *W1, *W2, *W3; /* device bf16 [H][n_in], [H][H], [4][H]            */
     const float *b1, *b2, *b3;    /* device fp32 [H], [H], [4]                        */
+    int32_t depth;                /* hidden layers: 2 (0 reads as 2) or 3              */
+    const uint16_t *Wm;           /* depth 3: device bf16 [H][H], the third hidden layer
+                                     h3 = tanh(Wm h2 + bm) that feeds W3               */
+    const float *bm;              /* depth 3: device fp32 [H]                          */
 } asd_mlp;
 
 typedef struct asd_mc_stats {
@@ -345,14 +349,16 @@ int asd_thermalize(const asd_system *sys, int n_samples, float *spins, float T, 
  * extension of the Monte Carlo sampler of Section 2.1).  Maximum likelihood of a
  * site's spin given its neighbours' spins, on configurations from plain Monte Carlo.
  *
- * Parameter vector (device FP32, P = asd_mlp_param_count(n_in) entries):
- *   [W1 H*n_in][b1 H][W2 H*H][b2 H][W3 4*H][b3 4]   (H = 64, row-major [out][in]).
- * BF16 weight buffer (device, asd_mlp_param_count_bf16 entries): [W1][W2][W3].
- * An asd_mlp view for inference points W1..W3 into the BF16 buffer and b1..b3 into
- * the parameter vector.
+ * `depth` = hidden layers of H = 64 units: 2 or 3.  Parameter vector (device FP32,
+ * P = asd_mlp_param_count(n_in, depth) entries):
+ *   [W1 H*n_in][b1 H][W2 H*H][b2 H]([Wm H*H][bm H] when depth = 3)[W3 4*H][b3 4]
+ * (row-major [out][in]).  BF16 weight buffer (device, asd_mlp_param_count_bf16
+ * entries): [W1][W2]([Wm])[W3].  An asd_mlp view for inference points W1, W2, Wm, W3
+ * into the BF16 buffer and the biases into the parameter vector.  n_in outside 3..24 or
+ * depth outside {2, 3}: count 0, ASD_EINVAL from the other calls.
  * ------------------------------------------------------------------------------- */
-int64_t asd_mlp_param_count(int n_in);
-int64_t asd_mlp_param_count_bf16(int n_in);
+int64_t asd_mlp_param_count(int n_in, int depth);
+int64_t asd_mlp_param_count_bf16(int n_in, int depth);
 
 /* Initial parameters (Glorot / Xavier uniform): every weight of a layer with fan_in inputs
  * and fan_out outputs is drawn from U(-a, a), a = sqrt(6 / (fan_in + fan_out)), biases are
@@ -361,11 +367,13 @@ int64_t asd_mlp_param_count_bf16(int n_in);
  * w_bf16 device [asd_mlp_param_count_bf16] (nullable) receives the BF16 weight copy.
  * Random initial weights break the symmetry between hidden units that an all-zero start
  * keeps through training.  ASD_EINVAL for n_in outside 3..24. */
-int asd_mlp_init(float *params, int n_in, uint64_t seed, uint16_t *w_bf16, void *stream);
+int asd_mlp_init(float *params, int n_in, int depth, uint64_t seed, uint16_t *w_bf16,
+                 void *stream);
 
 /* BF16 weight copy [W1][W2][W3] of a parameter vector (round to nearest even), for an
  * asd_mlp view of parameters set by the caller.  params device FP32 [P]; w_bf16 device. */
-int asd_mlp_weights_bf16(const float *params, int n_in, uint16_t *w_bf16, void *stream);
+int asd_mlp_weights_bf16(const float *params, int n_in, int depth, uint16_t *w_bf16,
+                         void *stream);
 
 /* Training pairs: for sample s and site i (k = s*N + i), x[k] = the z neighbour spins
  * (3z floats, zeros for empty slots) and y[k] = S_i.  spins device [S][N][3];
@@ -383,8 +391,8 @@ int asd_mlp_loss_grad(const asd_mlp *net, int64_t n, const float *x, const float
 /* One Adam step (bias-corrected, step >= 1) on params with gradient grad * grad_scale,
  * moments m, v (device FP32 [P]); then writes the BF16 copy of the weights to w_bf16. */
 int asd_mlp_adam_step(float *params, const float *grad, float grad_scale, float *m, float *v,
-                      int n_in, float lr, float beta1, float beta2, float eps, int step,
-                      uint16_t *w_bf16, void *stream);
+                      int n_in, int depth, float lr, float beta1, float beta2, float eps,
+                      int step, uint16_t *w_bf16, void *stream);
 
 #ifdef __cplusplus
 }

@@ -53,7 +53,8 @@ class asd_system(ctypes.Structure):
 class asd_mlp(ctypes.Structure):
     _fields_ = [("n_in", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
                 ("W1", ctypes.c_void_p), ("W2", ctypes.c_void_p), ("W3", ctypes.c_void_p),
-                ("b1", ctypes.c_void_p), ("b2", ctypes.c_void_p), ("b3", ctypes.c_void_p)]
+                ("b1", ctypes.c_void_p), ("b2", ctypes.c_void_p), ("b3", ctypes.c_void_p),
+                ("depth", ctypes.c_int32), ("Wm", ctypes.c_void_p), ("bm", ctypes.c_void_p)]
 
 
 class asd_mc_stats(ctypes.Structure):
@@ -91,16 +92,16 @@ _SIGS = {
                                       ctypes.c_int, ctypes.c_int, ctypes.POINTER(asd_mlp),
                                       ctypes.c_float, ctypes.c_int, ctypes.c_uint64,
                                       ctypes.c_uint64, _VP, ctypes.POINTER(asd_mc_stats), _VP]),
-    "asd_mlp_param_count": (ctypes.c_int64, [ctypes.c_int]),
-    "asd_mlp_param_count_bf16": (ctypes.c_int64, [ctypes.c_int]),
-    "asd_mlp_init": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, _VP, _VP]),
-    "asd_mlp_weights_bf16": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "asd_mlp_param_count": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int]),
+    "asd_mlp_param_count_bf16": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int]),
+    "asd_mlp_init": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _VP, _VP]),
+    "asd_mlp_weights_bf16": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "asd_mlp_gather": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP, _VP, _VP, _VP]),
     "asd_mlp_loss_grad": (ctypes.c_int, [ctypes.POINTER(asd_mlp), ctypes.c_int64, _VP, _VP, _VP, _VP,
                                          _VP]),
     "asd_mlp_adam_step": (ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP, _VP, ctypes.c_int,
-                                         ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                                         ctypes.c_float, ctypes.c_int, _VP, _VP]),
+                                         ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_float, ctypes.c_int, _VP, _VP]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name, None)
@@ -289,14 +290,17 @@ def selftest_timeout(limit_ns, stream=None):
 
 class Mlp:
     """Learned-proposal network: FP32 master parameters, BF16 weight copy, Adam moments
-    (device tensors) and the asd_mlp view the sampler reads.  Without `params` the
-    library draws Glorot-uniform weights from `seed` (asd_mlp_init)."""
+    (device tensors) and the asd_mlp view the sampler reads.  `depth` = hidden layers of
+    64 units (2 or 3).  Without `params` the library draws Glorot-uniform weights from
+    `seed` (asd_mlp_init)."""
 
-    def __init__(self, n_in, params=None, device="cuda", seed=0):
+    def __init__(self, n_in, params=None, device="cuda", seed=0, depth=2):
         import torch
-        self.n_in = n_in
-        P = lib.asd_mlp_param_count(n_in)
-        Pw = lib.asd_mlp_param_count_bf16(n_in)
+        self.n_in, self.depth = n_in, depth
+        P = lib.asd_mlp_param_count(n_in, depth)
+        Pw = lib.asd_mlp_param_count_bf16(n_in, depth)
+        if P <= 0:
+            raise ValueError(f"bad network shape (n_in {n_in}, depth {depth})")
         self.P = P
         self.grad = torch.zeros(P, dtype=torch.float32, device=device)
         self.m = torch.zeros(P, dtype=torch.float32, device=device)
@@ -306,27 +310,33 @@ class Mlp:
         self.step = 0
         if params is None:
             self.params = torch.empty(P, dtype=torch.float32, device=device)
-            check(lib.asd_mlp_init(_ptr(self.params), n_in, int(seed), _ptr(self.wb), None),
-                  "mlp_init")
+            check(lib.asd_mlp_init(_ptr(self.params), n_in, depth, int(seed), _ptr(self.wb),
+                                   None), "mlp_init")
         else:
             p = np.asarray(params, np.float32)
             assert p.shape == (P,)
             self.params = torch.from_numpy(p.copy()).to(device)
             self._refresh_bf16()
+        # views into the packed vectors: [W1 b1][W2 b2]([Wm bm])[W3 b3] and [W1][W2]([Wm])[W3]
         H, es = 64, self.params.element_size()
         c = asd_mlp()
-        c.n_in, c.n_hidden = n_in, H
+        c.n_in, c.n_hidden, c.depth = n_in, H, depth
         wp, bs = self.wb.data_ptr(), self.wb.element_size()
-        c.W1, c.W2, c.W3 = wp, wp + H * n_in * bs, wp + (H * n_in + H * H) * bs
         pp = self.params.data_ptr()
-        c.b1 = pp + H * n_in * es
-        c.b2 = pp + (H * n_in + H + H * H) * es
-        c.b3 = pp + (H * n_in + H + H * H + H + 4 * H) * es
+        c.W1, c.b1 = wp, pp + H * n_in * es
+        c.W2, c.b2 = wp + H * n_in * bs, pp + (H * n_in + H + H * H) * es
+        hidden = H * n_in + H + H * H + H          # parameters before the next layer
+        wnext = H * n_in + H * H                   # BF16 weights before the next layer
+        if depth == 3:
+            c.Wm, c.bm = wp + wnext * bs, pp + (hidden + H * H) * es
+            hidden += H * H + H
+            wnext += H * H
+        c.W3, c.b3 = wp + wnext * bs, pp + (hidden + 4 * H) * es
         self.c = c
 
     def _refresh_bf16(self):
-        check(lib.asd_mlp_weights_bf16(_ptr(self.params), self.n_in, _ptr(self.wb), None),
-              "mlp_weights_bf16")
+        check(lib.asd_mlp_weights_bf16(_ptr(self.params), self.n_in, self.depth, _ptr(self.wb),
+                                       None), "mlp_weights_bf16")
 
     def loss_grad(self, x, y, n=None, stream=None):
         n = x.shape[0] if n is None else n
@@ -336,9 +346,9 @@ class Mlp:
     def adam(self, lr=1e-3, scale=1.0, b1=0.9, b2=0.999, eps=1e-8, stream=None):
         self.step += 1
         check(lib.asd_mlp_adam_step(_ptr(self.params), _ptr(self.grad), float(scale), _ptr(self.m),
-                                    _ptr(self.v), self.n_in, float(lr), float(b1), float(b2),
-                                    float(eps), self.step, _ptr(self.wb), _stream(stream)),
-              "mlp_adam_step")
+                                    _ptr(self.v), self.n_in, self.depth, float(lr), float(b1),
+                                    float(b2), float(eps), self.step, _ptr(self.wb),
+                                    _stream(stream)), "mlp_adam_step")
 
 
 class System:

@@ -211,7 +211,9 @@ extern "C" int asd_thermalize(const asd_system *sys, int n_samples, float *spins
                       "learned proposal needs a network");
         ASD_CHECK_ARG(net->n_in == 3 * sys->z && net->n_in <= kMlpMaxIn &&
                           net->n_hidden == kMlpHidden,
-                      "network shape must be [3z -> 64 -> 64 -> 4]");
+                      "network shape must be [3z -> 64 (x2 or x3) -> 4]");
+        ASD_CHECK_ARG(mlp_depth(*net) == 2 || (mlp_depth(*net) == 3 && net->Wm && net->bm),
+                      "network depth must be 2, or 3 with the third layer's weights");
         view = mlp_view(*net);
     }
     cudaStream_t s = (cudaStream_t)stream;

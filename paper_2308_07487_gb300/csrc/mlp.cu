@@ -1,19 +1,21 @@
 // Training of the learned von Mises-Fisher proposal (extension of the Monte Carlo of
 // Section 2.1; the paper has no learned component).
 //
-// Model: x (neighbour spins, 3z) -> tanh(W1 x + b1) -> tanh(W2 h1 + b2) -> o = W3 h2 + b3,
+// Model: x (neighbour spins, 3z) -> tanh(W1 x + b1) -> tanh(W2 h1 + b2)
+// [-> tanh(Wm h2 + bm) with three hidden layers] -> o = W3 h_last + b3,
 // mu = o[0:3]/|o[0:3]|, kappa = softplus(o[3]) + 1e-4.  Loss: the negative log-likelihood
 // of the site spin y under vMF(mu, kappa):
 //   NLL = -log kappa + log(2 pi) + kappa + log(1 - e^{-2 kappa}) - kappa mu.y
 // (log of the normaliser 4 pi sinh(kappa) / kappa written to stay finite).
 // Gradients: dNLL/dkappa = coth(kappa) - 1/kappa - mu.y (the Langevin function, with a
 // series below kappa = 1e-2), dNLL/dv = -kappa (y - mu (mu.y)) / |v| for v = o[0:3],
-// then back through the two tanh layers.
+// then back through the tanh layers.
 //
 // loss_grad: persistent blocks of 64 threads, one sample per thread per chunk.  The
-// activations and deltas of a chunk go to shared memory; each thread then owns a
-// strided set of parameter entries and sums their gradient over the chunk, so the
-// whole launch issues one global atomic per parameter per block.
+// activations and deltas of a chunk go to shared memory (rows padded to H + 1 floats, so
+// a thread's own row and a warp's sweep along one row are both free of bank conflicts);
+// each thread then owns a strided set of parameter entries and sums their gradient over
+// the chunk, so the whole launch issues one global atomic per parameter per block.
 #include <cuda_bf16.h>
 
 #include "asd_internal.h"
@@ -25,9 +27,22 @@ namespace {
 
 constexpr int H = kMlpHidden;
 constexpr int kChunk = 64;
+constexpr int kHP = H + 1;   // padded activation row
 
-__host__ __device__ inline int64_t n_params(int nin) { return (int64_t)H * nin + H + H * H + H + 4 * H + 4; }
-__host__ __device__ inline int64_t n_weights(int nin) { return (int64_t)H * nin + H * H + 4 * H; }
+// Packed parameters [W1 H*nin][b1 H] then, per further hidden layer, [W H*H][b H], then
+// [W3 4*H][b3 4]; BF16 weights [W1]([W2][Wm])[W3].
+__host__ __device__ inline int64_t n_params(int nin, int depth)
+{
+    return (int64_t)H * nin + H + (int64_t)(depth - 1) * (H * H + H) + 4 * H + 4;
+}
+__host__ __device__ inline int64_t n_weights(int nin, int depth)
+{
+    return (int64_t)H * nin + (int64_t)(depth - 1) * H * H + 4 * H;
+}
+inline bool shape_ok(int nin, int depth)
+{
+    return nin >= 3 && nin <= kMlpMaxIn && (depth == 2 || depth == 3);
+}
 
 __global__ void gather_kernel(int64_t N, int S, int z, const int *__restrict__ nbr,
                               const float *__restrict__ spins, float *__restrict__ x,
@@ -56,56 +71,66 @@ __global__ void __launch_bounds__(kChunk) loss_grad_kernel(MlpView net, int64_t 
                                                             float *__restrict__ grad,
                                                             double *__restrict__ loss)
 {
-    const int nin = net.n_in;
-    const int P = (int)n_params(nin);
+    const int nin = net.n_in, depth = net.depth;
+    const int P = (int)n_params(nin, depth);
     extern __shared__ float sm[];
-    float *W1 = sm;                    // [H][nin]
-    float *W2 = W1 + H * nin;          // [H][H]
-    float *W3 = W2 + H * H;            // [4][H]
-    float *Xs = W3 + 4 * H;            // [chunk][nin]
-    float *H1 = Xs + kChunk * nin;     // [chunk][H]
-    float *H2 = H1 + kChunk * H;       // [chunk][H]
-    float *D1 = H2 + kChunk * H;       // [chunk][H]
-    float *D2 = D1 + kChunk * H;       // [chunk][H]
-    float *DO = D2 + kChunk * H;       // [chunk][4]
-    float *acc = DO + kChunk * 4;      // [P] gradient accumulator of this block
+    float *W1 = sm;                                 // [H][nin]
+    float *Wh = W1 + H * nin;                       // [depth - 1][H][H]: W2 (Wm)
+    float *W3 = Wh + (depth - 1) * H * H;           // [4][H]
+    float *Xs = W3 + 4 * H;                         // [chunk][nin + 1]
+    float *Hs = Xs + kChunk * (nin + 1);            // [depth][chunk][kHP] activations
+    float *Ds = Hs + depth * kChunk * kHP;          // [depth][chunk][kHP] deltas
+    float *DO = Ds + depth * kChunk * kHP;          // [chunk][4]
+    float *acc = DO + kChunk * 4;                   // [P] gradient accumulator of this block
     __shared__ double lsum[kChunk];
 
     const int t = threadIdx.x;
     for (int e = t; e < H * nin; e += kChunk) W1[e] = __bfloat162float(net.W1[e]);
-    for (int e = t; e < H * H; e += kChunk) W2[e] = __bfloat162float(net.W2[e]);
+    for (int e = t; e < H * H; e += kChunk) Wh[e] = __bfloat162float(net.W2[e]);
+    if (depth == 3)
+        for (int e = t; e < H * H; e += kChunk) Wh[H * H + e] = __bfloat162float(net.Wm[e]);
     for (int e = t; e < 4 * H; e += kChunk) W3[e] = __bfloat162float(net.W3[e]);
     for (int e = t; e < P; e += kChunk) acc[e] = 0.f;
     double my_loss = 0.0;
     __syncthreads();
 
+    const int nin1 = nin + 1;
     for (int64_t base = (int64_t)blockIdx.x * kChunk; base < n; base += (int64_t)gridDim.x * kChunk) {
         const int64_t s = base + t;
         const bool ok = s < n;
         float xv[kMlpMaxIn];
         for (int c = 0; c < nin; ++c) {
             xv[c] = ok ? x[s * nin + c] : 0.f;
-            Xs[t * nin + c] = xv[c];
+            Xs[t * nin1 + c] = xv[c];
         }
-        float h1[H], h2[H], o[4];
+        // forward: hc = the current layer, hp = the one before it
+        float hp[H], hc[H], o[4];
 #pragma unroll
         for (int k = 0; k < H; ++k) {
             float a = __ldg(net.b1 + k);
             for (int c = 0; c < nin; ++c) a = fmaf(W1[k * nin + c], xv[c], a);
-            h1[k] = tanhf(a);
+            hc[k] = tanhf(a);
+            Hs[t * kHP + k] = hc[k];
         }
+        for (int l = 1; l < depth; ++l) {
+            const float *Wl = Wh + (l - 1) * H * H;
+            const float *bl = l == 1 ? net.b2 : net.bm;
 #pragma unroll
-        for (int k = 0; k < H; ++k) {
-            float a = __ldg(net.b2 + k);
+            for (int k = 0; k < H; ++k) hp[k] = hc[k];
 #pragma unroll
-            for (int c = 0; c < H; ++c) a = fmaf(W2[k * H + c], h1[c], a);
-            h2[k] = tanhf(a);
+            for (int k = 0; k < H; ++k) {
+                float a = __ldg(bl + k);
+#pragma unroll
+                for (int c = 0; c < H; ++c) a = fmaf(Wl[k * H + c], hp[c], a);
+                hc[k] = tanhf(a);
+                Hs[(l * kChunk + t) * kHP + k] = hc[k];
+            }
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float a = __ldg(net.b3 + k);
 #pragma unroll
-            for (int c = 0; c < H; ++c) a = fmaf(W3[k * H + c], h2[c], a);
+            for (int c = 0; c < H; ++c) a = fmaf(W3[k * H + c], hc[c], a);
             o[k] = a;
         }
         float yv[3] = {0.f, 0.f, 0.f};
@@ -125,46 +150,70 @@ __global__ void __launch_bounds__(kChunk) loss_grad_kernel(MlpView net, int64_t 
         } else {
             dO[0] = dO[1] = dO[2] = dO[3] = 0.f;
         }
-        float d2[H];
+        // backward: delta of the last hidden layer, then down through the layers
+        float d[H];
 #pragma unroll
         for (int k = 0; k < H; ++k) {
             float g = 0.f;
 #pragma unroll
             for (int q = 0; q < 4; ++q) g = fmaf(W3[q * H + k], dO[q], g);
-            d2[k] = g * (1.f - h2[k] * h2[k]);
+            d[k] = g * (1.f - hc[k] * hc[k]);
+            Ds[((depth - 1) * kChunk + t) * kHP + k] = d[k];
         }
+        for (int l = depth - 1; l >= 1; --l) {
+            const float *Wl = Wh + (l - 1) * H * H;
+            const float *hl = Hs + ((l - 1) * kChunk + t) * kHP;
 #pragma unroll
-        for (int c = 0; c < H; ++c) {
-            float g = 0.f;
+            for (int c = 0; c < H; ++c) {
+                float g = 0.f;
 #pragma unroll
-            for (int k = 0; k < H; ++k) g = fmaf(W2[k * H + c], d2[k], g);
-            D1[t * H + c] = g * (1.f - h1[c] * h1[c]);
-            H1[t * H + c] = h1[c];
-            H2[t * H + c] = h2[c];
-            D2[t * H + c] = d2[c];
+                for (int k = 0; k < H; ++k) g = fmaf(Wl[k * H + c], d[k], g);
+                hp[c] = g * (1.f - hl[c] * hl[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < H; ++c) {
+                d[c] = hp[c];
+                Ds[((l - 1) * kChunk + t) * kHP + c] = d[c];
+            }
         }
         for (int q = 0; q < 4; ++q) DO[t * 4 + q] = dO[q];
         __syncthreads();
-        // parameter gradients summed over the chunk
+        // parameter gradients summed over the chunk: layer l's weights pair its deltas
+        // with the previous layer's activations (the inputs for l = 0)
         for (int e = t; e < P; e += kChunk) {
             float g = 0.f;
             int r = e;
             if (r < H * nin) {
                 const int k = r / nin, c = r % nin;
-                for (int m = 0; m < kChunk; ++m) g = fmaf(D1[m * H + k], Xs[m * nin + c], g);
+                for (int m = 0; m < kChunk; ++m) g = fmaf(Ds[m * kHP + k], Xs[m * nin1 + c], g);
             } else if ((r -= H * nin) < H) {
-                for (int m = 0; m < kChunk; ++m) g += D1[m * H + r];
-            } else if ((r -= H) < H * H) {
-                const int k = r / H, c = r % H;
-                for (int m = 0; m < kChunk; ++m) g = fmaf(D2[m * H + k], H1[m * H + c], g);
-            } else if ((r -= H * H) < H) {
-                for (int m = 0; m < kChunk; ++m) g += D2[m * H + r];
-            } else if ((r -= H) < 4 * H) {
-                const int q = r / H, c = r % H;
-                for (int m = 0; m < kChunk; ++m) g = fmaf(DO[m * 4 + q], H2[m * H + c], g);
+                for (int m = 0; m < kChunk; ++m) g += Ds[m * kHP + r];
             } else {
-                r -= 4 * H;
-                for (int m = 0; m < kChunk; ++m) g += DO[m * 4 + r];
+                r -= H;
+                bool done = false;
+                for (int l = 1; l < depth && !done; ++l) {
+                    const float *Dl = Ds + l * kChunk * kHP, *Hp = Hs + (l - 1) * kChunk * kHP;
+                    if (r < H * H) {
+                        const int k = r / H, c = r % H;
+                        for (int m = 0; m < kChunk; ++m) g = fmaf(Dl[m * kHP + k], Hp[m * kHP + c], g);
+                        done = true;
+                    } else if ((r -= H * H) < H) {
+                        for (int m = 0; m < kChunk; ++m) g += Dl[m * kHP + r];
+                        done = true;
+                    } else {
+                        r -= H;
+                    }
+                }
+                if (!done) {
+                    const float *Hl = Hs + (depth - 1) * kChunk * kHP;
+                    if (r < 4 * H) {
+                        const int q = r / H, c = r % H;
+                        for (int m = 0; m < kChunk; ++m) g = fmaf(DO[m * 4 + q], Hl[m * kHP + c], g);
+                    } else {
+                        r -= 4 * H;
+                        for (int m = 0; m < kChunk; ++m) g += DO[m * 4 + r];
+                    }
+                }
             }
             acc[e] += g;
         }
@@ -181,32 +230,38 @@ __global__ void __launch_bounds__(kChunk) loss_grad_kernel(MlpView net, int64_t 
     }
 }
 
-// Position of parameter e of the packed vector [W1][b1][W2][b2][W3][b3] in the packed
-// BF16 weight buffer [W1][W2][W3]; -1 for biases.  *fan receives fan_in + fan_out of the
-// weight's layer.
-__device__ __forceinline__ int64_t weight_slot(int64_t e, int nin, int *fan)
+// Position of parameter e of the packed vector in the packed BF16 weight buffer; -1 for
+// biases.  *fan receives fan_in + fan_out of the weight's layer.
+__device__ __forceinline__ int64_t weight_slot(int64_t e, int nin, int depth, int *fan)
 {
-    const int64_t ob1 = (int64_t)H * nin, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H,
-                  ob3 = oW3 + 4 * H;
-    if (e < ob1) {
-        *fan = nin + H;
-        return e;
-    }
-    if (e >= oW2 && e < ob2) {
-        *fan = H + H;
-        return (int64_t)H * nin + (e - oW2);
-    }
-    if (e >= oW3 && e < ob3) {
-        *fan = H + 4;
-        return (int64_t)H * nin + H * H + (e - oW3);
-    }
+    int64_t o = 0, w = 0;   // start of the layer in the parameters / in the BF16 buffer
     *fan = 0;
-    return -1;
+    if (e < o + (int64_t)H * nin) {
+        *fan = nin + H;
+        return w + (e - o);
+    }
+    o += (int64_t)H * nin + H;
+    w += (int64_t)H * nin;
+    if (e < o) return -1;   // b1
+    for (int l = 1; l < depth; ++l) {
+        if (e < o + H * H) {
+            *fan = 2 * H;
+            return w + (e - o);
+        }
+        o += H * H + H;
+        w += H * H;
+        if (e < o) return -1;
+    }
+    if (e < o + 4 * H) {
+        *fan = H + 4;
+        return w + (e - o);
+    }
+    return -1;              // b3
 }
 
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float scale,
                             float *__restrict__ m, float *__restrict__ v, int64_t P, int nin,
-                            float lr, float b1, float b2, float eps, float c1, float c2,
+                            int depth, float lr, float b1, float b2, float eps, float c1, float c2,
                             __nv_bfloat16 *__restrict__ wb)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -218,21 +273,20 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
     v[e] = vv;
     const float np = p[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
     p[e] = np;
-    // packed BF16 weights [W1][W2][W3]; biases are skipped
     int fan = 0;
-    const int64_t w = weight_slot(e, nin, &fan);
+    const int64_t w = weight_slot(e, nin, depth, &fan);
     if (w >= 0) wb[w] = __float2bfloat16_rn(np);
 }
 
 // Glorot-uniform weights (U(-a, a), a = sqrt(6 / (fan_in + fan_out))) from one Philox draw
 // per parameter (counter = its index, key = the seed), zero biases; the BF16 copy beside.
-__global__ void init_kernel(float *__restrict__ p, int64_t P, int nin, uint32_t k0, uint32_t k1,
-                            __nv_bfloat16 *__restrict__ wb)
+__global__ void init_kernel(float *__restrict__ p, int64_t P, int nin, int depth, uint32_t k0,
+                            uint32_t k1, __nv_bfloat16 *__restrict__ wb)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= P) return;
     int fan = 0;
-    const int64_t w = weight_slot(e, nin, &fan);
+    const int64_t w = weight_slot(e, nin, depth, &fan);
     float v = 0.f;
     if (w >= 0) {
         const U4 r = philox4x32_10(U4{(uint32_t)e, (uint32_t)(e >> 32), 0x6D6C7069u, 0u}, k0, k1);
@@ -243,13 +297,13 @@ __global__ void init_kernel(float *__restrict__ p, int64_t P, int nin, uint32_t 
     if (w >= 0 && wb) wb[w] = __float2bfloat16_rn(v);
 }
 
-__global__ void bf16_kernel(const float *__restrict__ p, int64_t P, int nin,
+__global__ void bf16_kernel(const float *__restrict__ p, int64_t P, int nin, int depth,
                             __nv_bfloat16 *__restrict__ wb)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= P) return;
     int fan = 0;
-    const int64_t w = weight_slot(e, nin, &fan);
+    const int64_t w = weight_slot(e, nin, depth, &fan);
     if (w >= 0) wb[w] = __float2bfloat16_rn(p[e]);
 }
 
@@ -260,8 +314,14 @@ using namespace asd;
 
 extern "C" {
 
-int64_t asd_mlp_param_count(int n_in) { return n_params(n_in); }
-int64_t asd_mlp_param_count_bf16(int n_in) { return n_weights(n_in); }
+int64_t asd_mlp_param_count(int n_in, int depth)
+{
+    return shape_ok(n_in, depth) ? n_params(n_in, depth) : 0;
+}
+int64_t asd_mlp_param_count_bf16(int n_in, int depth)
+{
+    return shape_ok(n_in, depth) ? n_weights(n_in, depth) : 0;
+}
 
 int asd_mlp_gather(const asd_system *sys, int n_samples, const float *spins, float *x, float *y,
                    void *stream)
@@ -281,60 +341,66 @@ int asd_mlp_loss_grad(const asd_mlp *net, int64_t n, const float *x, const float
                       double *loss, void *stream)
 {
     ASD_CHECK_ARG(net && x && y && grad && loss, "null argument");
-    ASD_CHECK_ARG(net->n_hidden == kMlpHidden && net->n_in >= 3 && net->n_in <= kMlpMaxIn,
-                  "network shape must be [n_in <= 24 -> 64 -> 64 -> 4]");
+    const int depth = mlp_depth(*net);
+    ASD_CHECK_ARG(net->n_hidden == kMlpHidden && shape_ok(net->n_in, depth),
+                  "network shape must be [n_in <= 24 -> 64 (x2 or x3) -> 4]");
     ASD_CHECK_ARG(net->W1 && net->W2 && net->W3 && net->b1 && net->b2 && net->b3, "null weights");
+    ASD_CHECK_ARG(depth == 2 || (net->Wm && net->bm), "null weights of the third layer");
     ASD_CHECK_ARG(n >= 0, "bad n");
     if (n == 0) return ASD_OK;
     const int nin = net->n_in;
-    const size_t smem = sizeof(float) * ((size_t)H * nin + H * H + 4 * H + kChunk * nin +
-                                         4 * kChunk * H + kChunk * 4 + n_params(nin));
+    const size_t smem =
+        sizeof(float) * ((size_t)H * nin + (size_t)(depth - 1) * H * H + 4 * H +
+                         kChunk * (nin + 1) + 2 * (size_t)depth * kChunk * kHP + kChunk * 4 +
+                         n_params(nin, depth));
     auto k = loss_grad_kernel;
     ASD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0;
     ASD_CUDA_TRY(cudaGetDevice(&dev));
     ASD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int64_t chunks = (n + kChunk - 1) / kChunk;
-    int64_t blocks = chunks < (int64_t)sms * 2 ? chunks : (int64_t)sms * 2;
+    int64_t blocks = chunks < (int64_t)sms ? chunks : (int64_t)sms;
     k<<<(unsigned)blocks, kChunk, smem, (cudaStream_t)stream>>>(mlp_view(*net), n, x, y, grad, loss);
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;
 }
 
 int asd_mlp_adam_step(float *params, const float *grad, float grad_scale, float *m, float *v,
-                      int n_in, float lr, float beta1, float beta2, float eps, int step,
-                      uint16_t *w_bf16, void *stream)
+                      int n_in, int depth, float lr, float beta1, float beta2, float eps,
+                      int step, uint16_t *w_bf16, void *stream)
 {
     ASD_CHECK_ARG(params && grad && m && v && w_bf16, "null argument");
-    ASD_CHECK_ARG(n_in >= 3 && n_in <= kMlpMaxIn && step >= 1, "bad n_in or step");
-    const int64_t P = n_params(n_in);
+    ASD_CHECK_ARG(shape_ok(n_in, depth) && step >= 1, "bad n_in, depth or step");
+    const int64_t P = n_params(n_in, depth);
     const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
     adam_kernel<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        params, grad, grad_scale, m, v, P, n_in, lr, beta1, beta2, eps, c1, c2,
+        params, grad, grad_scale, m, v, P, n_in, depth, lr, beta1, beta2, eps, c1, c2,
         reinterpret_cast<__nv_bfloat16 *>(w_bf16));
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;
 }
 
-int asd_mlp_init(float *params, int n_in, uint64_t seed, uint16_t *w_bf16, void *stream)
+int asd_mlp_init(float *params, int n_in, int depth, uint64_t seed, uint16_t *w_bf16,
+                 void *stream)
 {
     ASD_CHECK_ARG(params, "null argument");
-    ASD_CHECK_ARG(n_in >= 3 && n_in <= kMlpMaxIn, "bad n_in (3..24)");
-    const int64_t P = n_params(n_in);
+    ASD_CHECK_ARG(shape_ok(n_in, depth), "bad n_in (3..24) or depth (2, 3)");
+    const int64_t P = n_params(n_in, depth);
     init_kernel<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        params, P, n_in, (uint32_t)seed, (uint32_t)(seed >> 32),
+        params, P, n_in, depth, (uint32_t)seed, (uint32_t)(seed >> 32),
         reinterpret_cast<__nv_bfloat16 *>(w_bf16));
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;
 }
 
-int asd_mlp_weights_bf16(const float *params, int n_in, uint16_t *w_bf16, void *stream)
+int asd_mlp_weights_bf16(const float *params, int n_in, int depth, uint16_t *w_bf16,
+                         void *stream)
 {
     ASD_CHECK_ARG(params && w_bf16, "null argument");
-    ASD_CHECK_ARG(n_in >= 3 && n_in <= kMlpMaxIn, "bad n_in (3..24)");
-    const int64_t P = n_params(n_in);
+    ASD_CHECK_ARG(shape_ok(n_in, depth), "bad n_in (3..24) or depth (2, 3)");
+    const int64_t P = n_params(n_in, depth);
     bf16_kernel<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        params, P, n_in, reinterpret_cast<__nv_bfloat16 *>(w_bf16));
+        params, P, n_in, depth, reinterpret_cast<__nv_bfloat16 *>(w_bf16));
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;
 }

@@ -20,49 +20,63 @@ def asd():
     return m
 
 
-def _bf16_point(p, nin):
+def _weight_ranges(nin, depth):
+    """[start, end) of every weight matrix in the packed parameter vector."""
+    out, o = [], 0
+    for name, shape in omlp._shapes(nin, depth):
+        n = int(np.prod(shape))
+        if not name.startswith("b"):
+            out.append((o, o + n))
+        o += n
+    return out
+
+
+def _bf16_point(p, nin, depth=2):
     """The oracle evaluates at the weights the GPU uses: BF16-rounded W, FP32 biases."""
     t = torch.from_numpy(p.astype(np.float32))
     q = t.clone()
-    H = 64
-    for a, b in ((0, H * nin), (H * nin + H, H * nin + H + H * H),
-                 (H * nin + 2 * H + H * H, H * nin + 2 * H + H * H + 4 * H)):
+    for a, b in _weight_ranges(nin, depth):
         q[a:b] = t[a:b].to(torch.bfloat16).float()
     return q.double().numpy()
 
 
-def test_loss_and_gradient_match_oracle(asd):
+@pytest.mark.parametrize("depth", [2, 3])
+def test_loss_and_gradient_match_oracle(asd, depth):
     nin = 12
-    p = omlp.init(nin, 7) * 1.5
-    net = asd.Mlp(nin, p)
+    p = omlp.init(nin, 7, depth) * 1.5
+    net = asd.Mlp(nin, p, depth=depth)
     x = synth.random_unit(4 * 3000, 1).reshape(3000, 12)
     y = synth.random_unit(3000, 2)
     dx, dy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
     net.loss_grad(dx, dy)
     assert asd.sync_status() == 0
-    pb = _bf16_point(p, nin)
-    ref_l = omlp.nll(pb, x, y, nin)
-    ref_g = omlp.grad(pb, x, y, nin)
+    pb = _bf16_point(p, nin, depth)
+    ref_l = omlp.nll(pb, x, y, nin, depth)
+    ref_g = omlp.grad(pb, x, y, nin, depth)
     assert abs(net.loss.item() - ref_l) <= 1e-5 * abs(ref_l)
     g = net.grad.cpu().double().numpy()
     assert np.linalg.norm(g - ref_g) <= 1e-4 * np.linalg.norm(ref_g)
     assert np.abs(g - ref_g).max() <= 1e-3 * np.abs(ref_g).max()
 
 
-def test_library_initialiser(asd):
+@pytest.mark.parametrize("depth", [2, 3])
+def test_library_initialiser(asd, depth):
     """asd_mlp_init: Glorot-uniform weights inside +-sqrt(6 / (fan_in + fan_out)) with the
     moments of that uniform law, zero biases, the BF16 copy equal to the round-to-nearest
     of the parameters, the same draw for the same seed and a different one otherwise."""
     nin, H = 12, 64
-    a = asd.Mlp(nin, seed=7)
-    b = asd.Mlp(nin, seed=7)
-    c = asd.Mlp(nin, seed=8)
+    a = asd.Mlp(nin, seed=7, depth=depth)
+    b = asd.Mlp(nin, seed=7, depth=depth)
+    c = asd.Mlp(nin, seed=8, depth=depth)
     assert asd.sync_status() == 0
     p = a.params.cpu().double().numpy()
+    assert p.shape == (omlp.n_params(nin, depth),)
     assert np.array_equal(p, b.params.cpu().double().numpy())
     assert not np.array_equal(p, c.params.cpu().double().numpy())
-    w = omlp.unpack(p, nin)
-    for name, fan in (("W1", nin + H), ("W2", 2 * H), ("W3", H + 4)):
+    w = omlp.unpack(p, nin, depth)
+    layers = (("W1", nin + H), ("W2", 2 * H)) + ((("Wm", 2 * H),) if depth == 3 else ()) + \
+        (("W3", H + 4),)
+    for name, fan in layers:
         lim = math.sqrt(6.0 / fan)
         x = w[name].ravel()
         assert np.abs(x).max() <= lim and np.abs(x).max() > 0.9 * lim, name
@@ -70,12 +84,10 @@ def test_library_initialiser(asd):
         n = x.size
         assert abs(x.mean()) <= 5 * lim / math.sqrt(3 * n), name
         assert abs(x.var() / (lim * lim / 3) - 1) <= 5 * math.sqrt(0.8 / n), name
-    for name in ("b1", "b2", "b3"):
+    for name in ("b1", "b2", "b3") + (("bm",) if depth == 3 else ()):
         assert not w[name].any(), name
-    assert np.array_equal(a.wb.float().cpu().double().numpy(),
-                          _bf16_point(p, nin)[np.r_[0:H * nin, H * nin + H:H * nin + H + H * H,
-                                                    H * nin + 2 * H + H * H:
-                                                    H * nin + 2 * H + H * H + 4 * H]])
+    idx = np.concatenate([np.arange(a0, b0) for a0, b0 in _weight_ranges(nin, depth)])
+    assert np.array_equal(a.wb.float().cpu().double().numpy(), _bf16_point(p, nin, depth)[idx])
 
 
 def _heatbath_nll(x, y, beta, J=1.0):
@@ -95,7 +107,7 @@ def _energy_per_site(y, lat):
     return e / 2 / (y.shape[0] * lat.n_sites)
 
 
-def _train(asd, sysm, lat, T, S, seed, sweeps0=300, snaps=40, steps=600, B=8192):
+def _train(asd, sysm, lat, T, S, seed, sweeps0=300, snaps=40, steps=600, B=8192, depth=2):
     """Train a fresh network (library initialiser) on plain Metropolis configurations."""
     n_in = 3 * lat.nbr.shape[1]
     sp = torch.from_numpy(synth.random_unit(S * lat.n_sites, seed).reshape(S, lat.n_sites, 3)).cuda()
@@ -111,7 +123,7 @@ def _train(asd, sysm, lat, T, S, seed, sweeps0=300, snaps=40, steps=600, B=8192)
         ys.append(y)
     X, Y = torch.cat(xs), torch.cat(ys)
     n = X.shape[0]
-    net = asd.Mlp(n_in, seed=seed + 10)
+    net = asd.Mlp(n_in, seed=seed + 10, depth=depth)
     g = torch.Generator(device="cuda").manual_seed(0)
     for it in range(steps):
         idx = torch.randint(0, n, (B,), device="cuda", generator=g)
@@ -189,16 +201,18 @@ def test_learned_proposal_decorrelates_faster(asd, square16):
     assert tau_l < 0.6 * tau_m, res
 
 
-def test_learned_chain_is_exact_open_chain(asd):
+@pytest.mark.parametrize("depth", [2, 3])
+def test_learned_chain_is_exact_open_chain(asd, depth):
     """Exactness of the Metropolis-Hastings correction: on an open chain the bond angles
     are independent and <S_i . S_i+1> = -L(beta J) (Langevin function) exactly.  A network
-    trained on the chain (2 neighbours, 6 inputs) drives the learned proposal; the bond
-    average over 4095 bonds x 16 chains x 60 snapshots must agree with the closed form
-    within 5 standard errors of 12 block means (about 8e-4)."""
+    (two or three hidden layers) trained on the chain (2 neighbours, 6 inputs) drives the
+    learned proposal; the bond average over 4095 bonds x 16 chains x 60 snapshots must
+    agree with the closed form within 5 standard errors of 12 block means (about 8e-4)."""
     n, S, T = 4096, 16, 0.5
     lat = synth.open_chain(n, J=1.0)
     sysm = asd.System(lat)
-    net, sp, _, _ = _train(asd, sysm, lat, T, S, seed=21, sweeps0=200, snaps=16, steps=300)
+    net, sp, _, _ = _train(asd, sysm, lat, T, S, seed=21, sweeps0=200, snaps=16, steps=300,
+                           depth=depth)
     s2 = sp.clone()
     sysm.thermalize(s2, T, 50, asd.ASD_LEARNED, net=net, seed=5)
     snaps, ac, pr = [], 0, 0

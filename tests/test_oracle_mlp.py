@@ -2,6 +2,7 @@
 normaliser integrated numerically, and the back-propagated gradient against central
 finite differences (independent of the backward formulas)."""
 import numpy as np
+import pytest
 
 from oracle import mlp
 from paper_2308_07487_gb300 import synth
@@ -25,17 +26,37 @@ def test_vmf_density_integrates_to_one():
     assert abs(mlp.nll(p, x, y, nin) - ref) < 1e-9 * abs(ref)
 
 
-def test_gradient_matches_finite_differences():
+@pytest.mark.parametrize("depth", [2, 3])
+def test_gradient_matches_finite_differences(depth):
     nin = 12
-    p = mlp.init(nin, 5) * 2.0
+    p = mlp.init(nin, 5, depth) * 2.0
+    assert len(p) == mlp.n_params(nin, depth)
     x = synth.random_unit(4 * 16, 2).reshape(16, 12)
     y = synth.random_unit(16, 3)
-    g = mlp.grad(p, x, y, nin)
+    g = mlp.grad(p, x, y, nin, depth)
     rng = np.random.default_rng(0)
-    idx = rng.choice(len(p), 60, replace=False)
+    # every layer's weights and biases are sampled (the blocks of the packed vector)
+    idx = rng.choice(len(p), 80, replace=False)
     eps = 1e-6
     for i in idx:
         e = np.zeros_like(p)
         e[i] = eps
-        fd = (mlp.nll(p + e, x, y, nin) - mlp.nll(p - e, x, y, nin)) / (2 * eps)
+        fd = (mlp.nll(p + e, x, y, nin, depth) - mlp.nll(p - e, x, y, nin, depth)) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_three_layers_reduce_to_two_with_an_identity_like_layer():
+    """A third hidden layer that passes its input through (Wm = a * identity, bm = 0 with a
+    small a and the output weights scaled by 1/a) reproduces the two-layer network to
+    first order in a: a check of the packed layout and of the extra layer's place."""
+    nin, a = 12, 1e-4
+    p2 = mlp.init(nin, 7)
+    w2 = mlp.unpack(p2, nin)
+    parts = [w2["W1"].ravel(), w2["b1"], w2["W2"].ravel(), w2["b2"],
+             (a * np.eye(mlp.H)).ravel(), np.zeros(mlp.H), (w2["W3"] / a).ravel(), w2["b3"]]
+    p3 = np.concatenate(parts)
+    x = synth.random_unit(4 * 8, 4).reshape(8, 12)
+    mu2, k2, _ = mlp.forward(p2, x, nin)
+    mu3, k3, _ = mlp.forward(p3, x, nin, 3)
+    np.testing.assert_allclose(mu3, mu2, atol=1e-6)
+    np.testing.assert_allclose(k3, k2, rtol=1e-6)
