@@ -94,7 +94,7 @@ typedef struct asd_corr_desc {
                                256 (tensor forms)                                        */
     int32_t raster_m;       /* 0 = automatic, else row tiles per raster group (1..64)  */
     int32_t stages;         /* 0 = automatic, else shared-memory pipeline stages (2..8) */
-    int32_t k_chunks;       /* 0 = automatic (split-BF16: one per ~1536 K elements;
+    int32_t k_chunks;       /* 0 = automatic (split-BF16: one per <= 1024 K elements;
                                other forms: 1), else partial accumulators per tile along K
                                (1..256): each starts from zero, which bounds the
                                tensor-core FP32 accumulation error; the epilogue bins each

@@ -358,8 +358,14 @@ int asd_mlp_loss_grad(const asd_mlp *net, int64_t n, const float *x, const float
     int dev = 0, sms = 0;
     ASD_CUDA_TRY(cudaGetDevice(&dev));
     ASD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // as many resident blocks per SM as shared memory allows (the kernel is latency-bound:
+    // two blocks of a two-layer network fit, one of a three-layer network)
+    int smem_sm = 0;
+    ASD_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    int per_sm = smem_sm / (int)(smem + 1024);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
     int64_t chunks = (n + kChunk - 1) / kChunk;
-    int64_t blocks = chunks < (int64_t)sms ? chunks : (int64_t)sms;
+    int64_t blocks = chunks < (int64_t)sms * per_sm ? chunks : (int64_t)sms * per_sm;
     k<<<(unsigned)blocks, kChunk, smem, (cudaStream_t)stream>>>(mlp_view(*net), n, x, y, grad, loss);
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;

@@ -154,13 +154,13 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
                 part = fmaf(wr.x, u, fmaf(wr.y, v, part));        // cos(a - b)
                 part_s = fmaf(wr.y, u, fmaf(-wr.x, v, part_s));   // sin(a - b)
             }
-            double dp = part;
-            for (int o = 16; o > 0; o >>= 1) dp += __shfl_xor_sync(0xffffffffu, dp, o);
-            if (lane == 0) atomicAdd(&sq[q * e.q_parts], dp);
+            // the warp's 32 partial sums (64 pairs each) in FP32, one FP64 add per warp
+            // (FP64 arithmetic runs on a narrow pipe on this part)
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) atomicAdd(&sq[q * e.q_parts], (double)part);
             if (e.q_parts == 2) {
-                double ds = part_s;
-                for (int o = 16; o > 0; o >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, o);
-                if (lane == 0) atomicAdd(&sq[2 * q + 1], ds);
+                for (int o = 16; o > 0; o >>= 1) part_s += __shfl_xor_sync(0xffffffffu, part_s, o);
+                if (lane == 0) atomicAdd(&sq[2 * q + 1], (double)part_s);
             }
         }
     }

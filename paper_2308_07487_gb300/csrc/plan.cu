@@ -400,16 +400,16 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         if (p->EW != 4 && p->BN == 128) p->BN = d->n_q > 0 ? 192 : 256;
         // K chunks: split-BF16 is the FP32-accurate form; each chunk's accumulator starts
         // from zero, bounding the FP32 accumulation error of the tensor core (it adds each
-        // MMA's products into the FP32 accumulator with truncation) to ~768 terms per
-        // partial sum at any K (measured on the 64^3 glass, K = 1536, 12 random blocks of
-        // 16 rows: one chunk 1.1e-5 worst per bin, in a bin of 4 pairs; two 7.9e-6; on the
-        // 40^3 lattice, K = 3000: one chunk 1.4e-5, two 7.9e-6).  The other forms are
-        // limited by their operand rounding.  Each chunk's epilogue runs while the next
-        // chunk's MMAs do.
+        // MMA's products into the FP32 accumulator with truncation) to at most 1024 terms
+        // per partial sum at any K (measured on the 64^3 glass, K = 1536, 12 random blocks
+        // of 16 rows, thermalised LL trajectory: one chunk 4.6e-5 worst per bin, two chunks
+        // of 768 7.5e-6; on the 40^3 lattice, K = 3000: one chunk 1.4e-5, two 7.9e-6, three
+        // 6.2e-6).  The other forms are limited by their operand rounding.  Each chunk's
+        // epilogue runs while the next chunk's MMAs do.
         const int64_t nk = (int64_t)p->S * (p->Kseg / p->BK);
         int kc = d->k_chunks;
         if (kc == 0)
-            kc = d->precision == ASD_SPLIT_BF16 ? (int)((p->S * p->Kseg + 767) / 768) : 1;
+            kc = d->precision == ASD_SPLIT_BF16 ? (int)((p->S * p->Kseg + 1023) / 1024) : 1;
         if (kc > 256) kc = 256;
         if (kc > nk) kc = (int)nk;
         p->k_chunks = kc < 1 ? 1 : kc;
