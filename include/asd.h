@@ -16,7 +16,8 @@
  *  - Return value: ASD_OK (0) or a negative ASD_E* code.  Arguments are validated on
  *    the host before anything is launched; on ASD_EINVAL nothing was enqueued.
  *    ASD_ECUDA keeps the CUDA error text for asd_strerror().  A bounded device-side
- *    wait that gave up is reported as ASD_ETIMEOUT by asd_sync_status().
+ *    wait that gave up is reported as ASD_ETIMEOUT by asd_sync_status(), a failed
+ *    index check of a checked build (ASD_CHECK_BOUNDS) as ASD_EBOUNDS.
  *  - Units: the device is the current CUDA device of the calling thread.
  */
 #ifndef ASD_H
@@ -29,7 +30,7 @@
 extern "C" {
 #endif
 
-#define ASD_ABI_VERSION 2
+#define ASD_ABI_VERSION 3
 
 enum asd_status {
     ASD_OK = 0,
@@ -37,7 +38,9 @@ enum asd_status {
     ASD_ENOMEM = -2,       /* device or host allocation failed                   */
     ASD_ECUDA = -3,        /* a CUDA runtime/driver call failed                  */
     ASD_ETIMEOUT = -4,     /* a bounded device wait gave up (device error word)  */
-    ASD_EUNSUPPORTED = -5  /* valid request this build or device cannot serve    */
+    ASD_EUNSUPPORTED = -5, /* valid request this build or device cannot serve    */
+    ASD_EBOUNDS = -6       /* a kernel index check of a checked build failed (the
+                              access was skipped; device error word)               */
 };
 
 /* Precision forms of the contraction (the epilogue and bins are FP32 per tile,
@@ -90,8 +93,9 @@ typedef struct asd_corr_desc {
     int32_t n_bins;         /* 0 .. 4096                                               */
     int32_t n_q;            /* 0 .. 256                                                */
     const double *q;        /* host [n_q][3]                                           */
-    int32_t tile_n;         /* 0 = automatic (128 for N <= 4096, else 256), else 128 or
-                               256 (tensor forms)                                        */
+    int32_t tile_n;         /* 0 = automatic (128 for N <= 4096, else 192 with phase
+                               weights and 256 without), else 128, 192 or 256 (tensor
+                               forms; phase weights need <= 192)                        */
     int32_t raster_m;       /* 0 = automatic, else row tiles per raster group (1..64)  */
     int32_t stages;         /* 0 = automatic, else shared-memory pipeline stages (2..8) */
     int32_t k_chunks;       /* 0 = automatic (split-BF16: one per <= 1024 K elements;
@@ -99,15 +103,28 @@ typedef struct asd_corr_desc {
                                (1..256): each starts from zero, which bounds the
                                tensor-core FP32 accumulation error; the epilogue bins each
                                one (FP32 within a tile, FP64 across tiles)               */
-    int32_t epi_warps;      /* 0 = automatic (4), 4 or 8 epilogue warps per CTA (8 needs
-                               tile_n 256; its phase loop takes 4 q per pass instead
-                               of 8)                                                     */
+    int32_t epi_warps;      /* 0 = automatic (8 for positions with 192- or 256-wide
+                               tiles, else 4), 4 or 8 epilogue warps per CTA (8 needs
+                               tile_n 192 or 256)                                         */
     int32_t phase_sine;     /* 0: Sq_sum[t][q] holds the cosine part of Eq. 3's phase sum;
                                1: Sq_sum[t][q][2] holds (cosine, sine) parts, the sine
                                part sum_ij sin(q.(r_i - r_j)) G_ij(t) (Eq. 3's imaginary
                                part is its negative)                                     */
     int32_t static_schedule;/* 0: work items claimed from a global counter (dynamic,
                                the default); 1: static round-robin order                 */
+    int32_t deterministic;  /* 0: sums across threads and tiles by FP32 / FP64 atomics
+                               (the last bits depend on the schedule); 1: every such sum
+                               in 64-bit fixed point (integer adds, any order gives the
+                               same bits), so C_sum / Sq_sum are bitwise reproducible for
+                               any schedule, raster, stage count and batch order at a
+                               given precision, tile width and epilogue-warp count.  The
+                               fixed-point unit is 2^-e, 2^e the largest power of two
+                               with 2 x rows x N x S*3*T0 x max|x|^2 x 2^e < 2^61 (rows of
+                               the launch, max|x| over the prepared trajectory, twice that
+                               with centring): no sum can overflow, and each rounded term
+                               (one per tile, K-chunk and bin or q; one per pair for bins
+                               outside a tile's private window) adds at most half a unit.
+                               Tensor-core and FP32 forms; not the separable route.      */
 } asd_corr_desc;
 
 typedef struct asd_corr_plan asd_corr_plan;
@@ -229,8 +246,28 @@ int asd_pair_corr_normalize(const asd_corr_plan *plan, const double *C_sum, cons
                             double *C, double *Sq, void *stream);
 
 /* Synchronise `stream` and report (then clear) the device error word:
- * ASD_OK, ASD_ETIMEOUT or ASD_ECUDA. */
+ * ASD_OK, ASD_ETIMEOUT, ASD_EBOUNDS or ASD_ECUDA. */
 int asd_sync_status(void *stream);
+
+/* Build flags of the loaded library: bit 0 (ASD_BUILD_CHECK_BOUNDS) is set in a checked
+ * build.  A checked build (compiled with ASD_CHECK_BOUNDS=1) tests, in its kernels, every
+ * computed index into shared memory and tables -- private-bin offsets and rows, fallback
+ * bins, the lattice d2 table, bin thresholds, decoded work items, column and q indices --
+ * before the access; the first failure is recorded in the device error word (reported by
+ * asd_sync_status as ASD_EBOUNDS, with its site in the error text) and the access is
+ * skipped.  It stands in for a memory checker and is slower; results are otherwise the
+ * same. */
+#define ASD_BUILD_CHECK_BOUNDS 1
+int asd_build_flags(void);
+
+/*
+ * Self-test of the index-check path of a checked build (the paper has no counterpart).
+ * Enqueues one thread that tests an index equal to the length of a 16-entry shared array
+ * it owns, the check fails, the store is skipped and the failure is recorded, so the next
+ * asd_sync_status reports ASD_EBOUNDS.  In an unchecked build the call returns
+ * ASD_EUNSUPPORTED and enqueues nothing.
+ */
+int asd_selftest_bounds(void *stream);
 
 /*
  * Self-test of the failure path (the paper has no counterpart).  Enqueues on `stream` one

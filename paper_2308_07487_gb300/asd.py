@@ -2,7 +2,9 @@
 
 Every computation runs in libasd.so.  Importing this module loads the library and
 raises ImportError if it has not been built (``python -m paper_2308_07487_gb300.build``
-or ``__graft_entry__.build()``): there is no fallback path.
+or ``__graft_entry__.build()``): there is no fallback path.  With ASD_CHECKED=1 in the
+environment it loads the index-checked build libasd_checked.so instead
+(``build.build(check_bounds=True)``).
 Device pointers are passed as integers (e.g. ``tensor.data_ptr()``); streams as
 ``torch.cuda.current_stream().cuda_stream``.
 """
@@ -13,12 +15,17 @@ import os
 
 import numpy as np
 
-_SO = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libasd.so")
+_CHECKED = os.environ.get("ASD_CHECKED", "0") == "1"
+_SO = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib",
+                   "libasd_checked.so" if _CHECKED else "libasd.so")
 if not os.path.exists(_SO):
-    raise ImportError(f"libasd.so not built ({_SO}); run paper_2308_07487_gb300/build.py")
+    raise ImportError(f"{os.path.basename(_SO)} not built ({_SO}); run "
+                      "paper_2308_07487_gb300/build.py" + (" --checked" if _CHECKED else ""))
 lib = ctypes.CDLL(_SO)
 
 ASD_OK, ASD_EINVAL, ASD_ENOMEM, ASD_ECUDA, ASD_ETIMEOUT, ASD_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+ASD_EBOUNDS = -6
+ASD_BUILD_CHECK_BOUNDS = 1
 ASD_FP32, ASD_TF32, ASD_BF16, ASD_SPLIT_BF16 = 0, 1, 2, 3
 PRECISIONS = {"fp32": ASD_FP32, "tf32": ASD_TF32, "bf16": ASD_BF16, "split_bf16": ASD_SPLIT_BF16}
 ASD_GEOM_LATTICE, ASD_GEOM_POSITIONS = 0, 1
@@ -40,7 +47,8 @@ class asd_corr_desc(ctypes.Structure):
                 ("n_q", ctypes.c_int32), ("q", c_f64p), ("tile_n", ctypes.c_int32),
                 ("raster_m", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("k_chunks", ctypes.c_int32), ("epi_warps", ctypes.c_int32),
-                ("phase_sine", ctypes.c_int32), ("static_schedule", ctypes.c_int32)]
+                ("phase_sine", ctypes.c_int32), ("static_schedule", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32)]
 
 
 class asd_system(ctypes.Structure):
@@ -82,6 +90,8 @@ _SIGS = {
     "asd_sq_omega": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_int, ctypes.c_double, _VP, ctypes.c_int, _VP, _VP]),
     "asd_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, _VP]),
+    "asd_selftest_bounds": (ctypes.c_int, [_VP]),
+    "asd_build_flags": (ctypes.c_int, []),
     "asd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "asd_ll_integrate": (ctypes.c_int, [ctypes.POINTER(asd_system), ctypes.c_int, _VP, ctypes.c_float,
                                         ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
@@ -149,7 +159,7 @@ class CorrPlan:
     def __init__(self, N, F, T0, n_t, precision="split_bf16", S=1, center=False, coords=None,
                  L=(1, 1, 1), periodic=False, pos=None, bin_width=1.0, n_bins=0, q=None,
                  tile_n=0, raster_m=0, stages=0, k_chunks=0, epi_warps=0,
-                 phase_sine=False, static_schedule=False):
+                 phase_sine=False, static_schedule=False, deterministic=False):
         d = asd_corr_desc()
         d.n_sites, d.n_frames, d.n_samples, d.T0, d.n_t = N, F, S, T0, n_t
         d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -182,6 +192,7 @@ class CorrPlan:
         d.epi_warps = int(epi_warps)
         d.phase_sine = int(bool(phase_sine))
         d.static_schedule = int(bool(static_schedule))
+        d.deterministic = int(bool(deterministic))
         self.q_parts = 1 + d.phase_sine  # Sq_sum is [n_t][n_q] or [n_t][n_q][2]
         self.desc = d
         self.N, self.F, self.S, self.T0, self.n_t = N, F, S, T0, n_t
@@ -286,6 +297,17 @@ def sync_status(stream=None):
 def selftest_timeout(limit_ns, stream=None):
     """asd_selftest_timeout: a bounded wait that runs out; read with sync_status."""
     check(lib.asd_selftest_timeout(int(limit_ns), _stream(stream)), "selftest_timeout")
+
+
+def build_flags():
+    """asd_build_flags: ASD_BUILD_CHECK_BOUNDS in the index-checked build."""
+    return int(lib.asd_build_flags())
+
+
+def selftest_bounds(stream=None):
+    """asd_selftest_bounds (checked build): an index check that fails; read with
+    sync_status (ASD_EBOUNDS)."""
+    check(lib.asd_selftest_bounds(_stream(stream)), "selftest_bounds")
 
 
 class Mlp:

@@ -35,15 +35,61 @@ void set_error_text(const std::string &s);
         }                                                    \
     } while (0)
 
-// Device error word (one per device, module scope): bounded waits write a code here.
+// Device error word (one per device, module scope): bounded waits write a code here,
+// and so do the index checks of a checked build (DEV_BOUNDS + site).
 enum DeviceError : int {
     DEV_OK = 0,
     DEV_TIMEOUT_TMA = 1,
     DEV_TIMEOUT_MMA = 2,
     DEV_TIMEOUT_EPI = 3,
-    DEV_TIMEOUT_SELFTEST = 4
+    DEV_TIMEOUT_SELFTEST = 4,
+    DEV_BOUNDS = 256
 };
 int *device_error_word();          // device address of the word for the current device
+
+// Sites of the index checks (ASD_CHECK_BOUNDS builds).
+enum BoundSite : int {
+    BND_SELFTEST = 0,   // asd_selftest_bounds
+    BND_WORK = 1,       // decoded work item (displacement) outside its problem
+    BND_PRIV = 2,       // private-bin offset outside the window rows (+ trash row)
+    BND_FALLBACK = 3,   // fallback bin outside the launch's bin arrays
+    BND_LUT = 4,        // lattice d2 outside the d2 -> bin table
+    BND_THR = 5,        // threshold index outside [0, n_bins]
+    BND_REGION = 6,     // a problem's bins and table larger than the launch's region
+    BND_Q = 7,          // q index outside the phase arrays or the cos / sin rows
+    BND_CACC = 8,       // per-CTA bin accumulator index
+    BND_SIMT_BIN = 9,   // FP32 form: bin index
+    BND_SIMT_Q = 10,    // FP32 form: q index
+    BND_N_SITES
+};
+
+#ifndef ASD_CHECK_BOUNDS
+#define ASD_CHECK_BOUNDS 0
+#endif
+#if ASD_CHECK_BOUNDS
+// Checked build: a failed index check records the first failure and the caller skips
+// the access (no trap: the kernel carries on and the host reads the word).
+__device__ __forceinline__ bool in_bounds(bool ok, int site, int *err)
+{
+    if (!ok) atomicCAS(err, 0, (int)DEV_BOUNDS + site);
+    return ok;
+}
+#define ASD_INB(cond, site, err) (::asd::in_bounds((cond), (site), (err)))
+#else
+#define ASD_INB(cond, site, err) (true)
+#endif
+
+// Deterministic sums (asd_corr_desc.deterministic): values become 64-bit fixed point,
+// x -> round(x 2^e), so sums over threads and tiles are integer adds whose result does
+// not depend on their order.  The scale 2^e comes from a bound on every partial sum.
+__device__ __forceinline__ long long to_fixed(double x, double scale)
+{
+    return __double2ll_rn(x * scale);
+}
+__device__ __forceinline__ void add_fixed(long long *dst, long long v)
+{
+    atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)v);
+}
 
 // ----------------------------------------------------------------------------------
 // tensor-core operand layout
@@ -86,6 +132,11 @@ struct EpiParams {
     const float2 *cs;       // [N][nq_pad] (cos, sin)(q.r_i)
     double *C_sum;          // [n_t][n_bins]
     double *Sq_sum;         // [n_t][n_q]
+    // deterministic mode: fixed-point sums [n_t][n_bins] and [n_t][n_q][q_parts] and the
+    // scale 2^e (device, set after the operands are prepared); null otherwise
+    long long *C_fix;
+    long long *Sq_fix;
+    const double *fix_scale;
 };
 
 // One problem of the (possibly batched) tensor-core launch.
@@ -94,8 +145,8 @@ struct TcProblem {
     CUtensorMap mapB[2];              // [plane]
     CUtensorMap mapW[2];              // phase column weights [plane]: rows (pass, output),
                                       // columns = sites (BF16 hi / lo)
-    int64_t tile_begin;               // first flattened tile of this problem
-    int64_t n_tiles;                  // n_t * tiles_m * tiles_n
+    int64_t tile_begin;               // first flattened work item of this problem
+    int64_t n_tiles;                  // work items: n_t * tiles_m * tiles_n
     int N;                            // columns (sites)
     int row_begin, row_end;
     int tiles_m, tiles_n;
@@ -131,6 +182,7 @@ struct TcLaunchArgs {
     uint32_t VB;           // bytes of the per-problem epilogue region (largest problem)
     unsigned long long *counter;  // dynamic schedule: work-item counter (zero at launch), or null
     int NB, NQ;            // epilogue shared-memory layout maxima
+    int det;               // 1: some problem sums in fixed point (fallback bins 8 bytes)
     int *err;
 };
 
@@ -194,6 +246,10 @@ struct asd_corr_plan {
     size_t smem_bytes;
     int EW;                    // epilogue warps (4 or 8)
     int k_chunks;
+    // deterministic mode: fixed-point sums, the operand bound and the scale (device)
+    long long *C_fix, *Sq_fix;
+    unsigned int *amax_bits;   // max |x| over the prepared trajectory rows (FP32 bits)
+    double *fix_scale;         // 2^e of the current launch
     // last asd_pair_corr_prepare
     const float *prepared_traj;
     int64_t prepared_begin, prepared_end;
@@ -211,16 +267,23 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
 int tc_configure(asd_corr_plan *p);    // stages / smem for the plan's form
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
               int BN, int swizzle_bytes, int stages, size_t smem, uint32_t var_bytes,
-              int max_nb, int max_nq, int ew, int sm_count, unsigned long long *counter,
-              cudaStream_t s);
-// work items of one problem: n_t * k_chunks * tiles_m * tiles_n
-inline int64_t tc_work_items(int n_t, int k_chunks, int tiles_m, int tiles_n)
+              int max_nb, int max_nq, int ew, int det, int sm_count,
+              unsigned long long *counter, cudaStream_t s);
+// work items of one problem: one per (displacement, row tile, column tile); the K chunks
+// of an item run as consecutive sub-items on one CTA
+inline int64_t tc_work_items(int n_t, int tiles_m, int tiles_n)
 {
-    return (int64_t)n_t * k_chunks * tiles_m * tiles_n;
+    return (int64_t)n_t * tiles_m * tiles_n;
 }
-size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut, int ew);
+size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut, int ew, int det);
 // bytes of the per-problem epilogue region (private bins + bin table)
 uint32_t tc_var_bytes(int NW, int n_bins, int n_lut, int ew);
 // epilogue bytes with the per-problem region given separately
-size_t tc_epilogue_smem_vb(uint32_t var_bytes, int n_bins, int n_q, int BN, int ew);
+size_t tc_epilogue_smem_vb(uint32_t var_bytes, int n_bins, int n_q, int BN, int ew, int det);
+// deterministic mode (plan.cu): before a launch over `rows` rows, zero the plan's
+// fixed-point sums of displacements [t_begin, t_end) and set its scale; after it, add
+// them to C_sum / Sq_sum
+int fix_begin(asd_corr_plan *p, int64_t rows, int t_begin, int t_end, cudaStream_t s);
+int fix_end(asd_corr_plan *p, int t_begin, int t_end, double *C_sum, double *Sq_sum,
+            cudaStream_t s);
 }  // namespace asd

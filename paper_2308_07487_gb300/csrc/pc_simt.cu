@@ -6,7 +6,8 @@
 // tile in place: distance bins through FP64 shared-memory atomics, phase weights
 // through cos(a-b) = cos a cos b + sin a sin b with warp shuffles (Section 3.3, the
 // shuffle + shared-memory + atomic reduction), then one FP64 global atomic per bin
-// (and per q) per tile.  A is read straight from the trajectory row at the K-offset
+// (and per q) per tile.  In the deterministic mode the same sums are 64-bit fixed point
+// (integer atomics, the same bits in any order).  A is read straight from the trajectory row at the K-offset
 // s*3F + 3t; B is the prepared, zero-padded FP32 copy.
 #include "asd_internal.h"
 #include "geom.cuh"
@@ -28,6 +29,7 @@ struct SimtParams {
     int row_begin, row_end;
     int t_begin;      // displacement of grid slice blockIdx.z = 0
     EpiParams e;
+    int *err;         // device error word (index checks of a checked build)
 };
 
 __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
@@ -37,6 +39,10 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
     extern __shared__ double red[];  // [n_bins] then [n_q][q_parts]
     double *sbins = red;
     double *sq = red + P.e.n_bins;
+    // deterministic mode: the same arrays as fixed point
+    long long *sbins_i = reinterpret_cast<long long *>(sbins);
+    long long *sq_i = reinterpret_cast<long long *>(sq);
+    const double fscale = P.e.fix_scale ? *P.e.fix_scale : 0.0;
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -129,7 +135,10 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
                                      ? lattice_d2(ci, e.coords[jc], e.Lx, e.Ly, e.Lz, e.periodic)
                                      : position_d2(pi, e.pos[jc]);
                 const int b = bin_of_d2(d2, e.inv_w, e.n_bins, e.thr);
-                if (ok && b < e.n_bins) atomicAdd(&sbins[b], (double)acc[r][c]);
+                if (ok && b < e.n_bins && ASD_INB(b >= 0, BND_SIMT_BIN, P.err)) {
+                    if (fscale != 0.0) add_fixed(&sbins_i[b], to_fixed((double)acc[r][c], fscale));
+                    else atomicAdd(&sbins[b], (double)acc[r][c]);
+                }
             }
         }
     }
@@ -157,14 +166,28 @@ __global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
             // the warp's 32 partial sums (64 pairs each) in FP32, one FP64 add per warp
             // (FP64 arithmetic runs on a narrow pipe on this part)
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) atomicAdd(&sq[q * e.q_parts], (double)part);
+            const bool qok = lane == 0 && ASD_INB(q < e.nq_pad, BND_SIMT_Q, P.err);
+            if (qok) {
+                if (fscale != 0.0) add_fixed(&sq_i[q * e.q_parts], to_fixed((double)part, fscale));
+                else atomicAdd(&sq[q * e.q_parts], (double)part);
+            }
             if (e.q_parts == 2) {
                 for (int o = 16; o > 0; o >>= 1) part_s += __shfl_xor_sync(0xffffffffu, part_s, o);
-                if (lane == 0) atomicAdd(&sq[2 * q + 1], (double)part_s);
+                if (qok) {
+                    if (fscale != 0.0) add_fixed(&sq_i[2 * q + 1], to_fixed((double)part_s, fscale));
+                    else atomicAdd(&sq[2 * q + 1], (double)part_s);
+                }
             }
         }
     }
     __syncthreads();
+    if (fscale != 0.0) {
+        for (int b = tid; b < e.n_bins; b += 256)
+            if (sbins_i[b] != 0) add_fixed(&e.C_fix[(int64_t)t * e.n_bins + b], sbins_i[b]);
+        for (int o = tid; o < e.n_q * e.q_parts; o += 256)
+            if (sq_i[o] != 0) add_fixed(&e.Sq_fix[(int64_t)t * e.n_q * e.q_parts + o], sq_i[o]);
+        return;
+    }
     for (int b = tid; b < e.n_bins; b += 256)
         if (sbins[b] != 0.0) atomicAdd(&e.C_sum[(int64_t)t * e.n_bins + b], sbins[b]);
     for (int o = tid; o < e.n_q * e.q_parts; o += 256)
@@ -205,6 +228,11 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
     e.cs = p->cs;
     e.C_sum = C_sum;
     e.Sq_sum = Sq_sum;
+    e.C_fix = p->C_fix;
+    e.Sq_fix = p->Sq_fix;
+    e.fix_scale = p->d.deterministic ? p->fix_scale : nullptr;
+    P.err = device_error_word();
+    if (!P.err) return ASD_ECUDA;
     dim3 grid((unsigned)((row_end - row_begin + TM - 1) / TM), (unsigned)((p->N + TN - 1) / TN),
               (unsigned)(t_end - t_begin));
     if (grid.y > 65535u || grid.z > 65535u) {

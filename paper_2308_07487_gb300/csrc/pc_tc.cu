@@ -15,14 +15,14 @@ extern template int tc_launch_form<ASD_SPLIT_BF16>(const TcLaunchArgs &, size_t,
 
 uint32_t tc_var_bytes(int NW, int n_bins, int n_lut, int ew) { return var_bytes(NW, n_bins, n_lut, ew); }
 
-size_t tc_epilogue_smem_vb(uint32_t vb, int n_bins, int n_q, int BN, int ew)
+size_t tc_epilogue_smem_vb(uint32_t vb, int n_bins, int n_q, int BN, int ew, int det)
 {
-    return epi_layout(vb, n_bins, n_q, BN, ew).total;
+    return epi_layout(vb, n_bins, n_q, BN, ew, det).total;
 }
 
-size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut, int ew)
+size_t tc_epilogue_smem(int NW, int n_bins, int n_q, int BN, int n_lut, int ew, int det)
 {
-    return epi_layout(var_bytes(NW, n_bins, n_lut, ew), n_bins, n_q, BN, ew).total;
+    return epi_layout(var_bytes(NW, n_bins, n_lut, ew), n_bins, n_q, BN, ew, det).total;
 }
 
 // Bins window and stage count for the plan's current table choice; returns the number of
@@ -32,7 +32,9 @@ static int configure_once(asd_corr_plan *p, size_t cap, size_t stage_bytes)
     // private bins: as many as fit with at least 3 stages (2 when tight)
     int NW = p->n_bins;
     p->use_window = 0;
-    auto epi = [&](int nw) { return tc_epilogue_smem(nw, p->n_bins, p->n_q, p->BN, p->n_lut, p->EW); };
+    auto epi = [&](int nw) {
+        return tc_epilogue_smem(nw, p->n_bins, p->n_q, p->BN, p->n_lut, p->EW, p->d.deterministic);
+    };
     for (int min_st = 3; min_st >= 2; --min_st) {
         NW = p->n_bins;
         while (NW > 8 && epi(NW) + min_st * stage_bytes > cap) NW = (NW * 3) / 4;
@@ -71,7 +73,8 @@ int tc_configure(asd_corr_plan *p)
     if (st > 8) st = 8;
     if (p->d.stages > 0 && p->d.stages < st) st = p->d.stages;
     p->stages = st;
-    p->smem_bytes = tc_epilogue_smem(p->NW, p->n_bins, p->n_q, p->BN, p->n_lut, p->EW) +
+    p->smem_bytes = tc_epilogue_smem(p->NW, p->n_bins, p->n_q, p->BN, p->n_lut, p->EW,
+                                     p->d.deterministic) +
                     (size_t)p->stages * stage_bytes + 2048;
     // more than half of the SM's shared memory: never two CTAs (and TMEM owners) per SM
     if (p->smem_bytes < kMinSmem) p->smem_bytes = kMinSmem;
@@ -80,8 +83,8 @@ int tc_configure(asd_corr_plan *p)
 
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
               int BN, int swizzle_bytes, int stages, size_t smem, uint32_t var_bytes_,
-              int max_nb, int max_nq, int ew, int sm_count, unsigned long long *counter,
-              cudaStream_t s)
+              int max_nb, int max_nq, int ew, int det, int sm_count,
+              unsigned long long *counter, cudaStream_t s)
 {
     if (total_tiles <= 0) return ASD_OK;
     LaunchArgs a{};
@@ -96,6 +99,7 @@ int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOver
     if (a.counter) ASD_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s));
     a.NB = max_nb;
     a.NQ = max_nq;
+    a.det = det;
     a.err = device_error_word();
     if (!a.err) return ASD_ECUDA;
     (void)swizzle_bytes;
@@ -121,6 +125,36 @@ __global__ void wait_selftest_kernel(int *err, unsigned long long limit_ns)
 }
 
 }  // namespace asd
+
+#if ASD_CHECK_BOUNDS
+namespace asd {
+// One thread stores into a 16-entry shared array at index 16: the check fails, the store
+// is skipped and BND_SELFTEST is recorded.
+__global__ void bounds_selftest_kernel(int *err, int idx)
+{
+    __shared__ int a[16];
+    if (threadIdx.x == 0 && ASD_INB(idx >= 0 && idx < 16, BND_SELFTEST, err)) a[idx] = 1;
+}
+}  // namespace asd
+#endif
+
+int asd_build_flags(void) { return ASD_CHECK_BOUNDS ? ASD_BUILD_CHECK_BOUNDS : 0; }
+
+int asd_selftest_bounds(void *stream)
+{
+#if ASD_CHECK_BOUNDS
+    using namespace asd;
+    int *err = device_error_word();
+    if (!err) return ASD_ECUDA;
+    bounds_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(err, 16);
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+#else
+    (void)stream;
+    asd::set_error_text("not a checked build (ASD_CHECK_BOUNDS)");
+    return ASD_EUNSUPPORTED;
+#endif
+}
 
 int asd_selftest_timeout(int64_t limit_ns, void *stream)
 {

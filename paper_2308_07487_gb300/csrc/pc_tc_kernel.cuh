@@ -351,14 +351,17 @@ __host__ __device__ inline uint32_t var_bytes(int NW, int nb, int nlut, int ew)
 
 // Epilogue shared memory: the fixed arrays (sized for the largest n_bins / n_q of the
 // launch) and the per-problem region of `vb` bytes.
-__host__ __device__ inline EpiLayout epi_layout(uint32_t vb, int nb, int nq, int BN, int ew)
+__host__ __device__ inline EpiLayout epi_layout(uint32_t vb, int nb, int nq, int BN, int ew,
+                                                int det)
 {
     EpiLayout L;
     uint32_t o = 0;
+    // per-CTA bin sums (FP64, or 64-bit fixed point in the deterministic mode)
     L.cacc = take(o, 8u * (nb > 0 ? nb : 1));
-    // phase sums per q: (cosine, sine) parts
+    // phase sums per q: (cosine, sine) parts (FP64 or fixed point)
     L.qacc = take(o, 8u * 2 * (nq > 0 ? nq : 1));
-    L.fb = take(o, 4u * (nb > 0 ? nb : 1));
+    // fallback bins of pairs outside the private window (FP32, or fixed point)
+    L.fb = take(o, (det ? 8u : 4u) * (nb > 0 ? nb : 1));
     L.colgeo = take(o, 16u * BN);
     L.colpk = take(o, 4u * BN);
     L.boxred = take(o, 4u * ew * 12);
@@ -380,14 +383,17 @@ struct TileInfo {
 // launch would otherwise repeat a search over the descriptors in global memory per item).
 struct WorkCursor {
     int p = -1;
-    int64_t begin = 0, end = 0;  // flattened items [begin, end) belong to problem p
+    int64_t begin = 0, end = 0;  // flattened work items [begin, end) belong to problem p
     int tiles_m, tiles_n, kch, G, nk, row_begin, row_end, t_begin;
-    int64_t per_kc;
+    int64_t per_t;
 };
 
+// A work item is one (problem, displacement, row tile, column tile); its K chunks are
+// consecutive sub-items on the same CTA (they share the tile's geometry and private
+// bins).  decode(tau, c) gives chunk c of work item tau.
 __device__ __forceinline__ TileInfo decode(WorkCursor &cu, const TcProblem *__restrict__ probs,
                                            int n_probs, const TcOverride &ov, int64_t tau,
-                                           int BN)
+                                           int c, int BN)
 {
     if (cu.p < 0 || tau >= cu.end) {
         int p = cu.p < 0 ? 0 : cu.p;
@@ -417,15 +423,14 @@ __device__ __forceinline__ TileInfo decode(WorkCursor &cu, const TcProblem *__re
         cu.row_begin = ov.active ? ov.row_begin : P.row_begin;
         cu.row_end = ov.active ? ov.row_end : P.row_end;
         cu.t_begin = ov.active ? ov.t_begin : 0;
-        cu.per_kc = (int64_t)cu.tiles_m * cu.tiles_n;
+        cu.per_t = (int64_t)cu.tiles_m * cu.tiles_n;
     }
     const int64_t l = tau - cu.begin;
     TileInfo ti;
     ti.p = cu.p;
-    ti.t = cu.t_begin + (int)(l / (cu.per_kc * cu.kch));
-    const int64_t rem0 = l % (cu.per_kc * cu.kch);
-    const int kc = (int)(rem0 / cu.per_kc);
-    const int64_t rem = rem0 % cu.per_kc;
+    ti.t = cu.t_begin + (int)(l / cu.per_t);
+    const int kc = c;
+    const int64_t rem = l % cu.per_t;
     const int64_t gspan = (int64_t)cu.G * cu.tiles_n;
     const int first_m = (int)(rem / gspan) * cu.G;
     const int gsz = min(cu.G, cu.tiles_m - first_m);
@@ -443,10 +448,12 @@ __device__ __forceinline__ TileInfo decode(WorkCursor &cu, const TcProblem *__re
 // 8-byte load corrects it by one either way (the same result as two dependent fix-ups,
 // since the guess is within one bin).  Returns 0 .. n_bins + 1 (>= n_bins: dropped).
 __device__ __forceinline__ int bin_of_d2_pair(float d2, float inv_w, int nb,
-                                              const float2 *__restrict__ thr2)
+                                              const float2 *__restrict__ thr2, int *err)
 {
     const float r = d2 * rsqrtf(fmaxf(d2, 1e-30f));
     const int k = min((int)(r * inv_w), nb);
+    if (!ASD_INB(k >= 0, BND_THR, err)) return nb;  // dropped
+    (void)err;
     const float2 t = thr2[k];
     return k + (d2 >= t.y ? 1 : 0) - (d2 < t.x ? 1 : 0);
 }
@@ -456,6 +463,10 @@ struct BinArgs {
     int Lx, Ly, Lz, periodic;
     float inv_w;
     int nb, blo, nwp, trash;
+    int NB;                  // fallback bins of the launch
+    int n_lut;
+    double fscale;           // fixed-point scale (deterministic mode), else 0
+    int *err;
 };
 
 enum { BIN_LUT = 0, BIN_THR = 1, BIN_POS = 2 };
@@ -471,7 +482,7 @@ template <int MODE, int STRIDE>
 __device__ __forceinline__ void bin_chunk(const uint32_t (&g)[32], bool row_ok, int4 ri, float4 rp,
                                           const float4 *__restrict__ cgeo,
                                           const float *__restrict__ thr,
-                                          float *__restrict__ myb, float *__restrict__ fb,
+                                          float *__restrict__ myb, void *__restrict__ fbv,
                                           const BinArgs ba)
 {
     int slot[32];
@@ -481,27 +492,37 @@ __device__ __forceinline__ void bin_chunk(const uint32_t (&g)[32], bool row_ok, 
         int b;
         if (MODE == BIN_POS) {
             b = bin_of_d2_pair(position_d2(rp, cg), ba.inv_w, ba.nb,
-                               reinterpret_cast<const float2 *>(thr));
+                               reinterpret_cast<const float2 *>(thr), ba.err);
         } else {
             const int4 cj = make_int4(__float_as_int(cg.x), __float_as_int(cg.y),
                                       __float_as_int(cg.z), 0);
             const int d2 = lattice_d2i(ri, cj, ba.Lx, ba.Ly, ba.Lz, ba.periodic);
             if (MODE == BIN_LUT)
-                b = reinterpret_cast<const uint16_t *>(thr)[d2];
+                b = ASD_INB((unsigned)d2 < (unsigned)ba.n_lut, BND_LUT, ba.err)
+                        ? reinterpret_cast<const uint16_t *>(thr)[d2]
+                        : ba.nb;
             else
                 b = bin_of_d2_pair((float)d2, ba.inv_w, ba.nb,
-                                   reinterpret_cast<const float2 *>(thr));
+                                   reinterpret_cast<const float2 *>(thr), ba.err);
         }
         const int lb = b - ba.blo;
         slot[k] = (unsigned)lb < (unsigned)ba.nwp ? lb : (b < ba.nb ? -1 - b : ba.trash);
     }
+    const bool det = ba.fscale != 0.0;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
         // rows past the range: their accumulator rows may come from A rows that were
         // never prepared, so the value is replaced (a product with 0 would keep a NaN)
         const float val = row_ok ? __uint_as_float(g[k]) : 0.f;
-        if (slot[k] < 0) atomicAdd(&fb[-1 - slot[k]], val);
-        else myb[slot[k] * STRIDE] += val;
+        if (slot[k] < 0) {
+            const int b = -1 - slot[k];
+            if (!ASD_INB(b < ba.NB, BND_FALLBACK, ba.err)) continue;
+            // deterministic mode: fixed-point sums (integer adds in any order)
+            if (det) add_fixed(static_cast<long long *>(fbv) + b, to_fixed(val, ba.fscale));
+            else atomicAdd(static_cast<float *>(fbv) + b, val);
+        } else if (ASD_INB(slot[k] <= ba.trash, BND_PRIV, ba.err)) {
+            myb[slot[k] * STRIDE] += val;
+        }
     }
 }
 
@@ -514,8 +535,10 @@ template <bool LUT, int STRIDE>
 __device__ __forceinline__ void pk_offsets(uint32_t (&off)[32], uint32_t rpk, uint32_t Lpk,
                                            const uint4 *__restrict__ cpk,
                                            const void *__restrict__ tab, float inv_w, int nb,
-                                           uint32_t trash_off)
+                                           uint32_t trash_off, int n_lut, int *err)
 {
+    (void)n_lut;
+    (void)err;
 #pragma unroll
     for (int k4 = 0; k4 < 8; ++k4) {
         const uint4 c4 = cpk[k4];
@@ -526,10 +549,12 @@ __device__ __forceinline__ void pk_offsets(uint32_t (&off)[32], uint32_t rpk, ui
             d = __vminu4(d, __vsub4(Lpk, d));
             const uint32_t d2 = __dp4a(d, d, 0u);
             if (LUT) {
-                off[4 * k4 + u] = reinterpret_cast<const uint16_t *>(tab)[d2];
+                off[4 * k4 + u] = ASD_INB(d2 < (uint32_t)n_lut, BND_LUT, err)
+                                      ? reinterpret_cast<const uint16_t *>(tab)[d2]
+                                      : trash_off;
             } else {
-                const int b =
-                    bin_of_d2_pair((float)d2, inv_w, nb, reinterpret_cast<const float2 *>(tab));
+                const int b = bin_of_d2_pair((float)d2, inv_w, nb,
+                                             reinterpret_cast<const float2 *>(tab), err);
                 off[4 * k4 + u] = b < nb ? (uint32_t)(b * STRIDE) : trash_off;
             }
         }
@@ -544,11 +569,11 @@ template <int STRIDE>
 __device__ __forceinline__ void pos_offsets(uint32_t (&off)[32], float4 rp,
                                             const float4 *__restrict__ cgeo,
                                             const float2 *__restrict__ thr2, float inv_w, int nb,
-                                            int blo, uint32_t trash_off)
+                                            int blo, uint32_t trash_off, int *err)
 {
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        const int b = bin_of_d2_pair(position_d2(rp, cgeo[k]), inv_w, nb, thr2);
+        const int b = bin_of_d2_pair(position_d2(rp, cgeo[k]), inv_w, nb, thr2, err);
         off[k] = b < nb ? (uint32_t)((b - blo) * STRIDE) : trash_off;
     }
 }
@@ -573,14 +598,19 @@ __device__ __forceinline__ float warp_sum16(float (&z)[16], int lane)
     return z[0] + __shfl_xor_sync(0xffffffffu, z[0], 1);
 }
 
-// K block of a work item before which pass pp (of npass) of the previous item's phase
-// product is issued, always inside the item.  The epilogue needs the first part of the
-// item to bin and convert the previous tile, the rest of it to read the product out before
-// the accumulator is needed again: one pass goes in at 2/3 of the item, more passes are
-// spread over the rest of it.
-__device__ __forceinline__ int phase_slot(int pp, int nk, int npass)
+// K block of a work item before which sub-pass g (of G) of the previous item's phase
+// product is loaded and issued.  A sub-pass is one W stage (64 columns of one pass, the
+// pass's kWStages sub-passes in order).  The epilogue needs the first part of the item to
+// bin and convert the previous tile (the first sub-pass waits for that), the rest of it
+// to read the product out before the accumulator is needed again.  Sub-passes go in from
+// kSlotLo / kSlotDen of the item, evenly spaced up to kSlotHi / kSlotDen.  Measured on the
+// 32^3 glass (bins + 64 q, one pass of 3 sub-passes): all at 2/3 of the item 95.0 ms;
+// spread over [1/2, 5/6] 102.0, [1/3, 2/3] 101.4, [1/2, 1] 107.6, [1/6, 5/6] 112.1: the
+// binning of the previous tile sets the earliest slot, the read-out the latest.
+constexpr int kSlotLo = 2, kSlotHi = 2, kSlotDen = 3;
+__device__ __forceinline__ int phase_slot(int g, int nk, int G)
 {
-    return ((pp + 2) * nk) / (npass + 2);
+    return (nk * kSlotLo) / kSlotDen + (g * nk * (kSlotHi - kSlotLo)) / (kSlotDen * G);
 }
 
 // ------------------------------------------------------------------------------------
@@ -622,7 +652,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     const int stages = args.stages;
     uint8_t *tiles = smem;
     uint8_t *epi = tiles + (size_t)stages * kStageBytes;
-    const EpiLayout EL = epi_layout(args.VB, args.NB, args.NQ, BN, EW);
+    const EpiLayout EL = epi_layout(args.VB, args.NB, args.NQ, BN, EW, args.det);
     uint64_t *bars = reinterpret_cast<uint64_t *>(epi + EL.total);
     // bars: full[stages], empty[stages], tfull[2], tempty[2], drain, wqfull[kWQ],
     // wqempty[kWQ], conv, pfull, pempty; then the work ring wq[kWQ] and the TMEM address
@@ -676,90 +706,100 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             uint32_t phase = 0;
             bool ok = true;
             WorkCursor cu;
-            // the previous work item, while its phase passes are still to be loaded: they
-            // go in among this item's K blocks (pass pp before block phase_slot(pp)), so
-            // the phase product of item v - 1 runs while item v's MMAs run
-            int pend_p = -1, pend_n0 = 0, pend_np = 0;
+            // the previous work item, while its phase sub-passes are still to be loaded:
+            // they go in among this item's K blocks (sub-pass g before block
+            // phase_slot(g)), so the phase product of item v - 1 runs while item v's MMAs
+            // run
+            int pend_p = -1, pend_n0 = 0, pend_G = 0;
             auto next_stage = [&]() {
                 if (++stage == stages) {
                     stage = 0;
                     phase ^= 1;
                 }
             };
-            auto load_pass = [&](int pp) {
+            // W stage j of pass pp (sub-pass g = pp kWStages + j)
+            auto load_sub = [&](int g) {
                 const TcProblem &Q = probs[pend_p];
-                for (int j = 0; j < kWStages; ++j) {
-                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, args.err, DEV_TIMEOUT_TMA))
-                        return false;
-                    const uint32_t fb = full0 + 8 * stage;
-                    mbar_expect_tx(fb, kWPlanes * kWBytes);
-                    uint8_t *st = tiles + (size_t)stage * kStageBytes;
+                const int pp = g / kWStages, j = g % kWStages;
+                if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, args.err, DEV_TIMEOUT_TMA))
+                    return false;
+                const uint32_t fb = full0 + 8 * stage;
+                mbar_expect_tx(fb, kWPlanes * kWBytes);
+                uint8_t *st = tiles + (size_t)stage * kStageBytes;
 #pragma unroll
-                    for (int pl = 0; pl < kWPlanes; ++pl)
-                        tma_load_2d(saddr(st + pl * kWBytes), &Q.mapW[pl], fb, pend_n0 + 64 * j,
-                                    pp * kPCols);
-                    next_stage();
-                }
+                for (int pl = 0; pl < kWPlanes; ++pl)
+                    tma_load_2d(saddr(st + pl * kWBytes), &Q.mapW[pl], fb, pend_n0 + 64 * j,
+                                pp * kPCols);
+                next_stage();
                 return true;
             };
-            for (int64_t v = 0; ok; ++v) {
-                // publish the next work item (-1: none left) once its ring slot is free
-                const int qs = (int)(v % kWQ);
-                if (!mbar_wait(wqempty0 + 8 * qs, (uint32_t)((v / kWQ) & 1) ^ 1u, args.err,
-                               DEV_TIMEOUT_TMA)) {
-                    ok = false;
-                    break;
-                }
+            int64_t v = 0;  // sub-items published
+            for (int64_t vt = 0; ok; ++vt) {
+                // claim the next work item; its K chunks are published one by one
                 int64_t tau = args.counter ? (int64_t)atomicAdd(args.counter, 1ull)
-                                           : cid + v * n_ctas;
+                                           : cid + vt * n_ctas;
                 if (tau >= args.total_tiles) tau = -1;
-                wq[qs] = tau;
-                mbar_arrive(wqfull0 + 8 * qs);  // release: the slot is visible to the waiters
-                if (tau < 0) break;
-                const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau, BN);
-                const TcProblem &P = probs[ti.p];
-                const int nk = ti.kg1 - ti.kg0;
-                int pp = 0;
-                for (int kg = ti.kg0; kg < ti.kg1 && ok; ++kg) {
-                    if constexpr (kPhaseOK) {
-                        while (pend_p >= 0 && pp < pend_np &&
-                               kg - ti.kg0 == phase_slot(pp, nk, pend_np)) {
-                            if (!load_pass(pp++)) {
-                                ok = false;
-                                break;
-                            }
-                        }
-                        if (!ok) break;
-                    }
-                    const int s = kg / P.nkb, kb = kg % P.nkb;
-                    const int xw = s * P.F3 + 3 * ti.t;
-                    const int c = xw % P.n_copies;
-                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, args.err, DEV_TIMEOUT_TMA)) {
+                const int kch = tau < 0 ? 1 : probs[decode(cu, probs, args.n_probs, args.ov,
+                                                           tau, 0, BN).p].k_chunks;
+                for (int kci = 0; kci < kch && ok; ++kci, ++v) {
+                    // publish the sub-item (tau 256 + chunk; -1: none left) once its ring slot
+                    // is free
+                    const int qs = (int)(v % kWQ);
+                    if (!mbar_wait(wqempty0 + 8 * qs, (uint32_t)((v / kWQ) & 1) ^ 1u, args.err,
+                                   DEV_TIMEOUT_TMA)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t fb = full0 + 8 * stage;
-                    mbar_expect_tx(fb, kStageBytes);
-                    uint8_t *st = tiles + (size_t)stage * kStageBytes;
+                    wq[qs] = tau < 0 ? -1 : tau * 256 + kci;
+                    mbar_arrive(wqfull0 + 8 * qs);  // release: the slot is visible to the waiters
+                    if (tau < 0) break;
+                    const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau, kci, BN);
+                    const TcProblem &P = probs[ti.p];
+                    const int nk = ti.kg1 - ti.kg0;
+                    int g = 0;
+                    for (int kg = ti.kg0; kg < ti.kg1 && ok; ++kg) {
+                        if constexpr (kPhaseOK) {
+                            while (pend_p >= 0 && g < pend_G &&
+                                   kg - ti.kg0 == phase_slot(g, nk, pend_G)) {
+                                if (!load_sub(g++)) {
+                                    ok = false;
+                                    break;
+                                }
+                            }
+                            if (!ok) break;
+                        }
+                        const int s = kg / P.nkb, kb = kg % P.nkb;
+                        const int xw = s * P.F3 + 3 * ti.t;
+                        const int c = xw % P.n_copies;
+
+                        if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, args.err, DEV_TIMEOUT_TMA)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t fb = full0 + 8 * stage;
+                        mbar_expect_tx(fb, kStageBytes);
+                        uint8_t *st = tiles + (size_t)stage * kStageBytes;
 #pragma unroll
-                    for (int pl = 0; pl < kPlanes; ++pl) {
-                        tma_load_2d(saddr(st + pl * kABytes), &P.mapA[pl][c], fb,
-                                    xw - c + kb * kBK, ti.m0);
-                        tma_load_2d(saddr(st + kPlanes * kABytes + pl * kBBytes), &P.mapB[pl], fb,
-                                    s * P.Kseg + kb * kBK, ti.n0);
+                        for (int pl = 0; pl < kPlanes; ++pl) {
+                            tma_load_2d(saddr(st + pl * kABytes), &P.mapA[pl][c], fb,
+                                        xw - c + kb * kBK, ti.m0);
+                            tma_load_2d(saddr(st + kPlanes * kABytes + pl * kBBytes),
+                                        &P.mapB[pl], fb, s * P.Kseg + kb * kBK, ti.n0);
+                        }
+                        next_stage();
                     }
-                    next_stage();
+                    pend_p = -1;
+                    if (kPhaseOK && P.epi.n_q > 0) {
+                        pend_p = ti.p;
+                        pend_n0 = ti.n0;
+                        pend_G = P.epi.npass * kWStages;
+                    }
                 }
-                pend_p = -1;
-                if (kPhaseOK && P.epi.n_q > 0) {
-                    pend_p = ti.p;
-                    pend_n0 = ti.n0;
-                    pend_np = P.epi.npass;
-                }
+                if (tau < 0) break;
             }
-            // the last item's phase passes
+            // the last item's phase sub-passes
             if (kPhaseOK && ok && pend_p >= 0)
-                for (int pp = 0; pp < pend_np && ok; ++pp) ok = load_pass(pp);
+                for (int g = 0; g < pend_G && ok; ++g) ok = load_sub(g);
             // drain: wait until the last fill of every stage has landed
             for (int k = 0; k < stages; ++k) {
                 if (--stage < 0) {
@@ -779,52 +819,52 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             uint32_t v = 0;
             bool ok = true;
             WorkCursor cu;
-            // previous item with phase passes still to issue (its accumulator buffer), the
-            // count of converted tiles waited for and of phase passes issued
-            int pend_acc = -1, pend_np = 0;
+            // previous item with phase sub-passes still to issue (its accumulator buffer),
+            // the count of converted tiles waited for and of phase passes issued
+            int pend_acc = -1, pend_G = 0;
             uint32_t n_conv = 0, n_pass = 0;
             const uint32_t ptm = tmem + 2 * BN;  // phase product P
-            // one pass of the previous item's phase product: P = G W over the kWStages W
-            // stages of the ring, A = the BF16 hi / lo copy of G in its accumulator columns
-            auto issue_pass = [&](int pp) {
+            // sub-pass g of the previous item's phase product: pass pp = g / kWStages adds
+            // G[:, c] W[c, :] for the 64 columns c of W stage j = g % kWStages to P, A = the
+            // BF16 hi / lo copy of G in its accumulator columns
+            auto issue_sub = [&](int g) {
+                const int pp = g / kWStages, j = g % kWStages;
                 const uint32_t g0 = tmem + (uint32_t)pend_acc * BN;
-                for (int j = 0; j < kWStages; ++j) {
-                    if (!mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_MMA))
+                if (!mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_MMA)) return false;
+                if (j == 0) {
+                    // G stored as BF16 by the epilogue (once per item), P read out
+                    if (pp == 0 && !mbar_wait(conv, n_conv++ & 1, args.err, DEV_TIMEOUT_MMA))
                         return false;
-                    if (j == 0) {
-                        // G stored as BF16 by the epilogue (once per item), P read out
-                        if (pp == 0 &&
-                            !mbar_wait(conv, n_conv++ & 1, args.err, DEV_TIMEOUT_MMA))
-                            return false;
-                        if (!mbar_wait(pempty, (n_pass & 1) ^ 1, args.err, DEV_TIMEOUT_MMA))
-                            return false;
-                    }
-                    tc_after();
-                    uint8_t *st = tiles + (size_t)stage * kStageBytes;
-                    const uint64_t w0 = sdesc(saddr(st), 128);
-                    const uint64_t w1 = sdesc(saddr(st + kWBytes), 128);
+                    if (!mbar_wait(pempty, (n_pass & 1) ^ 1, args.err, DEV_TIMEOUT_MMA))
+                        return false;
+                }
+                tc_after();
+                uint8_t *st = tiles + (size_t)stage * kStageBytes;
+                const uint64_t w0 = sdesc(saddr(st), 128);
+                const uint64_t w1 = sdesc(saddr(st + kWBytes), 128);
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        // columns c = 64 j + 16 ks: chunk c / 32 holds hi in its first 16
-                        // TMEM columns and lo in the next 16
-                        const int c = 64 * j + 16 * ks;
-                        const uint32_t ahi = g0 + 32 * (c >> 5) + 8 * ((c >> 4) & 1);
-                        const uint64_t off = (uint64_t)(ks * 32) >> 4;
-                        const uint32_t accum = (j | ks) != 0;
-                        tc_mma_ts(ptm, ahi, w0 + off, kIdescP, accum);           // hi*hi
-                        if (kWPlanes == 2) {
-                            tc_mma_ts(ptm, ahi, w1 + off, kIdescP, 1u);          // hi*lo
-                            tc_mma_ts(ptm, ahi + 16, w0 + off, kIdescP, 1u);     // lo*hi
-                        }
-                    }
-                    tc_commit(empty0 + 8 * stage);
-                    if (++stage == stages) {
-                        stage = 0;
-                        phase ^= 1;
+                for (int ks = 0; ks < 4; ++ks) {
+                    // columns c = 64 j + 16 ks: chunk c / 32 holds hi in its first 16 TMEM
+                    // columns and lo in the next 16
+                    const int c = 64 * j + 16 * ks;
+                    const uint32_t ahi = g0 + 32 * (c >> 5) + 8 * ((c >> 4) & 1);
+                    const uint64_t off = (uint64_t)(ks * 32) >> 4;
+                    const uint32_t accum = (j | ks) != 0;
+                    tc_mma_ts(ptm, ahi, w0 + off, kIdescP, accum);           // hi*hi
+                    if (kWPlanes == 2) {
+                        tc_mma_ts(ptm, ahi, w1 + off, kIdescP, 1u);          // hi*lo
+                        tc_mma_ts(ptm, ahi + 16, w0 + off, kIdescP, 1u);     // lo*hi
                     }
                 }
-                tc_commit(pfull);
-                ++n_pass;
+                tc_commit(empty0 + 8 * stage);
+                if (++stage == stages) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+                if (j == kWStages - 1) {
+                    tc_commit(pfull);
+                    ++n_pass;
+                }
                 return true;
             };
             for (;; ++v) {
@@ -836,7 +876,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 const int64_t tau = wq[qs];
                 mbar_arrive(wqempty0 + 8 * qs);
                 if (tau < 0) break;
-                const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau, BN);
+                const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau >> 8,
+                                           (int)(tau & 255), BN);
                 const uint32_t acc = v & 1, use = v >> 1;
                 if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, args.err, DEV_TIMEOUT_MMA)) {
                     ok = false;
@@ -845,12 +886,12 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 tc_after();
                 const uint32_t d = tmem + acc * BN;
                 const int nk = ti.kg1 - ti.kg0;
-                int pp = 0;
+                int g = 0;
                 for (int kg = ti.kg0; kg < ti.kg1; ++kg) {
                     const int kb = kg - ti.kg0;  // 0 for the first block of this chunk
                     if constexpr (kPhaseOK) {
-                        while (pend_acc >= 0 && pp < pend_np && kb == phase_slot(pp, nk, pend_np)) {
-                            if (!issue_pass(pp++)) {
+                        while (pend_acc >= 0 && g < pend_G && kb == phase_slot(g, nk, pend_G)) {
+                            if (!issue_sub(g++)) {
                                 ok = false;
                                 break;
                             }
@@ -890,12 +931,12 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 pend_acc = -1;
                 if (kPhaseOK && probs[ti.p].epi.n_q > 0) {
                     pend_acc = (int)acc;
-                    pend_np = probs[ti.p].epi.npass;
+                    pend_G = probs[ti.p].epi.npass * kWStages;
                 }
             }
-            // the last item's phase passes
+            // the last item's phase sub-passes
             if (kPhaseOK && ok && pend_acc >= 0)
-                for (int pp = 0; pp < pend_np && ok; ++pp) ok = issue_pass(pp);
+                for (int g = 0; g < pend_G && ok; ++g) ok = issue_sub(g);
             // drain every MMA this thread issued before TMEM is released
             tc_commit(drain);
             mbar_wait(drain, 0, args.err, DEV_TIMEOUT_MMA);
@@ -913,13 +954,18 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         float *fb = reinterpret_cast<float *>(epi + EL.fb);
         double *cacc = reinterpret_cast<double *>(epi + EL.cacc);
         double *qacc = reinterpret_cast<double *>(epi + EL.qacc);
+        // the same arrays as 64-bit fixed point (problems in the deterministic mode)
+        long long *fbi = reinterpret_cast<long long *>(epi + EL.fb);
+        long long *cacci = reinterpret_cast<long long *>(epi + EL.cacc);
+        long long *qacci = reinterpret_cast<long long *>(epi + EL.qacc);
         float4 *colgeo = reinterpret_cast<float4 *>(epi + EL.colgeo);
         uint32_t *colpk = reinterpret_cast<uint32_t *>(epi + EL.colpk);
         float *boxred = reinterpret_cast<float *>(epi + EL.boxred);
         float *thr_s = bins;
         for (int k = et; k < args.NB; k += kEpiThreads) {
-            fb[k] = 0.f;
-            cacc[k] = 0.0;
+            if (args.det) fbi[k] = 0;
+            else fb[k] = 0.f;
+            cacc[k] = 0.0;  // (all-zero bits: also fixed-point zero)
         }
         for (int k = et; k < 2 * args.NQ; k += kEpiThreads) qacc[k] = 0.0;
 
@@ -952,21 +998,39 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         };
         uint32_t v = 0;
         bool ok = true;
+        // geometry of the current tile, set by its first K chunk: this thread's row site,
+        // the bin window start and, for positions, whether the tile's bins fit the window
+        int4 ri = make_int4(0, 0, 0, 0);
+        float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
+        int blo = 0, bhi_tile = 0;
+        bool pos_fit = false;
         // per-CTA FP64 sums of the current (problem, t), added to the outputs when it changes
+        // (deterministic mode: fixed-point sums into the problem's fixed-point arrays)
         auto flush_acc = [&](int p, int t) {
             const EpiParams &E = probs[p].epi;
             double *Cs = args.ov.active ? args.ov.C_sum : E.C_sum;
             double *Qs = args.ov.active ? args.ov.Sq_sum : E.Sq_sum;
+            const bool det = E.fix_scale != nullptr;
+            const bool t_ok = ASD_INB((unsigned)t < (unsigned)probs[p].n_t, BND_WORK, args.err);
             for (int b = et; b < E.n_bins; b += kEpiThreads) {
-                if (cacc[b] != 0.0) atomicAdd(&Cs[(int64_t)t * E.n_bins + b], cacc[b]);
+                const int64_t o = (int64_t)t * E.n_bins + b;
+                if (det) {
+                    if (cacci[b] != 0 && t_ok) add_fixed(&E.C_fix[o], cacci[b]);
+                } else if (cacc[b] != 0.0 && t_ok) {
+                    atomicAdd(&Cs[o], cacc[b]);
+                }
                 cacc[b] = 0.0;
             }
             for (int q = et; q < E.n_q; q += kEpiThreads)
                 for (int part = 0; part < E.q_parts; ++part) {
-                    double &acc = qacc[2 * q + part];
-                    if (acc != 0.0)
-                        atomicAdd(&Qs[((int64_t)t * E.n_q + q) * E.q_parts + part], acc);
-                    acc = 0.0;
+                    const int64_t o = ((int64_t)t * E.n_q + q) * E.q_parts + part;
+                    if (det) {
+                        if (qacci[2 * q + part] != 0 && t_ok)
+                            add_fixed(&E.Sq_fix[o], qacci[2 * q + part]);
+                    } else if (qacc[2 * q + part] != 0.0 && t_ok) {
+                        atomicAdd(&Qs[o], qacc[2 * q + part]);
+                    }
+                    qacc[2 * q + part] = 0.0;
                 }
         };
         for (;; ++v) {
@@ -981,125 +1045,145 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             __syncwarp();
             if (lane == 0) mbar_arrive(wqempty0 + 8 * qs);
             if (tau < 0) break;
-            const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau, BN);
+            const int kci = (int)(tau & 255);
+            const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau >> 8, kci, BN);
             const TcProblem &P = probs[ti.p];
             const EpiParams &E = P.epi;
+            // the first K chunk of a tile sets up its geometry and bin window; the chunks
+            // add into the same private bins, which the last one reduces
+            const bool first = kci == 0, last = kci == P.k_chunks - 1;
             const int i = ti.m0 + r;
             const bool row_ok = i < ti.row_end;
             // rows past the range (ragged tiles) read the
             // geometry of a valid site and contribute zeros
             const int ic = row_ok ? i : P.N - 1;
             const bool lattice = E.geom == ASD_GEOM_LATTICE;
-            // bin thresholds of this problem, then the column geometry of this tile
-            if (E.n_bins > 0 && ti.p != tab_p) {
-                // lay out the per-problem region for this problem: every thread is done
-                // with the previous problem's bins (flushed and zeroed at each tile's end)
-                // and table, then the new bins are zeroed and the new table loaded
-                epi_sync(kEpiThreads);
-                bins = reinterpret_cast<float *>(epi + EL.var);
-                thr_s = reinterpret_cast<float *>(epi + EL.var + var_bins_bytes(E.NW, EW));
-                for (int k = et; k < (E.NW + 1) * kBinStride; k += kEpiThreads) bins[k] = 0.f;
-                // thresholds, or the lattice d2 -> bin table, of this problem
-                if (E.n_lut > 0) {
-                    // fast form: entries become private-bin word offsets (the host checked
-                    // that (n_bins + 1) * stride fits 16 bits)
-                    // (dropped pairs: the trash row E.NW, which no flush reads)
-                    uint16_t *lut_s = reinterpret_cast<uint16_t *>(thr_s);
-                    for (int k = et; k < E.n_lut; k += kEpiThreads) {
-                        const int b = E.lut[k];
-                        lut_s[k] = (uint16_t)(fast_ok(E) ? (b < E.n_bins ? b : E.NW) * kBinStride
-                                                         : b);
+            // (a checked build also tests that the problem's bins and table fit the
+            // launch's per-problem region; if not, the problem is not binned)
+            const bool bins_on =
+                E.n_bins > 0 &&
+                ASD_INB(var_bytes(E.NW, E.n_bins, E.n_lut, EW) <= args.VB, BND_REGION, args.err);
+            // fixed-point scale of a problem in the deterministic mode (0: FP sums)
+            const double fscale = E.fix_scale ? *E.fix_scale : 0.0;
+            if (first) {
+                // bin thresholds of this problem, then the column geometry of this tile
+                if (bins_on && ti.p != tab_p) {
+                    // lay out the per-problem region for this problem: every thread is done
+                    // with the previous problem's bins (flushed and zeroed at each tile's end)
+                    // and table, then the new bins are zeroed and the new table loaded
+                    epi_sync(kEpiThreads);
+                    bins = reinterpret_cast<float *>(epi + EL.var);
+                    thr_s = reinterpret_cast<float *>(epi + EL.var + var_bins_bytes(E.NW, EW));
+                    for (int k = et; k < (E.NW + 1) * kBinStride; k += kEpiThreads) bins[k] = 0.f;
+                    // thresholds, or the lattice d2 -> bin table, of this problem
+                    if (E.n_lut > 0) {
+                        // fast form: entries become private-bin word offsets (the host checked
+                        // that (n_bins + 1) * stride fits 16 bits)
+                        // (dropped pairs: the trash row E.NW, which no flush reads)
+                        uint16_t *lut_s = reinterpret_cast<uint16_t *>(thr_s);
+                        for (int k = et; k < E.n_lut; k += kEpiThreads) {
+                            const int b = E.lut[k];
+                            lut_s[k] = (uint16_t)(fast_ok(E) ? (b < E.n_bins ? b : E.NW) * kBinStride
+                                                             : b);
+                        }
+                    } else {
+                        float2 *thr2 = reinterpret_cast<float2 *>(thr_s);
+                        for (int k = et; k <= E.n_bins; k += kEpiThreads)
+                            thr2[k] = make_float2(E.thr[k], E.thr[k + 1]);
                     }
-                } else {
-                    float2 *thr2 = reinterpret_cast<float2 *>(thr_s);
-                    for (int k = et; k <= E.n_bins; k += kEpiThreads)
-                        thr2[k] = make_float2(E.thr[k], E.thr[k + 1]);
+                    tab_p = ti.p;
                 }
-                tab_p = ti.p;
-            }
-            for (int c = et; c < BN; c += kEpiThreads) {
-                const int j = min(ti.n0 + c, P.N - 1);
-                if (lattice) {
-                    const int4 g = E.coords[j];
-                    colgeo[c] = make_float4(__int_as_float(g.x), __int_as_float(g.y),
-                                            __int_as_float(g.z), 0.f);
-                    colpk[c] = (uint32_t)g.x | ((uint32_t)g.y << 8) | ((uint32_t)g.z << 16);
-                } else {
-                    colgeo[c] = E.pos[j];
-                }
-            }
-            const int4 ri = E.coords[ic];
-            const float4 rp = E.pos[ic];
-            // bounding boxes for the bin window (only when the bins do not all fit)
-            if (E.use_window) {
-                float v6[12];
-                v6[0] = v6[3] = rp.x;
-                v6[1] = v6[4] = rp.y;
-                v6[2] = v6[5] = rp.z;
+                // column geometry of the tile (one load per column, which also feeds the
+                // column bounding box when the bins do not all fit the window)
                 float cl[3] = {3e38f, 3e38f, 3e38f}, ch[3] = {-3e38f, -3e38f, -3e38f};
                 for (int c = et; c < BN; c += kEpiThreads) {
                     const int j = min(ti.n0 + c, P.N - 1);
-                    const float4 pj = E.pos[j];
+                    float4 pj;
+                    if (lattice) {
+                        const int4 g = E.coords[j];
+                        colgeo[c] = make_float4(__int_as_float(g.x), __int_as_float(g.y),
+                                                __int_as_float(g.z), 0.f);
+                        colpk[c] = (uint32_t)g.x | ((uint32_t)g.y << 8) | ((uint32_t)g.z << 16);
+                        pj = make_float4((float)g.x, (float)g.y, (float)g.z, 0.f);
+                    } else {
+                        pj = E.pos[j];
+                        colgeo[c] = pj;
+                    }
                     cl[0] = fminf(cl[0], pj.x); ch[0] = fmaxf(ch[0], pj.x);
                     cl[1] = fminf(cl[1], pj.y); ch[1] = fmaxf(ch[1], pj.y);
                     cl[2] = fminf(cl[2], pj.z); ch[2] = fmaxf(ch[2], pj.z);
                 }
-                for (int a = 0; a < 3; ++a) {
-                    v6[6 + a] = cl[a];
-                    v6[9 + a] = ch[a];
-                }
-                if (!row_ok) {
+                ri = E.coords[ic];
+                rp = lattice ? make_float4((float)ri.x, (float)ri.y, (float)ri.z, 0.f) : E.pos[ic];
+                // bounding boxes for the bin window (only when the bins do not all fit)
+                if (E.use_window) {
+                    float v6[12];
+                    v6[0] = v6[3] = rp.x;
+                    v6[1] = v6[4] = rp.y;
+                    v6[2] = v6[5] = rp.z;
                     for (int a = 0; a < 3; ++a) {
-                        v6[a] = 3e38f;
-                        v6[3 + a] = -3e38f;
+                        v6[6 + a] = cl[a];
+                        v6[9 + a] = ch[a];
+                    }
+                    if (!row_ok) {
+                        for (int a = 0; a < 3; ++a) {
+                            v6[a] = 3e38f;
+                            v6[3 + a] = -3e38f;
+                        }
+                    }
+                    for (int o = 16; o > 0; o >>= 1)
+                        for (int k = 0; k < 12; ++k) {
+                            const float w = __shfl_xor_sync(0xffffffffu, v6[k], o);
+                            v6[k] = ((k % 6) < 3) ? fminf(v6[k], w) : fmaxf(v6[k], w);
+                        }
+                    if (lane == 0)
+                        for (int k = 0; k < 12; ++k) boxred[ew * 12 + k] = v6[k];
+                }
+                epi_sync(kEpiThreads);  // colgeo / boxred ready; previous tile fully flushed
+                if (ti.p != cur_p || ti.t != cur_t) {
+                    if (cur_p >= 0) flush_acc(cur_p, cur_t);
+                    cur_p = ti.p;
+                    cur_t = ti.t;
+                }
+                blo = 0;
+                // positions: whether every kept bin of the tile lies inside the private window
+                // [blo, blo + NW), from the largest distance between the two bounding boxes
+                pos_fit = !E.use_window;
+                bhi_tile = E.n_bins - 1;
+                if (E.use_window) {
+                    float d2min = 0.f, d2max = 0.f;
+                    for (int a = 0; a < 3; ++a) {
+                        float rl = 3e38f, rh = -3e38f, cl = 3e38f, ch = -3e38f;
+                        for (int w = 0; w < kEpiWarps; ++w) {
+                            rl = fminf(rl, boxred[w * 12 + a]);
+                            rh = fmaxf(rh, boxred[w * 12 + 3 + a]);
+                            cl = fminf(cl, boxred[w * 12 + 6 + a]);
+                            ch = fmaxf(ch, boxred[w * 12 + 9 + a]);
+                        }
+                        float gap = fmaxf(0.f, fmaxf(cl - rh, rl - ch));
+                        if (lattice && E.periodic) {
+                            const float L = a == 0 ? E.Lx : a == 1 ? E.Ly : E.Lz;
+                            gap = fminf(gap, fmaxf(0.f, fmaxf(cl + L - rh, rl - (ch + L))));
+                            gap = fminf(gap, fmaxf(0.f, fmaxf(cl - L - rh, rl - (ch - L))));
+                        }
+                        d2min += gap * gap;
+                        const float far = fmaxf(ch - rl, rh - cl);
+                        d2max += far * far;
+                    }
+                    // (the thresholds from shared memory unless it holds the lattice table)
+                    const float2 *thr2 = reinterpret_cast<const float2 *>(thr_s);
+                    const bool tab = E.n_lut > 0;
+                    blo = max(0, (tab ? bin_of_d2(d2min * 0.999f, E.inv_w, E.n_bins, E.thr)
+                                      : bin_of_d2_pair(d2min * 0.999f, E.inv_w, E.n_bins, thr2,
+                                                       args.err)) - 1);
+                    if (!lattice) {
+                        bhi_tile = min(E.n_bins - 1,
+                                       bin_of_d2_pair(d2max * 1.001f + 1e-30f, E.inv_w, E.n_bins,
+                                                      thr2, args.err) + 1);
+                        pos_fit = bhi_tile - blo < E.NW;
                     }
                 }
-                for (int o = 16; o > 0; o >>= 1)
-                    for (int k = 0; k < 12; ++k) {
-                        const float w = __shfl_xor_sync(0xffffffffu, v6[k], o);
-                        v6[k] = ((k % 6) < 3) ? fminf(v6[k], w) : fmaxf(v6[k], w);
-                    }
-                if (lane == 0)
-                    for (int k = 0; k < 12; ++k) boxred[ew * 12 + k] = v6[k];
-            }
-            epi_sync(kEpiThreads);  // colgeo / boxred ready; previous tile fully flushed
-            if (ti.p != cur_p || ti.t != cur_t) {
-                if (cur_p >= 0) flush_acc(cur_p, cur_t);
-                cur_p = ti.p;
-                cur_t = ti.t;
-            }
-            int blo = 0;
-            // positions: whether every kept bin of the tile lies inside the private window
-            // [blo, blo + NW), from the largest distance between the two bounding boxes
-            bool pos_fit = !E.use_window;
-            int bhi_tile = E.n_bins - 1;
-            if (E.use_window) {
-                float d2min = 0.f, d2max = 0.f;
-                for (int a = 0; a < 3; ++a) {
-                    float rl = 3e38f, rh = -3e38f, cl = 3e38f, ch = -3e38f;
-                    for (int w = 0; w < kEpiWarps; ++w) {
-                        rl = fminf(rl, boxred[w * 12 + a]);
-                        rh = fmaxf(rh, boxred[w * 12 + 3 + a]);
-                        cl = fminf(cl, boxred[w * 12 + 6 + a]);
-                        ch = fmaxf(ch, boxred[w * 12 + 9 + a]);
-                    }
-                    float gap = fmaxf(0.f, fmaxf(cl - rh, rl - ch));
-                    if (lattice && E.periodic) {
-                        const float L = a == 0 ? E.Lx : a == 1 ? E.Ly : E.Lz;
-                        gap = fminf(gap, fmaxf(0.f, fmaxf(cl + L - rh, rl - (ch + L))));
-                        gap = fminf(gap, fmaxf(0.f, fmaxf(cl - L - rh, rl - (ch - L))));
-                    }
-                    d2min += gap * gap;
-                    const float far = fmaxf(ch - rl, rh - cl);
-                    d2max += far * far;
-                }
-                blo = max(0, bin_of_d2(d2min * 0.999f, E.inv_w, E.n_bins, E.thr) - 1);
-                if (!lattice) {
-                    bhi_tile = min(E.n_bins - 1,
-                                   bin_of_d2(d2max * 1.001f + 1e-30f, E.inv_w, E.n_bins, E.thr) + 1);
-                    pos_fit = bhi_tile - blo < E.NW;
-                }
-            }
+            }  // first chunk
 
             // phase weights of this item go through the tensor core (see kPhaseOK)
             const bool ph = kPhaseOK && E.n_q > 0;
@@ -1110,7 +1194,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             tc_after();
             const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + acc * BN;
 
-            if (E.n_bins > 0) {
+            if (bins_on) {
                 BinArgs ba;
                 ba.Lx = E.Lx;
                 ba.Ly = E.Ly;
@@ -1121,6 +1205,10 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 ba.blo = E.use_window ? blo : 0;
                 ba.nwp = E.use_window ? E.NW : E.n_bins;
                 ba.trash = E.NW;
+                ba.NB = args.NB;
+                ba.n_lut = E.n_lut;
+                ba.fscale = fscale;
+                ba.err = args.err;
                 const int mode = !lattice ? BIN_POS : (E.n_lut > 0 ? BIN_LUT : BIN_THR);
                 if (fast_ok(E)) {
                     // rows past the range skip the pairs (the TMEM loads stay warp-wide)
@@ -1136,14 +1224,16 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         const uint4 *cp = reinterpret_cast<const uint4 *>(colpk + ch * 32);
                         if (lut)
                             pk_offsets<true, kBinStride>(off, rpk, E.Lpk, cp, thr_s, E.inv_w,
-                                                         E.n_bins, trash_off);
+                                                         E.n_bins, trash_off, E.n_lut, args.err);
                         else
                             pk_offsets<false, kBinStride>(off, rpk, E.Lpk, cp, thr_s, E.inv_w,
-                                                          E.n_bins, trash_off);
+                                                          E.n_bins, trash_off, E.n_lut, args.err);
                         tmem_wait32(g);
                         if (row_ok) {
 #pragma unroll
-                            for (int k = 0; k < 32; ++k) mb[off[k]] += __uint_as_float(g[k]);
+                            for (int k = 0; k < 32; ++k)
+                                if (ASD_INB(off[k] <= trash_off, BND_PRIV, args.err))
+                                    mb[off[k]] += __uint_as_float(g[k]);
                         }
                         if (ph) to_bf16(g, tbase + ch * 32, row_ok);
                     }
@@ -1157,11 +1247,13 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         uint32_t g[32], off[32];
                         tmem_ld32_issue(tbase + ch * 32, g);
                         pos_offsets<kBinStride>(off, rp, colgeo + ch * 32, thr2, E.inv_w,
-                                                E.n_bins, b0, trash_off);
+                                                E.n_bins, b0, trash_off, args.err);
                         tmem_wait32(g);
                         if (row_ok) {
 #pragma unroll
-                            for (int k = 0; k < 32; ++k) mb[off[k]] += __uint_as_float(g[k]);
+                            for (int k = 0; k < 32; ++k)
+                                if (ASD_INB(off[k] <= trash_off, BND_PRIV, args.err))
+                                    mb[off[k]] += __uint_as_float(g[k]);
                         }
                         if (ph) to_bf16(g, tbase + ch * 32, row_ok);
                     }
@@ -1171,12 +1263,13 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     tmem_ld32(tbase + ch * 32, g);
                     const float4 *cg = colgeo + ch * 32;
                     float *mb = bins + r + kBM * half;
+                    void *fbv = fscale != 0.0 ? static_cast<void *>(fbi) : static_cast<void *>(fb);
                     if (mode == BIN_LUT)
-                        bin_chunk<BIN_LUT, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fb, ba);
+                        bin_chunk<BIN_LUT, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fbv, ba);
                     else if (mode == BIN_THR)
-                        bin_chunk<BIN_THR, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fb, ba);
+                        bin_chunk<BIN_THR, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fbv, ba);
                     else
-                        bin_chunk<BIN_POS, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fb, ba);
+                        bin_chunk<BIN_POS, kBinStride>(g, row_ok, ri, rp, cg, thr_s, mb, fbv, ba);
                     if (ph) to_bf16(g, tbase + ch * 32, row_ok);
                 }
             } else if (ph) {
@@ -1193,8 +1286,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             tc_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(ph ? conv : tempty0 + 8 * acc);
-            epi_sync(kEpiThreads);  // all private bins written
-            if (E.n_bins > 0) {
+            if (last) epi_sync(kEpiThreads);  // all private bins written
+            if (bins_on && last) {
                 // private rows this tile may have written: with the branch-free position
                 // path only the tile's own bin range, else the whole window / bin set
                 const int NWp = !E.use_window ? E.n_bins
@@ -1223,14 +1316,22 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         for (int u = 0; u < 4; ++u) v4[u] += __shfl_xor_sync(0xffffffffu, v4[u], o);
                     if (lane == 0)
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (b0 + u < NWp && blo + b0 + u < E.n_bins)
-                                cacc[blo + b0 + u] += (double)v4[u];
+                        for (int u = 0; u < 4; ++u) {
+                            const int b = blo + b0 + u;
+                            if (b0 + u < NWp && b < E.n_bins &&
+                                ASD_INB(b < args.NB, BND_CACC, args.err)) {
+                                if (fscale != 0.0) cacci[b] += to_fixed((double)v4[u], fscale);
+                                else cacc[b] += (double)v4[u];
+                            }
+                        }
                 }
                 if (E.use_window) {
                     epi_sync(kEpiThreads);  // the fallback bins update the same accumulators
                     for (int b = et; b < E.n_bins; b += kEpiThreads) {
-                        if (fb[b] != 0.f) {
+                        if (fscale != 0.0) {
+                            cacci[b] += fbi[b];
+                            fbi[b] = 0;
+                        } else if (fb[b] != 0.f) {
                             cacc[b] += (double)fb[b];
                             fb[b] = 0.f;
                         }
@@ -1247,24 +1348,32 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 const float4 *cs4 = reinterpret_cast<const float4 *>(E.cs) +
                                     (int64_t)ic * (E.nq_pad / 2);
                 const uint32_t pt = tmem + ((uint32_t)(q4 * 32) << 16) + 2 * BN;
+                // (with 8 epilogue warps the two warps of a lane quarter take half of
+                // the pass's q-vectors each)
+                constexpr int kJ = kPhaseQ / 16 / kHalves;
+                // row weights of 16 q-vectors (8 float4: cos, sin of two q each): the
+                // loads of the next group are in flight while the current one is used,
+                // those of a pass's first group while its product completes
+                auto load_cs = [&](float4 (&c)[8], int q0) {
+                    if (q0 < E.n_q && ASD_INB(q0 + 16 <= E.nq_pad, BND_Q, args.err))
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) c[k] = cs4[q0 / 2 + k];
+                };
                 for (int pp = 0; pp < E.npass && ok; ++pp) {
+                    float4 c4[8];
+                    load_cs(c4, pp * kPhaseQ + 16 * half * kJ);
                     const bool gotp = mbar_wait(pfull, n_pass & 1, args.err, DEV_TIMEOUT_EPI);
                     ++n_pass;
                     ok = epi_sync_and(gotp, kEpiThreads);
                     if (!ok) break;
                     tc_after();
-                    // (with 8 epilogue warps the two warps of a lane quarter take half of
-                    // the pass's q-vectors each)
-                    constexpr int kJ = kPhaseQ / 16 / kHalves;
                     for (int j = half * kJ; j < (half + 1) * kJ; ++j) {
                         const int q0 = pp * kPhaseQ + 16 * j;
                         if (q0 >= E.n_q) break;
                         uint32_t u[16], w[16];
+                        if (j > half * kJ) load_cs(c4, q0);
                         tmem_ld16(pt + 16 * j, u);
                         tmem_ld16(pt + kPhaseQ + 16 * j, w);
-                        float4 c4[8];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) c4[k] = cs4[q0 / 2 + k];
                         tmem_wait16x2(u, w);
                         float x[16], y[16];
 #pragma unroll
@@ -1279,12 +1388,23 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                             y[2 * k + 1] = fmaf(sb, u1, -cb * v1);
                         }
                         const int qme = q0 + (lane >> 1);
+                        const bool qok = (lane & 1) == 0 && qme < E.n_q &&
+                                         ASD_INB(qme < args.NQ, BND_Q, args.err);
+                        // deterministic mode: fixed-point adds (any order, same bits)
                         const float xs = warp_sum16(x, lane);
-                        if ((lane & 1) == 0 && qme < E.n_q) atomicAdd(&qacc[2 * qme], (double)xs);
+                        if (qok) {
+                            if (fscale != 0.0)
+                                add_fixed(&qacci[2 * qme], to_fixed((double)xs, fscale));
+                            else atomicAdd(&qacc[2 * qme], (double)xs);
+                        }
                         if (E.q_parts == 2) {
                             const float ys = warp_sum16(y, lane);
-                            if ((lane & 1) == 0 && qme < E.n_q)
-                                atomicAdd(&qacc[2 * qme + 1], (double)ys);
+                            if (qok) {
+                                if (fscale != 0.0)
+                                    add_fixed(&qacci[2 * qme + 1], to_fixed((double)ys, fscale));
+                                else
+                                    atomicAdd(&qacc[2 * qme + 1], (double)ys);
+                            }
                         }
                     }
                     // P read: the next pass (or item) may overwrite it

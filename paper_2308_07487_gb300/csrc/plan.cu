@@ -68,6 +68,43 @@ __global__ void normalize_kernel(const double *C_sum, double *C, int n_t, int n_
     if (Sq_sum && k < (int64_t)n_t * n_q) Sq[k] = Sq_sum[k] * inv_nq;
 }
 
+// Deterministic mode.  Largest |x| of the trajectory (FP32 bits of non-negative floats
+// order like the floats, so an integer max is exact and order-free).
+__global__ void amax_kernel(const float *__restrict__ x, int64_t n, unsigned int *out)
+{
+    unsigned int m = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fabsf(x[k])));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Fixed-point scale 2^e of one launch: the largest power of two with
+// bound * 2^e < 2^61, bound = 2 rows N K max|a| max|b| (>= the sum of |terms| of any
+// partial or total sum the launch forms, with room for rounding).
+__global__ void fix_scale_kernel(const unsigned int *amax_bits, double rows, double N, double K,
+                                 double b_factor, double *scale)
+{
+    const double a = (double)__uint_as_float(*amax_bits);
+    const double bound = 2.0 * rows * N * K * a * (a * b_factor);
+    double sc = 1.0;
+    if (bound > 0.0 && bound < 1e300) {
+        int ex;
+        frexp(bound, &ex);             // bound in [2^(ex-1), 2^ex)
+        sc = ldexp(1.0, 61 - ex);      // bound * sc < 2^61
+    }
+    *scale = sc;
+}
+
+// out[k] += fix[k] / scale for k < n (then the next launch starts from zeroed sums)
+__global__ void fix_add_kernel(const long long *__restrict__ fix, int64_t n,
+                               const double *scale, double *__restrict__ out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] += (double)fix[k] / *scale;
+}
+
 static EpiParams epi_of(const asd_corr_plan *p)
 {
     EpiParams e{};
@@ -106,6 +143,9 @@ static EpiParams epi_of(const asd_corr_plan *p)
     e.npass = p->tc && p->n_q > 0 ? (p->n_q + kPhaseQ - 1) / kPhaseQ : 0;
     e.q_parts = p->q_parts;
     e.cs = p->cs;
+    e.C_fix = p->C_fix;
+    e.Sq_fix = p->Sq_fix;
+    e.fix_scale = p->d.deterministic ? p->fix_scale : nullptr;
     return e;
 }
 
@@ -216,8 +256,58 @@ static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int6
     tp->n_copies = p->n_copies;
     tp->group_m = p->d.raster_m > 0 ? p->d.raster_m : 16;
     tp->k_chunks = p->k_chunks;
-    tp->n_tiles = tc_work_items(p->n_t, p->k_chunks, tp->tiles_m, tp->tiles_n);
+    tp->n_tiles = tc_work_items(p->n_t, tp->tiles_m, tp->tiles_n);
     tp->epi = epi_of(p);
+    return ASD_OK;
+}
+
+// ---- deterministic mode (asd_corr_desc.deterministic) ----
+// Largest |x| of the trajectory, the operand bound of the fixed-point scale.
+static int fix_amax(asd_corr_plan *p, const float *traj, cudaStream_t s)
+{
+    if (!p->d.deterministic) return ASD_OK;
+    ASD_CUDA_TRY(cudaMemsetAsync(p->amax_bits, 0, sizeof(unsigned int), s));
+    const int64_t n = p->N * p->R;
+    amax_kernel<<<(unsigned)(p->sm_count * 8), 256, 0, s>>>(traj, n, p->amax_bits);
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}
+
+int fix_begin(asd_corr_plan *p, int64_t rows, int t_begin, int t_end, cudaStream_t s)
+{
+    if (!p->d.deterministic) return ASD_OK;
+    const int64_t nt = t_end - t_begin;
+    if (p->n_bins > 0)
+        ASD_CUDA_TRY(cudaMemsetAsync(p->C_fix + (int64_t)t_begin * p->n_bins, 0,
+                                     sizeof(long long) * nt * p->n_bins, s));
+    if (p->n_q > 0)
+        ASD_CUDA_TRY(cudaMemsetAsync(p->Sq_fix + (int64_t)t_begin * p->n_q * p->q_parts, 0,
+                                     sizeof(long long) * nt * p->n_q * p->q_parts, s));
+    // centring subtracts a mean from B: |b| <= 2 max|x|
+    fix_scale_kernel<<<1, 1, 0, s>>>(p->amax_bits, (double)rows, (double)p->N,
+                                     (double)p->S * 3.0 * p->T0, p->center ? 2.0 : 1.0,
+                                     p->fix_scale);
+    ASD_CUDA_TRY(cudaGetLastError());
+    return ASD_OK;
+}
+
+int fix_end(asd_corr_plan *p, int t_begin, int t_end, double *C_sum, double *Sq_sum,
+            cudaStream_t s)
+{
+    if (!p->d.deterministic) return ASD_OK;
+    const int64_t nt = t_end - t_begin;
+    if (p->n_bins > 0 && C_sum) {
+        const int64_t n = nt * p->n_bins, o = (int64_t)t_begin * p->n_bins;
+        fix_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->C_fix + o, n, p->fix_scale,
+                                                                  C_sum + o);
+        ASD_CUDA_TRY(cudaGetLastError());
+    }
+    if (p->n_q > 0 && Sq_sum) {
+        const int64_t n = nt * p->n_q * p->q_parts, o = (int64_t)t_begin * p->n_q * p->q_parts;
+        fix_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->Sq_fix + o, n,
+                                                                  p->fix_scale, Sq_sum + o);
+        ASD_CUDA_TRY(cudaGetLastError());
+    }
     return ASD_OK;
 }
 
@@ -238,6 +328,7 @@ const char *asd_strerror(int status)
     case ASD_ECUDA: base = "CUDA error"; break;
     case ASD_ETIMEOUT: base = "bounded device wait timed out"; break;
     case ASD_EUNSUPPORTED: base = "unsupported"; break;
+    case ASD_EBOUNDS: base = "index check failed (checked build)"; break;
     }
     s = base;
     if (status != ASD_OK && !g_err_text.empty()) s += ": " + g_err_text;
@@ -253,6 +344,12 @@ int asd_sync_status(void *stream)
         int zero = 0;
         ASD_CUDA_TRY(cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int)));
         char buf[96];
+        if (v >= DEV_BOUNDS) {
+            snprintf(buf, sizeof buf, "device error word = %d (index check site %d)", v,
+                     v - (int)DEV_BOUNDS);
+            set_error_text(buf);
+            return ASD_EBOUNDS;
+        }
         snprintf(buf, sizeof buf, "device error word = %d", v);
         set_error_text(buf);
         return ASD_ETIMEOUT;
@@ -273,6 +370,7 @@ void asd_pair_corr_plan_destroy(asd_corr_plan *p)
     cudaFree(p->W);
     cudaFree(p->sqF);
     cudaFree(p->counter);
+    cudaFree(p->C_fix);
     cudaFree(p->inv_counts);
     cudaFree(p->d_prob);
     cudaFree(p->batch_desc);
@@ -325,6 +423,7 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
     }
     ASD_CHECK_ARG(d->static_schedule == 0 || d->static_schedule == 1, "static_schedule: 0 or 1");
     ASD_CHECK_ARG(d->phase_sine == 0 || d->phase_sine == 1, "phase_sine: 0 or 1");
+    ASD_CHECK_ARG(d->deterministic == 0 || d->deterministic == 1, "deterministic: 0 or 1");
     if (d->geometry == ASD_GEOM_LATTICE) {
         ASD_CHECK_ARG(d->coords, "coords required for lattice geometry");
         for (int a = 0; a < 3; ++a) ASD_CHECK_ARG(d->L[a] >= 1 && d->L[a] <= 1 << 20, "bad L");
@@ -624,6 +723,21 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
             return fail(ASD_ECUDA);
     }
 
+    // ---- deterministic mode: fixed-point sums, operand bound, scale (one allocation) ----
+    if (d->deterministic) {
+        const size_t nc = (size_t)p->n_t * p->n_bins, nq = (size_t)p->n_t * p->n_q * p->q_parts;
+        const size_t bytes = 8 * (nc + nq) + 16;
+        if (cudaMalloc(&p->C_fix, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p->C_fix = nullptr;
+            return fail(ASD_ENOMEM);
+        }
+        if (cudaMemset(p->C_fix, 0, bytes) != cudaSuccess) return fail(ASD_ECUDA);
+        p->Sq_fix = p->C_fix + nc;
+        p->fix_scale = reinterpret_cast<double *>(p->C_fix + nc + nq);
+        p->amax_bits = reinterpret_cast<unsigned int *>(p->fix_scale + 1);
+    }
+
     // ---- tensor maps for the whole row range ----
     if (tc) {
         p->h_prob = new (std::nothrow) TcProblem;
@@ -664,6 +778,8 @@ int asd_pair_corr_prepare(asd_corr_plan *p, const float *traj, int64_t row_begin
     ASD_CHECK_ARG(((uintptr_t)traj & 15) == 0, "traj must be 16-byte aligned");
     int rc = launch_prep(p, traj, row_begin, row_end, (cudaStream_t)stream);
     if (rc) return rc;
+    rc = fix_amax(p, traj, (cudaStream_t)stream);
+    if (rc) return rc;
     p->prepared_traj = traj;
     p->prepared_begin = row_begin;
     p->prepared_end = row_end;
@@ -691,9 +807,12 @@ int asd_pair_corr_contract_range(asd_corr_plan *p, int64_t row_begin, int64_t ro
     ASD_CHECK_ARG(p->n_q == 0 || Sq_sum, "Sq_sum required when n_q > 0");
     if (row_begin == row_end || t_begin == t_end) return ASD_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!p->tc)
-        return launch_simt(p, p->prepared_traj, row_begin, row_end, t_begin, t_end, C_sum, Sq_sum,
-                           s);
+    int rc = fix_begin(p, row_end - row_begin, t_begin, t_end, s);
+    if (rc) return rc;
+    if (!p->tc) {
+        rc = launch_simt(p, p->prepared_traj, row_begin, row_end, t_begin, t_end, C_sum, Sq_sum, s);
+        return rc ? rc : fix_end(p, t_begin, t_end, C_sum, Sq_sum, s);
+    }
     TcOverride ov{};
     ov.active = 1;
     ov.row_begin = (int)row_begin;
@@ -701,13 +820,14 @@ int asd_pair_corr_contract_range(asd_corr_plan *p, int64_t row_begin, int64_t ro
     ov.t_begin = t_begin;
     ov.n_t = t_end - t_begin;
     ov.tiles_m = (int)((row_end - row_begin + kBM - 1) / kBM);
-    ov.n_tiles = tc_work_items(ov.n_t, p->k_chunks, ov.tiles_m, p->h_prob->tiles_n);
+    ov.n_tiles = tc_work_items(ov.n_t, ov.tiles_m, p->h_prob->tiles_n);
     ov.C_sum = C_sum;
     ov.Sq_sum = Sq_sum;
-    return launch_tc(p->d_prob, 1, ov.n_tiles, ov, p->prec, p->BN, p->swizzle_bytes, p->stages,
-                     p->smem_bytes, tc_var_bytes(p->NW, p->n_bins, p->n_lut, p->EW), p->n_bins,
-                     p->n_q, p->EW, p->sm_count,
-                     p->d.static_schedule ? nullptr : p->counter, s);
+    rc = launch_tc(p->d_prob, 1, ov.n_tiles, ov, p->prec, p->BN, p->swizzle_bytes, p->stages,
+                   p->smem_bytes, tc_var_bytes(p->NW, p->n_bins, p->n_lut, p->EW), p->n_bins,
+                   p->n_q, p->EW, p->d.deterministic, p->sm_count,
+                   p->d.static_schedule ? nullptr : p->counter, s);
+    return rc ? rc : fix_end(p, t_begin, t_end, C_sum, Sq_sum, s);
 }
 
 int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs, int n,
@@ -723,6 +843,8 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
         ASD_CHECK_ARG(p && trajs[k], "null plan or trajectory");
         ASD_CHECK_ARG(p->tc && p->prec == p0->prec && p->BN == p0->BN && p->EW == p0->EW,
                       "batched plans must share precision and tile width");
+        ASD_CHECK_ARG(p->d.deterministic == p0->d.deterministic,
+                      "batched plans must share the deterministic mode");
         ASD_CHECK_ARG(p->device == p0->device, "plans on different devices");
         ASD_CHECK_ARG(p->n_bins == 0 || (C_sum && C_sum[k]), "C_sum required");
         ASD_CHECK_ARG(p->n_q == 0 || (Sq_sum && Sq_sum[k]), "Sq_sum required");
@@ -747,7 +869,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
         };
         for (int k = 0; k < n; ++k) nlut[k] = plans[k]->n_lut;
         vb = largest();
-        while (tc_epilogue_smem_vb(vb, max_nb, max_nq, p0->BN, p0->EW) + 3 * stage_bytes > cap) {
+        while (tc_epilogue_smem_vb(vb, max_nb, max_nq, p0->BN, p0->EW, p0->d.deterministic) + 3 * stage_bytes > cap) {
             int kk = -1;
             for (int k = 0; k < n; ++k)
                 if (nlut[k] > 0 && (kk < 0 || region(k) > region(kk))) kk = k;
@@ -755,7 +877,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
             nlut[kk] = 0;
             vb = largest();
         }
-        const size_t epi = tc_epilogue_smem_vb(vb, max_nb, max_nq, p0->BN, p0->EW);
+        const size_t epi = tc_epilogue_smem_vb(vb, max_nb, max_nq, p0->BN, p0->EW, p0->d.deterministic);
         if (epi + 2 * stage_bytes > cap) {
             set_error_text("batched epilogue does not fit shared memory");
             return ASD_EUNSUPPORTED;
@@ -796,8 +918,8 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     for (int k = 0; k < n; ++k) order[k] = k;
     auto items = [&](int k) {
         const asd_corr_plan *p = plans[k];
-        return tc_work_items(p->n_t, p->k_chunks, (int)((p->N + kBM - 1) / kBM),
-                             p->h_prob->tiles_n);
+        return p->k_chunks *
+               tc_work_items(p->n_t, (int)((p->N + kBM - 1) / kBM), p->h_prob->tiles_n);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return items(a) > items(b); });
     std::vector<TcProblem> h((size_t)n);
@@ -810,7 +932,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
         hk.row_begin = 0;
         hk.row_end = (int)p->N;
         hk.tiles_m = (int)((p->N + kBM - 1) / kBM);
-        hk.n_tiles = tc_work_items(p->n_t, p->k_chunks, hk.tiles_m, hk.tiles_n);
+        hk.n_tiles = tc_work_items(p->n_t, hk.tiles_m, hk.tiles_n);
         hk.tile_begin = total;
         hk.epi.n_lut = nlut[k];  // 0: the threshold rule (see above)
         hk.epi.C_sum = C_sum ? C_sum[k] : nullptr;
@@ -826,6 +948,8 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     }
     for (int k = 0; k < n; ++k) {
         int rc = launch_prep(plans[k], trajs[k], 0, plans[k]->N, s);
+        if (!rc) rc = fix_amax(plans[k], trajs[k], s);
+        if (!rc) rc = fix_begin(plans[k], plans[k]->N, 0, plans[k]->n_t, s);
         if (rc) return rc;
     }
     TcOverride ov{};
@@ -834,8 +958,13 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     bool dyn = true;
     for (int k = 0; k < n; ++k) dyn = dyn && !plans[k]->d.static_schedule;
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(dbuf + kMaxProblems);
-    return launch_tc(dbuf, n, total, ov, p0->prec, p0->BN, p0->swizzle_bytes, stages, smem, vb,
-                     max_nb, max_nq, p0->EW, p0->sm_count, dyn ? ctr : nullptr, s);
+    int rc = launch_tc(dbuf, n, total, ov, p0->prec, p0->BN, p0->swizzle_bytes, stages, smem, vb,
+                       max_nb, max_nq, p0->EW, p0->d.deterministic, p0->sm_count,
+                       dyn ? ctr : nullptr, s);
+    for (int k = 0; k < n && !rc; ++k)
+        rc = fix_end(plans[k], 0, plans[k]->n_t, C_sum ? C_sum[k] : nullptr,
+                     Sq_sum ? Sq_sum[k] : nullptr, s);
+    return rc;
 }
 
 int asd_pair_corr_normalize(const asd_corr_plan *p, const double *C_sum, const double *Sq_sum,
