@@ -114,6 +114,8 @@ struct EpiParams {
     int Lx, Ly, Lz;
     int periodic;
     float inv_w;
+    float w;                // bin width in FP32
+    int thr_exact;          // every threshold thr[k] = RN(RN(k w)^2) (computable in-kernel)
     int n_bins;
     int NW;                 // private bins held per thread (window width)
     int use_window;         // 1: window start derived from per-tile boxes
@@ -221,6 +223,7 @@ struct asd_corr_plan {
     int4 *coords;
     float4 *pos;
     float *thr;
+    int thr_exact;             // thr[k] == RN(RN(k w)^2) for every k (see EpiParams)
     uint16_t *lut;             // lattice d2 -> bin table (nullptr when d2 can reach kLutMax)
     int n_lut;
     float2 *cs;

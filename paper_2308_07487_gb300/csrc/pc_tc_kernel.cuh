@@ -561,19 +561,34 @@ __device__ __forceinline__ void pk_offsets(uint32_t (&off)[32], uint32_t rpk, ui
     }
 }
 
+// The same bin when every threshold is an exact FP32 square (k w)^2 = RN(RN(k w)^2), as
+// for a power-of-two width (the host checks the whole table): the two thresholds around
+// the first guess are computed instead of loaded.
+__device__ __forceinline__ int bin_of_d2_exact(float d2, float inv_w, float w, int nb)
+{
+    const float r = d2 * rsqrtf(fmaxf(d2, 1e-30f));
+    const int k = min((int)(r * inv_w), nb);
+    const float kw = __fmul_rn((float)k, w), kw1 = __fmul_rn((float)(k + 1), w);
+    const float lo = __fmul_rn(kw, kw), hi = __fmul_rn(kw1, kw1);
+    return k + (d2 >= hi ? 1 : 0) - (d2 < lo ? 1 : 0);
+}
+
 // Fast form of bin_chunk's first phase for FP32 positions, when every pair of the tile
 // falls inside the private window (see the epilogue): the exact bin of each pair from
-// its FP32 d2 and the thresholds, as a private-bin word offset; dropped pairs go to the
-// trash row, so no pair takes a branch.
-template <int STRIDE>
+// its FP32 d2 and the thresholds (loaded, or computed when EXACT), as a private-bin word
+// offset; dropped pairs go to the trash row, so no pair takes a branch.
+template <int STRIDE, bool EXACT>
 __device__ __forceinline__ void pos_offsets(uint32_t (&off)[32], float4 rp,
                                             const float4 *__restrict__ cgeo,
-                                            const float2 *__restrict__ thr2, float inv_w, int nb,
-                                            int blo, uint32_t trash_off, int *err)
+                                            const float2 *__restrict__ thr2, float inv_w,
+                                            float w, int nb, int blo, uint32_t trash_off,
+                                            int *err)
 {
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        const int b = bin_of_d2_pair(position_d2(rp, cgeo[k]), inv_w, nb, thr2, err);
+        const float d2 = position_d2(rp, cgeo[k]);
+        const int b = EXACT ? bin_of_d2_exact(d2, inv_w, w, nb)
+                            : bin_of_d2_pair(d2, inv_w, nb, thr2, err);
         off[k] = b < nb ? (uint32_t)((b - blo) * STRIDE) : trash_off;
     }
 }
@@ -655,16 +670,19 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     const EpiLayout EL = epi_layout(args.VB, args.NB, args.NQ, BN, EW, args.det);
     uint64_t *bars = reinterpret_cast<uint64_t *>(epi + EL.total);
     // bars: full[stages], empty[stages], tfull[2], tempty[2], drain, wqfull[kWQ],
-    // wqempty[kWQ], conv, pfull, pempty; then the work ring wq[kWQ] and the TMEM address
-    // slot
+    // wqempty[kWQ], conv, pfull, pempty, tmm[2]; then the work ring wq[kWQ] and the TMEM
+    // address slot
     const uint32_t wqfull0 = saddr(bars + 2 * stages + 5);
     const uint32_t wqempty0 = saddr(bars + 2 * stages + 5 + kWQ);
-    // conv: the epilogue has stored a tile's G as BF16 hi / lo (one arrival per warp);
-    // pfull: the phase product of a pass is complete; pempty: the epilogue has read it
+    // conv: the epilogue has stored a chunk's G as BF16 hi / lo (one arrival per warp);
+    // pfull: the phase product to be read out is complete; pempty: the epilogue has read
+    // it; tmm[a]: the phase product of the chunk in accumulator a is complete, so the
+    // buffer is free (for phase work the MMA thread releases the accumulator, not the
+    // epilogue)
     const uint32_t conv = saddr(bars + 2 * stages + 5 + 2 * kWQ);
-    const uint32_t pfull = conv + 8, pempty = conv + 16;
-    volatile int64_t *wq = reinterpret_cast<volatile int64_t *>(bars + 2 * stages + 8 + 2 * kWQ);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 8 + 3 * kWQ);
+    const uint32_t pfull = conv + 8, pempty = conv + 16, tmm0 = conv + 24;
+    volatile int64_t *wq = reinterpret_cast<volatile int64_t *>(bars + 2 * stages + 10 + 2 * kWQ);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 10 + 3 * kWQ);
     const uint32_t full0 = saddr(bars), empty0 = saddr(bars + stages);
     const uint32_t tfull0 = saddr(bars + 2 * stages), tempty0 = saddr(bars + 2 * stages + 2);
     const uint32_t drain = saddr(bars + 2 * stages + 4);
@@ -689,6 +707,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         mbar_init(conv, kEpiWarps);
         mbar_init(pfull, 1);
         mbar_init(pempty, kEpiWarps);
+        mbar_init(tmm0, 1);
+        mbar_init(tmm0 + 8, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) tmem_alloc(saddr(tmem_slot), kTmemAlloc);
@@ -819,10 +839,19 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             uint32_t v = 0;
             bool ok = true;
             WorkCursor cu;
-            // previous item with phase sub-passes still to issue (its accumulator buffer),
-            // the count of converted tiles waited for and of phase passes issued
+            // previous sub-item with phase sub-passes still to issue: its accumulator
+            // buffer and sub-pass count; whether its product adds to P (a later K chunk of
+            // a tile with one pass: P sums the chunks and is read out once) and whether it
+            // completes P for the read-out
             int pend_acc = -1, pend_G = 0;
-            uint32_t n_conv = 0, n_pass = 0;
+            bool pend_add = false, pend_done = false;
+            // converted chunks waited for; passes that started P afresh (one read-out each)
+            uint32_t n_conv = 0, n_own = 0;
+            // how each accumulator was last released (0: not used yet, 1: by the epilogue
+            // on tempty, 2: by this thread's commit on tmm after the chunk's phase product)
+            // and the waits taken on each barrier
+            int rel[2] = {0, 0};
+            uint32_t n_te[2] = {0, 0}, n_tm[2] = {0, 0};
             const uint32_t ptm = tmem + 2 * BN;  // phase product P
             // sub-pass g of the previous item's phase product: pass pp = g / kWStages adds
             // G[:, c] W[c, :] for the 64 columns c of W stage j = g % kWStages to P, A = the
@@ -832,11 +861,15 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 const uint32_t g0 = tmem + (uint32_t)pend_acc * BN;
                 if (!mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_MMA)) return false;
                 if (j == 0) {
-                    // G stored as BF16 by the epilogue (once per item), P read out
+                    // G stored as BF16 by the epilogue (once per chunk); a pass that starts
+                    // P afresh waits until the previous P has been read out
                     if (pp == 0 && !mbar_wait(conv, n_conv++ & 1, args.err, DEV_TIMEOUT_MMA))
                         return false;
-                    if (!mbar_wait(pempty, (n_pass & 1) ^ 1, args.err, DEV_TIMEOUT_MMA))
-                        return false;
+                    if (!pend_add) {
+                        if (!mbar_wait(pempty, (n_own & 1) ^ 1, args.err, DEV_TIMEOUT_MMA))
+                            return false;
+                        ++n_own;
+                    }
                 }
                 tc_after();
                 uint8_t *st = tiles + (size_t)stage * kStageBytes;
@@ -849,7 +882,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     const int c = 64 * j + 16 * ks;
                     const uint32_t ahi = g0 + 32 * (c >> 5) + 8 * ((c >> 4) & 1);
                     const uint64_t off = (uint64_t)(ks * 32) >> 4;
-                    const uint32_t accum = (j | ks) != 0;
+                    const uint32_t accum = pend_add || (j | ks) != 0;
                     tc_mma_ts(ptm, ahi, w0 + off, kIdescP, accum);           // hi*hi
                     if (kWPlanes == 2) {
                         tc_mma_ts(ptm, ahi, w1 + off, kIdescP, 1u);          // hi*lo
@@ -861,10 +894,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     stage = 0;
                     phase ^= 1;
                 }
-                if (j == kWStages - 1) {
-                    tc_commit(pfull);
-                    ++n_pass;
-                }
+                if (j == kWStages - 1 && pend_done) tc_commit(pfull);
+                // the chunk's accumulator is free once its phase product has completed
+                if (g == pend_G - 1) tc_commit(tmm0 + 8 * pend_acc);
                 return true;
             };
             for (;; ++v) {
@@ -876,13 +908,23 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 const int64_t tau = wq[qs];
                 mbar_arrive(wqempty0 + 8 * qs);
                 if (tau < 0) break;
-                const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau >> 8,
-                                           (int)(tau & 255), BN);
-                const uint32_t acc = v & 1, use = v >> 1;
-                if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, args.err, DEV_TIMEOUT_MMA)) {
+                const int kci = (int)(tau & 255);
+                const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau >> 8, kci, BN);
+                const TcProblem &P = probs[ti.p];
+                const bool phs = kPhaseOK && P.epi.n_q > 0;
+                const uint32_t acc = v & 1;
+                // wait until the accumulator's previous chunk has released it
+                if (rel[acc] == 1 &&
+                    !mbar_wait(tempty0 + 8 * acc, n_te[acc]++ & 1, args.err, DEV_TIMEOUT_MMA)) {
                     ok = false;
                     break;
                 }
+                if (rel[acc] == 2 &&
+                    !mbar_wait(tmm0 + 8 * acc, n_tm[acc]++ & 1, args.err, DEV_TIMEOUT_MMA)) {
+                    ok = false;
+                    break;
+                }
+                rel[acc] = phs ? 2 : 1;
                 tc_after();
                 const uint32_t d = tmem + acc * BN;
                 const int nk = ti.kg1 - ti.kg0;
@@ -929,9 +971,13 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 if (!ok) break;
                 tc_commit(tfull0 + 8 * acc);
                 pend_acc = -1;
-                if (kPhaseOK && probs[ti.p].epi.n_q > 0) {
+                if (phs) {
+                    // one pass: P sums the tile's chunks and is read out after the last
+                    const bool across = P.epi.npass == 1;
                     pend_acc = (int)acc;
-                    pend_G = probs[ti.p].epi.npass * kWStages;
+                    pend_G = P.epi.npass * kWStages;
+                    pend_add = across && kci > 0;
+                    pend_done = !across || kci == P.k_chunks - 1;
                 }
             }
             // the last item's phase sub-passes
@@ -1246,8 +1292,14 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     for (int ch = ch0; ch < ch1; ++ch) {
                         uint32_t g[32], off[32];
                         tmem_ld32_issue(tbase + ch * 32, g);
-                        pos_offsets<kBinStride>(off, rp, colgeo + ch * 32, thr2, E.inv_w,
-                                                E.n_bins, b0, trash_off, args.err);
+                        if (E.thr_exact)
+                            pos_offsets<kBinStride, true>(off, rp, colgeo + ch * 32, thr2,
+                                                          E.inv_w, E.w, E.n_bins, b0, trash_off,
+                                                          args.err);
+                        else
+                            pos_offsets<kBinStride, false>(off, rp, colgeo + ch * 32, thr2,
+                                                           E.inv_w, E.w, E.n_bins, b0,
+                                                           trash_off, args.err);
                         tmem_wait32(g);
                         if (row_ok) {
 #pragma unroll
@@ -1338,7 +1390,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     }
                 }
             }
-            if (ph) {
+            // the phase product is read out once per pass; with one pass per tile P sums
+            // the tile's K chunks and is read out after the last
+            if (ph && (E.npass > 1 || last)) {
                 // Phase product of each pass: P[r][o] = sum_c G_rc W_co, u = P[.][0:64)
                 // (cosine column weights), v = P[.][64:128) (sine).  Row r adds
                 // cos(q.r_i) u + sin(q.r_i) v (cosine part) and sin(q.r_i) u - cos(q.r_i) v
@@ -1413,9 +1467,6 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     if (lane == 0) mbar_arrive(pempty);
                 }
                 if (!ok) break;
-                // the phase product has consumed G: the accumulator buffer is free
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
             }
         }
         epi_sync(kEpiThreads);

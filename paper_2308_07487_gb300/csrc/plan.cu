@@ -114,6 +114,8 @@ static EpiParams epi_of(const asd_corr_plan *p)
     e.Lz = p->d.L[2];
     e.periodic = p->d.periodic;
     e.inv_w = p->n_bins > 0 ? (float)(1.0 / p->d.bin_width) : 1.0f;
+    e.w = (float)p->d.bin_width;
+    e.thr_exact = p->thr_exact;
     e.n_bins = p->n_bins;
     e.NW = p->NW;
     e.use_window = p->use_window;
@@ -597,6 +599,14 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
             float f = (float)v;
             if ((double)f < v) f = nextafterf(f, INFINITY);
             thr[k] = f;
+        }
+        // the kernels may compute the thresholds when each equals the FP32 square of the
+        // FP32 product k w (same operations, same rounding, on both sides)
+        p->thr_exact = nb > 0 && (double)(float)d->bin_width == d->bin_width;
+        for (int k = 0; k < nb + 2 && p->thr_exact; ++k) {
+            volatile float kw = (float)k * (float)d->bin_width;
+            volatile float sq = kw * kw;
+            p->thr_exact = sq == thr[k];
         }
         if (cudaMalloc(&p->thr, sizeof(float) * (nb + 2)) != cudaSuccess) {
             cudaGetLastError();
