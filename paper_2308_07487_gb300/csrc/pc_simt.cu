@@ -32,7 +32,8 @@ struct SimtParams {
     int *err;         // device error word (index checks of a checked build)
 };
 
-__global__ void __launch_bounds__(256) simt_kernel(SimtParams P)
+// (two CTAs per SM: at most 128 registers a thread)
+__global__ void __launch_bounds__(256, 2) simt_kernel(SimtParams P)
 {
     __shared__ __align__(16) float As[2][TK][TM];
     __shared__ __align__(16) float Bs[2][TK][TN];
