@@ -125,6 +125,12 @@ typedef struct asd_corr_desc {
                                (one per tile, K-chunk and bin or q; one per pair for bins
                                outside a tile's private window) adds at most half a unit.
                                Tensor-core and FP32 forms; not the separable route.      */
+    int32_t cta_pair;       /* 0: one CTA per tile (128 rows); 1: tensor forms only, CTA
+                               pairs (clusters of two CTAs on two SMs, tcgen05
+                               cta_group::2): 256-row tiles, each CTA loading its 128 A
+                               rows and half of the B columns, which halves the B-operand
+                               traffic per SM; tile_n 192 or 256; static schedule; not
+                               for batched launches                                       */
 } asd_corr_desc;
 
 typedef struct asd_corr_plan asd_corr_plan;

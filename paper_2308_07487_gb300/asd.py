@@ -48,7 +48,7 @@ class asd_corr_desc(ctypes.Structure):
                 ("raster_m", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("k_chunks", ctypes.c_int32), ("epi_warps", ctypes.c_int32),
                 ("phase_sine", ctypes.c_int32), ("static_schedule", ctypes.c_int32),
-                ("deterministic", ctypes.c_int32)]
+                ("deterministic", ctypes.c_int32), ("cta_pair", ctypes.c_int32)]
 
 
 class asd_system(ctypes.Structure):
@@ -159,7 +159,7 @@ class CorrPlan:
     def __init__(self, N, F, T0, n_t, precision="split_bf16", S=1, center=False, coords=None,
                  L=(1, 1, 1), periodic=False, pos=None, bin_width=1.0, n_bins=0, q=None,
                  tile_n=0, raster_m=0, stages=0, k_chunks=0, epi_warps=0,
-                 phase_sine=False, static_schedule=False, deterministic=False):
+                 phase_sine=False, static_schedule=False, deterministic=False, cta_pair=False):
         d = asd_corr_desc()
         d.n_sites, d.n_frames, d.n_samples, d.T0, d.n_t = N, F, S, T0, n_t
         d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -193,6 +193,7 @@ class CorrPlan:
         d.phase_sine = int(bool(phase_sine))
         d.static_schedule = int(bool(static_schedule))
         d.deterministic = int(bool(deterministic))
+        d.cta_pair = int(bool(cta_pair))
         self.q_parts = 1 + d.phase_sine  # Sq_sum is [n_t][n_q] or [n_t][n_q][2]
         self.desc = d
         self.N, self.F, self.S, self.T0, self.n_t = N, F, S, T0, n_t

@@ -62,7 +62,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, check_bounds: bool =
     if force:
         for o in glob.glob(os.path.join(obj_dir, "*.o")):
             os.remove(o)
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 8))) as ex:
         res = list(ex.map(lambda s: _compile(s, verbose_ptxas, check_bounds), srcs))
     objs = [o for o, _ in res]
     if verbose_ptxas:

@@ -189,7 +189,7 @@ struct TcLaunchArgs {
 };
 
 template <int FORM>
-int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int ew, int sm_count,
+int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int ew, int cg, int sm_count,
                    cudaStream_t s);
 
 }  // namespace asd
@@ -248,6 +248,7 @@ struct asd_corr_plan {
     int stages;
     size_t smem_bytes;
     int EW;                    // epilogue warps (4 or 8)
+    int CG;                    // CTAs per tile: 1, or 2 for CTA pairs (256-row tiles)
     int k_chunks;
     // deterministic mode: fixed-point sums, the operand bound and the scale (device)
     long long *C_fix, *Sq_fix;
@@ -270,7 +271,7 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
 int tc_configure(asd_corr_plan *p);    // stages / smem for the plan's form
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
               int BN, int swizzle_bytes, int stages, size_t smem, uint32_t var_bytes,
-              int max_nb, int max_nq, int ew, int det, int sm_count,
+              int max_nb, int max_nq, int ew, int det, int cg, int sm_count,
               unsigned long long *counter, cudaStream_t s);
 // work items of one problem: one per (displacement, row tile, column tile); the K chunks
 // of an item run as consecutive sub-items on one CTA

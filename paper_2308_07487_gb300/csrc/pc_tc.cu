@@ -6,11 +6,11 @@
 namespace asd {
 
 // instantiated in the per-form translation units
-extern template int tc_launch_form<ASD_BF16>(const TcLaunchArgs &, size_t, int, int, int,
+extern template int tc_launch_form<ASD_BF16>(const TcLaunchArgs &, size_t, int, int, int, int,
                                              cudaStream_t);
-extern template int tc_launch_form<ASD_TF32>(const TcLaunchArgs &, size_t, int, int, int,
+extern template int tc_launch_form<ASD_TF32>(const TcLaunchArgs &, size_t, int, int, int, int,
                                              cudaStream_t);
-extern template int tc_launch_form<ASD_SPLIT_BF16>(const TcLaunchArgs &, size_t, int, int, int,
+extern template int tc_launch_form<ASD_SPLIT_BF16>(const TcLaunchArgs &, size_t, int, int, int, int,
                                                    cudaStream_t);
 
 uint32_t tc_var_bytes(int NW, int n_bins, int n_lut, int ew) { return var_bytes(NW, n_bins, n_lut, ew); }
@@ -50,7 +50,8 @@ static int configure_once(asd_corr_plan *p, size_t cap, size_t stage_bytes)
 int tc_configure(asd_corr_plan *p)
 {
     const size_t cap = 232448 - 1024 /*alignment slack*/ - 1024 /*barriers*/;
-    const size_t stage_bytes = (size_t)p->n_planes * (kBM + p->BN) * p->swizzle_bytes;
+    // (a CTA pair's stage holds this CTA's half of the B columns)
+    const size_t stage_bytes = (size_t)p->n_planes * (kBM + p->BN / p->CG) * p->swizzle_bytes;
     int st = configure_once(p, cap, stage_bytes);
     // a d2 -> bin table that costs the third pipeline stage (or the whole bin set) is
     // dropped: the threshold rule bins the same pairs with a few more instructions, and
@@ -83,7 +84,7 @@ int tc_configure(asd_corr_plan *p)
 
 int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOverride ov, int prec,
               int BN, int swizzle_bytes, int stages, size_t smem, uint32_t var_bytes_,
-              int max_nb, int max_nq, int ew, int det, int sm_count,
+              int max_nb, int max_nq, int ew, int det, int cg, int sm_count,
               unsigned long long *counter, cudaStream_t s)
 {
     if (total_tiles <= 0) return ASD_OK;
@@ -104,9 +105,10 @@ int launch_tc(const TcProblem *d_probs, int n_probs, int64_t total_tiles, TcOver
     if (!a.err) return ASD_ECUDA;
     (void)swizzle_bytes;
     switch (prec) {
-    case ASD_BF16: return tc_launch_form<ASD_BF16>(a, smem, BN, ew, sm_count, s);
-    case ASD_TF32: return tc_launch_form<ASD_TF32>(a, smem, BN, ew, sm_count, s);
-    case ASD_SPLIT_BF16: return tc_launch_form<ASD_SPLIT_BF16>(a, smem, BN, ew, sm_count, s);
+    case ASD_BF16: return tc_launch_form<ASD_BF16>(a, smem, BN, ew, cg, sm_count, s);
+    case ASD_TF32: return tc_launch_form<ASD_TF32>(a, smem, BN, ew, cg, sm_count, s);
+    case ASD_SPLIT_BF16: return tc_launch_form<ASD_SPLIT_BF16>(a, smem, BN, ew, cg, sm_count,
+                                                                   s);
     default: return ASD_EINVAL;
     }
 }

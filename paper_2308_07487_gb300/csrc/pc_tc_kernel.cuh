@@ -105,7 +105,10 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
 }
 
 // Bounded wait for the phase with the given parity; false after kTimeoutNs (the error
-// word then holds `code`).
+// word then holds `code`).  (A CTA pair's waits on barriers the other CTA signals use the
+// same test: the tcgen05 fences around the arrive and the wait order the tensor-memory
+// accesses, and TMA and MMA completions are counted by the barrier itself; a cluster-scope
+// acquire in every wait measured 30 % slower.)
 __device__ __noinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, int *err, int code,
                                           unsigned long long limit_ns)
 {
@@ -125,6 +128,47 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *er
     return mbar_wait_for(bar, parity, err, code, kTimeoutNs);
 }
 
+// ---- CTA pairs (tcgen05 cta_group::2): two CTAs of a cluster share one 256-row MMA ----
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Shared-memory address of the same variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Arrive on a barrier of any CTA of the cluster (release at cluster scope).
+__device__ __forceinline__ void mbar_arrive_cl(uint32_t cl_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_addr)
+                 : "memory");
+}
+
+// TMA tile load into this CTA's shared memory whose completion is counted on a barrier
+// of the pair's first CTA (cl_bar: a cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap *map,
+                                                 uint32_t cl_bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile"
+        ".mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(cl_bar), "r"(x), "r"(y)
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
                                             int x, int y)
 {
@@ -135,55 +179,106 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// TMEM allocation by one warp; with CG = 2 one warp of each CTA of the pair performs it
+// together (the same columns in both CTAs).
+template <int CG>
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_slot, uint32_t ncols)
 {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_slot),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (CG == 2) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         dst_slot),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         dst_slot),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
 }
 
+template <int CG>
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-                 : "memory");
+    if constexpr (CG == 2)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                     "r"(ncols)
+                     : "memory");
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                     "r"(ncols)
+                     : "memory");
 }
 
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Arrive on `bar` (a cluster address with CG = 2: this CTA's or the peer's) once the
+// MMAs this thread issued so far have completed.
+template <int CG = 1>
 __device__ __forceinline__ void tc_commit(uint32_t bar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
+    if constexpr (CG == 2)
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+            : "memory");
+    else
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+            : "memory");
 }
 
-template <bool TF32>
+// D (TMEM) = / += A B^T with A and B in shared memory.  CG = 2: a 256-row MMA over the
+// pair, A rows 0-127 and B columns 0-N/2 from this CTA, the rest from the peer at the
+// same addresses, D rows split between the two CTAs' TMEM.
+template <bool TF32, int CG = 1>
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                        uint32_t acc)
 {
-    if (TF32)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-    else
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    if constexpr (CG == 2) {
+        if (TF32)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        else
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        if (TF32)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        else
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
 }
 
 // MMA with the A operand in tensor memory (128 lanes = rows, K along the columns, two
 // BF16 elements per 32-bit column, the even element in the low half) and B in shared
 // memory: the phase product P = G W of the epilogue.
+template <int CG = 1>
 __device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
                                           uint32_t acc)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+    if constexpr (CG == 2)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
 }
 
 // 32 lanes x 16 consecutive 32-bit columns (this thread's lane), and its wait, tied to the
@@ -313,11 +408,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, int swb)
     return d;
 }
 
-// Instruction descriptor: FP32 accumulate, A/B = BF16 (1) or TF32 (2), both K-major.
-__host__ __device__ constexpr uint32_t idesc(bool tf32, int N)
+// Instruction descriptor: FP32 accumulate, A/B = BF16 (1) or TF32 (2), both K-major,
+// N columns, M rows (128, or 256 for a CTA pair).
+__host__ __device__ constexpr uint32_t idesc(bool tf32, int N, int M = kBM)
 {
     return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) |
-           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // ------------------------------------------------------------------------------------
@@ -390,10 +486,11 @@ struct WorkCursor {
 
 // A work item is one (problem, displacement, row tile, column tile); its K chunks are
 // consecutive sub-items on the same CTA (they share the tile's geometry and private
-// bins).  decode(tau, c) gives chunk c of work item tau.
+// bins).  decode(tau, c) gives chunk c of work item tau.  Row tiles are row_step rows
+// (256 for a CTA pair, whose second CTA takes rows row_off = 128 on).
 __device__ __forceinline__ TileInfo decode(WorkCursor &cu, const TcProblem *__restrict__ probs,
                                            int n_probs, const TcOverride &ov, int64_t tau,
-                                           int c, int BN)
+                                           int c, int BN, int row_step = kBM, int row_off = 0)
 {
     if (cu.p < 0 || tau >= cu.end) {
         int p = cu.p < 0 ? 0 : cu.p;
@@ -435,7 +532,7 @@ __device__ __forceinline__ TileInfo decode(WorkCursor &cu, const TcProblem *__re
     const int first_m = (int)(rem / gspan) * cu.G;
     const int gsz = min(cu.G, cu.tiles_m - first_m);
     const int64_t r2 = rem % gspan;
-    ti.m0 = cu.row_begin + (first_m + (int)(r2 % gsz)) * kBM;
+    ti.m0 = cu.row_begin + (first_m + (int)(r2 % gsz)) * row_step + row_off;
     ti.n0 = (int)(r2 / gsz) * BN;
     ti.row_end = cu.row_end;
     ti.kg0 = (int)((int64_t)kc * cu.nk / cu.kch);
@@ -631,7 +728,14 @@ __device__ __forceinline__ int phase_slot(int g, int nk, int G)
 // ------------------------------------------------------------------------------------
 // the kernel
 // ------------------------------------------------------------------------------------
-template <int FORM, int BN, int SWB, int EW>
+// CG = 2: CTA pairs (clusters of two).  The pair computes a 256-row tile with one MMA
+// thread (in the first CTA) issuing tcgen05 cta_group::2 MMAs: each CTA loads its own
+// 128 A rows and half of the B columns, so per SM the operand traffic of a 256 x BN
+// tile is that of a 128 x (128 + BN/2) one; each CTA's TMEM holds its 128 rows and its
+// epilogue bins them.  Both CTAs walk the same fixed order of work items; the second
+// CTA's epilogue warps release accumulators and phase products on the first CTA's
+// barriers.
+template <int FORM, int BN, int SWB, int EW, int CG>
 __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_constant__ LaunchArgs args)
 {
     constexpr int kEpiWarps = EW;
@@ -641,11 +745,11 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     constexpr bool kTF32 = FORM == ASD_TF32;
     constexpr int kPlanes = FORM == ASD_SPLIT_BF16 ? 2 : 1;
     constexpr uint32_t kABytes = kBM * SWB;
-    constexpr uint32_t kBBytes = BN * SWB;
+    constexpr uint32_t kBBytes = (BN / CG) * SWB;   // this CTA's B columns
     constexpr uint32_t kStageBytes = kPlanes * (kABytes + kBBytes);
     constexpr int kKSteps = SWB / 32;          // one MMA k-step covers 32 bytes of K
     constexpr int kBK = SWB / (kTF32 ? 4 : 2); // K elements per stage
-    constexpr uint32_t kIdesc = idesc(kTF32, BN);
+    constexpr uint32_t kIdesc = idesc(kTF32, BN, kBM * CG);
     // Phase weights on the tensor core (problems with n_q > 0; the plan picks BN <= 192 and
     // 4 epilogue warps): after the epilogue has binned a tile it stores the tile's G, split
     // into BF16 hi + lo, back over the accumulator's own columns (chunk of 32 columns ->
@@ -656,9 +760,11 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     constexpr bool kPhaseOK = 2 * BN + kPCols <= (int)kTmemAlloc;
     constexpr int kWPlanes = FORM == ASD_BF16 ? 1 : 2;
     constexpr int kWStages = BN / 64;          // W stages per pass (64 columns c each)
-    constexpr uint32_t kIdescP = idesc(false, kPCols);
-    static_assert(!kPhaseOK || (kStageBytes >= kWPlanes * kWBytes && BN % 64 == 0),
+    constexpr uint32_t kWB = kWBytes / CG;     // one W plane of this CTA (its output half)
+    constexpr uint32_t kIdescP = idesc(false, kPCols, kBM * CG);
+    static_assert(!kPhaseOK || (kStageBytes >= kWPlanes * kWB && BN % 64 == 0),
                   "a W stage fits a ring stage");
+    static_assert(CG == 1 || CG == 2, "CTA groups of one or two");
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned base for the swizzled tiles
@@ -688,36 +794,48 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     const uint32_t drain = saddr(bars + 2 * stages + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // CTA pair: rank in the pair; the first CTA (rank 0) issues the MMAs.  lead(a) is the
+    // cluster address of barrier a in the first CTA, peer(a) in the other one.
+    const uint32_t rank = CG == 2 ? cluster_rank() : 0u;
+    const bool leader = rank == 0;
+    auto lead = [&](uint32_t a) { return CG == 2 ? mapa(a, 0) : a; };
+    auto peer = [&](uint32_t a) { return CG == 2 ? mapa(a, 1) : a; };
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(full0 + 8 * s, 1);
             // a stage is free again once the MMAs that read it have completed
             mbar_init(empty0 + 8 * s, 1);
         }
+        // (a pair's epilogue barriers count the warps of both CTAs)
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
-            mbar_init(tempty0 + 8 * a, kEpiWarps);
+            mbar_init(tempty0 + 8 * a, kEpiWarps * CG);
         }
         mbar_init(drain, 1);
         for (int k = 0; k < kWQ; ++k) {
             mbar_init(wqfull0 + 8 * k, 1);
-            // released by the MMA thread and one lane of every epilogue warp
-            mbar_init(wqempty0 + 8 * k, 1 + kEpiWarps);
+            // released by the MMA thread (the first CTA of a pair only) and one lane of
+            // every epilogue warp
+            mbar_init(wqempty0 + 8 * k, (leader ? 1 : 0) + kEpiWarps);
         }
-        mbar_init(conv, kEpiWarps);
+        mbar_init(conv, kEpiWarps * CG);
         mbar_init(pfull, 1);
-        mbar_init(pempty, kEpiWarps);
+        mbar_init(pempty, kEpiWarps * CG);
         mbar_init(tmm0, 1);
         mbar_init(tmm0 + 8, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(saddr(tmem_slot), kTmemAlloc);
+    if (warp == 1) tmem_alloc<CG>(saddr(tmem_slot), kTmemAlloc);
     tc_before();
     __syncthreads();
+    // a pair's barriers are initialised in both CTAs before either signals the other
+    if constexpr (CG == 2) cluster_sync();
     tc_after();
     const uint32_t tmem = *tmem_slot;
     const TcProblem *__restrict__ probs = args.probs;
-    const int64_t cid = blockIdx.x, n_ctas = gridDim.x;
+    // work units: CTAs, or pairs
+    const int64_t cid = blockIdx.x / CG, n_ctas = gridDim.x / CG;
+    const int row_step = kBM * CG, row_off = kBM * (int)rank;
 
     if (warp == 0) {
         // ======================= TMA producer =======================
@@ -731,6 +849,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             // phase_slot(g)), so the phase product of item v - 1 runs while item v's MMAs
             // run
             int pend_p = -1, pend_n0 = 0, pend_G = 0;
+            int64_t n_claimed = 0;  // work items claimed (static schedule)
             auto next_stage = [&]() {
                 if (++stage == stages) {
                     stage = 0;
@@ -738,84 +857,109 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 }
             };
             // W stage j of pass pp (sub-pass g = pp kWStages + j)
+            // (a pair: each CTA loads its half of the outputs; the first CTA's full barrier
+            // counts the bytes of both)
             auto load_sub = [&](int g) {
                 const TcProblem &Q = probs[pend_p];
                 const int pp = g / kWStages, j = g % kWStages;
                 if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, args.err, DEV_TIMEOUT_TMA))
                     return false;
                 const uint32_t fb = full0 + 8 * stage;
-                mbar_expect_tx(fb, kWPlanes * kWBytes);
+                if (leader) mbar_expect_tx(fb, CG * kWPlanes * kWB);
                 uint8_t *st = tiles + (size_t)stage * kStageBytes;
 #pragma unroll
-                for (int pl = 0; pl < kWPlanes; ++pl)
-                    tma_load_2d(saddr(st + pl * kWBytes), &Q.mapW[pl], fb, pend_n0 + 64 * j,
-                                pp * kPCols);
+                for (int pl = 0; pl < kWPlanes; ++pl) {
+                    const int y = pp * kPCols + (int)rank * (kPCols / CG);
+                    if constexpr (CG == 2)
+                        tma_load_2d_pair(saddr(st + pl * kWB), &Q.mapW[pl], lead(fb),
+                                         pend_n0 + 64 * j, y);
+                    else
+                        tma_load_2d(saddr(st + pl * kWB), &Q.mapW[pl], fb, pend_n0 + 64 * j, y);
+                }
                 next_stage();
                 return true;
             };
-            int64_t v = 0;  // sub-items published
-            for (int64_t vt = 0; ok; ++vt) {
-                // claim the next work item; its K chunks are published one by one
-                int64_t tau = args.counter ? (int64_t)atomicAdd(args.counter, 1ull)
-                                           : cid + vt * n_ctas;
-                if (tau >= args.total_tiles) tau = -1;
-                const int kch = tau < 0 ? 1 : probs[decode(cu, probs, args.n_probs, args.ov,
-                                                           tau, 0, BN).p].k_chunks;
-                for (int kci = 0; kci < kch && ok; ++kci, ++v) {
-                    // publish the sub-item (tau 256 + chunk; -1: none left) once its ring slot
-                    // is free
-                    const int qs = (int)(v % kWQ);
-                    if (!mbar_wait(wqempty0 + 8 * qs, (uint32_t)((v / kWQ) & 1) ^ 1u, args.err,
-                                   DEV_TIMEOUT_TMA)) {
+            // Sub-items (a work item's K chunks) in this CTA's work ring.  A lone CTA claims
+            // work items from the counter (dynamic schedule) or in a fixed order; both CTAs
+            // of a pair walk the same fixed order (measured against handing each item from
+            // the first CTA to the second: 542 against 506 TFLOP/s on the 26^3 lattice).
+            int64_t tau = 0;
+            int kci = 0, kch = 0;
+            for (int64_t v = 0; ok; ++v) {
+                const int qs = (int)(v % kWQ);
+                // the next chunk of the current item, or the first of a new one
+                if (++kci >= kch) {
+                    tau = args.counter && CG == 1 ? (int64_t)atomicAdd(args.counter, 1ull)
+                                                  : cid + n_claimed * n_ctas;
+                    ++n_claimed;
+                    if (tau >= args.total_tiles) tau = -1;
+                    kci = 0;
+                    kch = tau < 0 ? 1
+                                  : probs[decode(cu, probs, args.n_probs, args.ov, tau, 0, BN,
+                                                 row_step, row_off).p].k_chunks;
+                }
+                // publish the sub-item (tau 256 + chunk; -1: none left) once its ring slot
+                // is free
+                if (!mbar_wait(wqempty0 + 8 * qs, (uint32_t)((v / kWQ) & 1) ^ 1u, args.err,
+                               DEV_TIMEOUT_TMA)) {
+                    ok = false;
+                    break;
+                }
+                wq[qs] = tau < 0 ? -1 : tau * 256 + kci;
+                mbar_arrive(wqfull0 + 8 * qs);  // release: the slot is visible to the waiters
+                if (tau < 0) break;
+                const TileInfo ti =
+                    decode(cu, probs, args.n_probs, args.ov, tau, kci, BN, row_step, row_off);
+                const TcProblem &P = probs[ti.p];
+                const int nk = ti.kg1 - ti.kg0;
+                int g = 0;
+                for (int kg = ti.kg0; kg < ti.kg1 && ok; ++kg) {
+                    if constexpr (kPhaseOK) {
+                        while (pend_p >= 0 && g < pend_G &&
+                               kg - ti.kg0 == phase_slot(g, nk, pend_G)) {
+                            if (!load_sub(g++)) {
+                                ok = false;
+                                break;
+                            }
+                        }
+                        if (!ok) break;
+                    }
+                    const int s = kg / P.nkb, kb = kg % P.nkb;
+                    const int xw = s * P.F3 + 3 * ti.t;
+                    const int c = xw % P.n_copies;
+
+                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, args.err, DEV_TIMEOUT_TMA)) {
                         ok = false;
                         break;
                     }
-                    wq[qs] = tau < 0 ? -1 : tau * 256 + kci;
-                    mbar_arrive(wqfull0 + 8 * qs);  // release: the slot is visible to the waiters
-                    if (tau < 0) break;
-                    const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau, kci, BN);
-                    const TcProblem &P = probs[ti.p];
-                    const int nk = ti.kg1 - ti.kg0;
-                    int g = 0;
-                    for (int kg = ti.kg0; kg < ti.kg1 && ok; ++kg) {
-                        if constexpr (kPhaseOK) {
-                            while (pend_p >= 0 && g < pend_G &&
-                                   kg - ti.kg0 == phase_slot(g, nk, pend_G)) {
-                                if (!load_sub(g++)) {
-                                    ok = false;
-                                    break;
-                                }
-                            }
-                            if (!ok) break;
-                        }
-                        const int s = kg / P.nkb, kb = kg % P.nkb;
-                        const int xw = s * P.F3 + 3 * ti.t;
-                        const int c = xw % P.n_copies;
-
-                        if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, args.err, DEV_TIMEOUT_TMA)) {
-                            ok = false;
-                            break;
-                        }
-                        const uint32_t fb = full0 + 8 * stage;
-                        mbar_expect_tx(fb, kStageBytes);
-                        uint8_t *st = tiles + (size_t)stage * kStageBytes;
+                    const uint32_t fb = full0 + 8 * stage;
+                    if (leader) mbar_expect_tx(fb, CG * kStageBytes);
+                    uint8_t *st = tiles + (size_t)stage * kStageBytes;
+                    // this CTA's B columns (a pair splits the tile's columns)
+                    const int nb0 = ti.n0 + (int)rank * (BN / CG);
 #pragma unroll
-                        for (int pl = 0; pl < kPlanes; ++pl) {
+                    for (int pl = 0; pl < kPlanes; ++pl) {
+                        if constexpr (CG == 2) {
+                            tma_load_2d_pair(saddr(st + pl * kABytes), &P.mapA[pl][c],
+                                             lead(fb), xw - c + kb * kBK, ti.m0);
+                            tma_load_2d_pair(saddr(st + kPlanes * kABytes + pl * kBBytes),
+                                             &P.mapB[pl], lead(fb), s * P.Kseg + kb * kBK,
+                                             nb0);
+                        } else {
                             tma_load_2d(saddr(st + pl * kABytes), &P.mapA[pl][c], fb,
                                         xw - c + kb * kBK, ti.m0);
                             tma_load_2d(saddr(st + kPlanes * kABytes + pl * kBBytes),
-                                        &P.mapB[pl], fb, s * P.Kseg + kb * kBK, ti.n0);
+                                        &P.mapB[pl], fb, s * P.Kseg + kb * kBK, nb0);
                         }
-                        next_stage();
                     }
-                    pend_p = -1;
-                    if (kPhaseOK && P.epi.n_q > 0) {
-                        pend_p = ti.p;
-                        pend_n0 = ti.n0;
-                        pend_G = P.epi.npass * kWStages;
-                    }
+                    next_stage();
                 }
-                if (tau < 0) break;
+                pend_p = -1;
+                if (kPhaseOK && P.epi.n_q > 0) {
+                    pend_p = ti.p;
+                    pend_n0 = ti.n0;
+                    pend_G = P.epi.npass * kWStages;
+                }
             }
             // the last item's phase sub-passes
             if (kPhaseOK && ok && pend_p >= 0)
@@ -827,13 +971,24 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     phase ^= 1;
                 }
                 // the most recent fill of `stage` used parity `phase`; if that stage was never
-                // filled, its barrier is still in phase 0 and parity 1 reads as complete
-                mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_TMA);
+                // filled, its barrier is still in phase 0 and parity 1 reads as complete (a
+                // pair's fills all complete on the first CTA's barriers: it waits for both)
+                if (leader) mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_TMA);
             }
         }
     } else if (warp == 1) {
         // ======================= MMA issuer =======================
-        if (lane == 0) {
+        // (a pair's MMAs are issued by the first CTA; its commits release the stages and
+        // hand the accumulators to the epilogues of both CTAs)
+        auto commit_both = [&](uint32_t a) {
+            if constexpr (CG == 2) {
+                tc_commit<2>(a);
+                tc_commit<2>(peer(a));
+            } else {
+                tc_commit(a);
+            }
+        };
+        if (lane == 0 && leader) {
             int stage = 0;
             uint32_t phase = 0;
             uint32_t v = 0;
@@ -859,11 +1014,13 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             auto issue_sub = [&](int g) {
                 const int pp = g / kWStages, j = g % kWStages;
                 const uint32_t g0 = tmem + (uint32_t)pend_acc * BN;
-                if (!mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_MMA)) return false;
+                if (!mbar_wait(full0 + 8 * stage, phase, args.err, DEV_TIMEOUT_MMA))
+                    return false;
                 if (j == 0) {
                     // G stored as BF16 by the epilogue (once per chunk); a pass that starts
                     // P afresh waits until the previous P has been read out
-                    if (pp == 0 && !mbar_wait(conv, n_conv++ & 1, args.err, DEV_TIMEOUT_MMA))
+                    if (pp == 0 &&
+                        !mbar_wait(conv, n_conv++ & 1, args.err, DEV_TIMEOUT_MMA))
                         return false;
                     if (!pend_add) {
                         if (!mbar_wait(pempty, (n_own & 1) ^ 1, args.err, DEV_TIMEOUT_MMA))
@@ -874,7 +1031,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 tc_after();
                 uint8_t *st = tiles + (size_t)stage * kStageBytes;
                 const uint64_t w0 = sdesc(saddr(st), 128);
-                const uint64_t w1 = sdesc(saddr(st + kWBytes), 128);
+                const uint64_t w1 = sdesc(saddr(st + kWB), 128);
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
                     // columns c = 64 j + 16 ks: chunk c / 32 holds hi in its first 16 TMEM
@@ -883,20 +1040,20 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     const uint32_t ahi = g0 + 32 * (c >> 5) + 8 * ((c >> 4) & 1);
                     const uint64_t off = (uint64_t)(ks * 32) >> 4;
                     const uint32_t accum = pend_add || (j | ks) != 0;
-                    tc_mma_ts(ptm, ahi, w0 + off, kIdescP, accum);           // hi*hi
+                    tc_mma_ts<CG>(ptm, ahi, w0 + off, kIdescP, accum);           // hi*hi
                     if (kWPlanes == 2) {
-                        tc_mma_ts(ptm, ahi, w1 + off, kIdescP, 1u);          // hi*lo
-                        tc_mma_ts(ptm, ahi + 16, w0 + off, kIdescP, 1u);     // lo*hi
+                        tc_mma_ts<CG>(ptm, ahi, w1 + off, kIdescP, 1u);          // hi*lo
+                        tc_mma_ts<CG>(ptm, ahi + 16, w0 + off, kIdescP, 1u);     // lo*hi
                     }
                 }
-                tc_commit(empty0 + 8 * stage);
+                commit_both(empty0 + 8 * stage);
                 if (++stage == stages) {
                     stage = 0;
                     phase ^= 1;
                 }
-                if (j == kWStages - 1 && pend_done) tc_commit(pfull);
+                if (j == kWStages - 1 && pend_done) commit_both(pfull);
                 // the chunk's accumulator is free once its phase product has completed
-                if (g == pend_G - 1) tc_commit(tmm0 + 8 * pend_acc);
+                if (g == pend_G - 1) tc_commit<CG>(tmm0 + 8 * pend_acc);
                 return true;
             };
             for (;; ++v) {
@@ -909,18 +1066,19 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 mbar_arrive(wqempty0 + 8 * qs);
                 if (tau < 0) break;
                 const int kci = (int)(tau & 255);
-                const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau >> 8, kci, BN);
+                const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau >> 8, kci, BN,
+                                           row_step, row_off);
                 const TcProblem &P = probs[ti.p];
                 const bool phs = kPhaseOK && P.epi.n_q > 0;
                 const uint32_t acc = v & 1;
                 // wait until the accumulator's previous chunk has released it
-                if (rel[acc] == 1 &&
-                    !mbar_wait(tempty0 + 8 * acc, n_te[acc]++ & 1, args.err, DEV_TIMEOUT_MMA)) {
+                if (rel[acc] == 1 && !mbar_wait(tempty0 + 8 * acc, n_te[acc]++ & 1, args.err,
+                                                DEV_TIMEOUT_MMA)) {
                     ok = false;
                     break;
                 }
-                if (rel[acc] == 2 &&
-                    !mbar_wait(tmm0 + 8 * acc, n_tm[acc]++ & 1, args.err, DEV_TIMEOUT_MMA)) {
+                if (rel[acc] == 2 && !mbar_wait(tmm0 + 8 * acc, n_tm[acc]++ & 1, args.err,
+                                                DEV_TIMEOUT_MMA)) {
                     ok = false;
                     break;
                 }
@@ -953,23 +1111,23 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         const uint64_t off = (uint64_t)(ks * 32) >> 4;
                         const uint32_t first = (kb | ks) != 0;
                         if (kPlanes == 1) {
-                            tc_mma<kTF32>(d, a0 + off, b0 + off, kIdesc, first);
+                            tc_mma<kTF32, CG>(d, a0 + off, b0 + off, kIdesc, first);
                         } else {
                             const uint64_t a1 = sdesc(saddr(st + kABytes), SWB);
                             const uint64_t b1 = sdesc(saddr(st + 2 * kABytes + kBBytes), SWB);
-                            tc_mma<false>(d, a0 + off, b0 + off, kIdesc, first);  // hi*hi
-                            tc_mma<false>(d, a0 + off, b1 + off, kIdesc, 1u);     // hi*lo
-                            tc_mma<false>(d, a1 + off, b0 + off, kIdesc, 1u);     // lo*hi
+                            tc_mma<false, CG>(d, a0 + off, b0 + off, kIdesc, first);  // hi*hi
+                            tc_mma<false, CG>(d, a0 + off, b1 + off, kIdesc, 1u);     // hi*lo
+                            tc_mma<false, CG>(d, a1 + off, b0 + off, kIdesc, 1u);     // lo*hi
                         }
                     }
-                    tc_commit(empty0 + 8 * stage);
+                    commit_both(empty0 + 8 * stage);
                     if (++stage == stages) {
                         stage = 0;
                         phase ^= 1;
                     }
                 }
                 if (!ok) break;
-                tc_commit(tfull0 + 8 * acc);
+                commit_both(tfull0 + 8 * acc);
                 pend_acc = -1;
                 if (phs) {
                     // one pass: P sums the tile's chunks and is read out after the last
@@ -984,7 +1142,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             if (kPhaseOK && ok && pend_acc >= 0)
                 for (int g = 0; g < pend_G && ok; ++g) ok = issue_sub(g);
             // drain every MMA this thread issued before TMEM is released
-            tc_commit(drain);
+            tc_commit<CG>(drain);
             mbar_wait(drain, 0, args.err, DEV_TIMEOUT_MMA);
         }
     } else {
@@ -1092,7 +1250,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             if (lane == 0) mbar_arrive(wqempty0 + 8 * qs);
             if (tau < 0) break;
             const int kci = (int)(tau & 255);
-            const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau >> 8, kci, BN);
+            const TileInfo ti = decode(cu, probs, args.n_probs, args.ov, tau >> 8, kci, BN,
+                                       row_step, row_off);
             const TcProblem &P = probs[ti.p];
             const EpiParams &E = P.epi;
             // the first K chunk of a tile sets up its geometry and bin window; the chunks
@@ -1337,7 +1496,12 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             if (ph) tmem_wait_st();
             tc_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(ph ? conv : tempty0 + 8 * acc);
+            // (a pair's epilogue warps arrive on the first CTA's barriers)
+            if (lane == 0) {
+                const uint32_t a = ph ? conv : tempty0 + 8 * acc;
+                if constexpr (CG == 2) mbar_arrive_cl(lead(a));
+                else mbar_arrive(a);
+            }
             if (last) epi_sync(kEpiThreads);  // all private bins written
             if (bins_on && last) {
                 // private rows this tile may have written: with the branch-free position
@@ -1464,7 +1628,10 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     // P read: the next pass (or item) may overwrite it
                     tc_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(pempty);
+                    if (lane == 0) {
+                        if constexpr (CG == 2) mbar_arrive_cl(lead(pempty));
+                        else mbar_arrive(pempty);
+                    }
                 }
                 if (!ok) break;
             }
@@ -1474,40 +1641,86 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     }
     __syncwarp();
     __syncthreads();
+    // a pair: neither CTA leaves (or frees TMEM) while the other may still signal it or
+    // the first CTA's MMAs may still write its accumulators
+    if constexpr (CG == 2) cluster_sync();
     if (warp == 1) {
         tc_after();
-        tmem_dealloc(tmem, kTmemAlloc);
+        tmem_dealloc<CG>(tmem, kTmemAlloc);
     }
 }
 
-template <int FORM, int BN, int SWB, int EW>
+template <int FORM, int BN, int SWB, int EW, int CG>
 int launch_one(const LaunchArgs &a, size_t smem, int sm_count, cudaStream_t s)
 {
-    auto k = pc_tc_kernel<FORM, BN, SWB, EW>;
+    auto k = pc_tc_kernel<FORM, BN, SWB, EW, CG>;
     constexpr int kThreads = 64 + 32 * EW;
     ASD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    // persistent: one CTA per SM, no more CTAs than work items
-    const int grid = (int)(a.total_tiles < sm_count ? a.total_tiles : sm_count);
-    k<<<grid, kThreads, smem, s>>>(a);
+    if constexpr (CG == 1) {
+        // persistent: one CTA per SM, no more CTAs than work items
+        const int grid = (int)(a.total_tiles < sm_count ? a.total_tiles : sm_count);
+        k<<<grid, kThreads, smem, s>>>(a);
+    } else {
+        // persistent pairs: clusters of two CTAs, as many as can be resident at once (one
+        // CTA per SM), no more than work items
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)sm_count, 1, 1);
+        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        ASD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, k, &cfg));
+        if (clusters < 1) {
+            set_error_text("no CTA pair fits on the device");
+            return ASD_EUNSUPPORTED;
+        }
+        const int64_t pairs = a.total_tiles < clusters ? a.total_tiles : clusters;
+        cfg.gridDim = dim3((unsigned)(2 * pairs), 1, 1);
+        ASD_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, a));
+    }
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;
 }
 
 }  // namespace
 
-// Launch one precision form.  Instantiated combinations (the rest are rejected):
-//   BN = 256 and BN = 192 with 4 or 8 epilogue warps; BN = 128 with 4 warps (192 and 128
-//   are the tile widths that leave TMEM room for the phase product).
+// Launch one precision form with CTA pairs (tile widths 256 and 192, 4 or 8 epilogue
+// warps); instantiated in its own translation unit per form (pc_tc_*_pair.cu).
 template <int FORM>
-int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int ew, int sm_count,
+int tc_launch_pair(const TcLaunchArgs &a, size_t smem, int BN, int ew, int sm_count,
                    cudaStream_t s)
 {
     constexpr int SWB = FORM == ASD_SPLIT_BF16 ? 64 : 128;
-    if (BN == 256 && ew == 4) return launch_one<FORM, 256, SWB, 4>(a, smem, sm_count, s);
-    if (BN == 256 && ew == 8) return launch_one<FORM, 256, SWB, 8>(a, smem, sm_count, s);
-    if (BN == 192 && ew == 4) return launch_one<FORM, 192, SWB, 4>(a, smem, sm_count, s);
-    if (BN == 192 && ew == 8) return launch_one<FORM, 192, SWB, 8>(a, smem, sm_count, s);
-    if (BN == 128 && ew == 4) return launch_one<FORM, 128, SWB, 4>(a, smem, sm_count, s);
+    if (BN == 256 && ew == 4) return launch_one<FORM, 256, SWB, 4, 2>(a, smem, sm_count, s);
+    if (BN == 256 && ew == 8) return launch_one<FORM, 256, SWB, 8, 2>(a, smem, sm_count, s);
+    if (BN == 192 && ew == 4) return launch_one<FORM, 192, SWB, 4, 2>(a, smem, sm_count, s);
+    if (BN == 192 && ew == 8) return launch_one<FORM, 192, SWB, 8, 2>(a, smem, sm_count, s);
+    set_error_text("tensor-core kernel: CTA pairs need 192- or 256-wide tiles");
+    return ASD_EUNSUPPORTED;
+}
+
+// Launch one precision form.  Instantiated combinations (the rest are rejected):
+//   BN = 256 and BN = 192 with 4 or 8 epilogue warps; BN = 128 with 4 warps (192 and 128
+//   are the tile widths that leave TMEM room for the phase product); cg = 2 goes to the
+//   CTA-pair kernels.
+template <int FORM>
+int tc_launch_form(const TcLaunchArgs &a, size_t smem, int BN, int ew, int cg, int sm_count,
+                   cudaStream_t s)
+{
+    constexpr int SWB = FORM == ASD_SPLIT_BF16 ? 64 : 128;
+    if (cg == 2) return tc_launch_pair<FORM>(a, smem, BN, ew, sm_count, s);
+    if (BN == 256 && ew == 4) return launch_one<FORM, 256, SWB, 4, 1>(a, smem, sm_count, s);
+    if (BN == 256 && ew == 8) return launch_one<FORM, 256, SWB, 8, 1>(a, smem, sm_count, s);
+    if (BN == 192 && ew == 4) return launch_one<FORM, 192, SWB, 4, 1>(a, smem, sm_count, s);
+    if (BN == 192 && ew == 8) return launch_one<FORM, 192, SWB, 8, 1>(a, smem, sm_count, s);
+    if (BN == 128 && ew == 4) return launch_one<FORM, 128, SWB, 4, 1>(a, smem, sm_count, s);
     set_error_text("tensor-core kernel: unsupported (tile width, epilogue warps)");
     return ASD_EUNSUPPORTED;
 }

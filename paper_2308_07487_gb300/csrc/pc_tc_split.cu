@@ -1,6 +1,10 @@
-// Instantiation of the fused tensor-core kernel for the split form (see pc_tc_kernel.cuh).
+// Instantiation of the fused tensor-core kernel for the split-BF16 form, one CTA per tile
+// (see pc_tc_kernel.cuh; the CTA-pair kernels are in pc_tc_split_pair.cu).
 #include "pc_tc_kernel.cuh"
 
 namespace asd {
-template int tc_launch_form<ASD_SPLIT_BF16>(const TcLaunchArgs &, size_t, int, int, int, cudaStream_t);
+extern template int tc_launch_pair<ASD_SPLIT_BF16>(const TcLaunchArgs &, size_t, int, int, int,
+                                                   cudaStream_t);
+template int tc_launch_form<ASD_SPLIT_BF16>(const TcLaunchArgs &, size_t, int, int, int, int,
+                                            cudaStream_t);
 }  // namespace asd

@@ -230,8 +230,9 @@ static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int6
                                (uint64_t)p->N, (uint32_t)p->BK, kBM, p->swizzle_bytes);
             if (rc) return rc;
         }
+        // (a CTA pair loads half of the tile's B columns in each CTA)
         int rc = encode_2d(&tp->mapB[pl], p->B[pl], p->elem_bytes, (uint64_t)p->Kb, (uint64_t)p->N,
-                           (uint32_t)p->BK, (uint32_t)p->BN, p->swizzle_bytes);
+                           (uint32_t)p->BK, (uint32_t)(p->BN / p->CG), p->swizzle_bytes);
         if (rc) return rc;
     }
     // phase column weights: boxes of 64 sites x one pass (128 rows), BF16, 128-byte swizzle
@@ -240,15 +241,15 @@ static int fill_problem(asd_corr_plan *p, TcProblem *tp, int64_t row_begin, int6
         const size_t plane = (size_t)npass * 2 * kPhaseQ * p->Wld * 2;
         for (int pl = 0; pl < 2; ++pl) {
             int rc = encode_2d(&tp->mapW[pl], static_cast<char *>(p->W) + pl * plane, 2,
-                               (uint64_t)p->Wld, (uint64_t)npass * 2 * kPhaseQ, 64, 2 * kPhaseQ,
-                               128);
+                               (uint64_t)p->Wld, (uint64_t)npass * 2 * kPhaseQ, 64,
+                               (uint32_t)(2 * kPhaseQ / p->CG), 128);
             if (rc) return rc;
         }
     }
     tp->N = (int)p->N;
     tp->row_begin = (int)row_begin;
     tp->row_end = (int)row_end;
-    tp->tiles_m = (int)((row_end - row_begin + kBM - 1) / kBM);
+    tp->tiles_m = (int)((row_end - row_begin + kBM * p->CG - 1) / (kBM * p->CG));
     tp->tiles_n = (int)((p->N + p->BN - 1) / p->BN);
     tp->n_t = p->n_t;
     tp->S = p->S;
@@ -426,6 +427,9 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
     ASD_CHECK_ARG(d->static_schedule == 0 || d->static_schedule == 1, "static_schedule: 0 or 1");
     ASD_CHECK_ARG(d->phase_sine == 0 || d->phase_sine == 1, "phase_sine: 0 or 1");
     ASD_CHECK_ARG(d->deterministic == 0 || d->deterministic == 1, "deterministic: 0 or 1");
+    ASD_CHECK_ARG(d->cta_pair == 0 || d->cta_pair == 1, "cta_pair: 0 or 1");
+    ASD_CHECK_ARG(!d->cta_pair || d->precision != ASD_FP32, "cta_pair needs a tensor form");
+    ASD_CHECK_ARG(!d->cta_pair || d->tile_n != 128, "cta_pair needs tile_n 192 or 256");
     if (d->geometry == ASD_GEOM_LATTICE) {
         ASD_CHECK_ARG(d->coords, "coords required for lattice geometry");
         for (int a = 0; a < 3; ++a) ASD_CHECK_ARG(d->L[a] >= 1 && d->L[a] <= 1 << 20, "bad L");
@@ -489,6 +493,9 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         p->swizzle_bytes = d->precision == ASD_SPLIT_BF16 ? 64 : 128;
         p->BK = p->swizzle_bytes / p->elem_bytes;
         p->BN = d->tile_n ? d->tile_n : (p->N <= 4096 ? 128 : (d->n_q > 0 ? 192 : 256));
+        // CTA pairs: 192- or 256-wide tiles only
+        p->CG = d->cta_pair ? 2 : 1;
+        if (p->CG == 2 && p->BN == 128) p->BN = d->n_q > 0 ? 192 : 256;
         p->Rpad = (R + 7) / 8 * 8;
         p->Kseg = ((int64_t)3 * d->T0 + p->BK - 1) / p->BK * p->BK;
         // epilogue warps: two per scheduler (8) hide the latency of the binning epilogue
@@ -518,6 +525,7 @@ int asd_pair_corr_plan_create(const asd_corr_desc *d, asd_corr_plan **out)
         p->Rpad = 0;
         p->Kseg = ((int64_t)3 * d->T0 + 15) / 16 * 16;
         p->BN = 128;
+        p->CG = 1;
     }
     p->Kb = p->S * p->Kseg;
 
@@ -829,14 +837,14 @@ int asd_pair_corr_contract_range(asd_corr_plan *p, int64_t row_begin, int64_t ro
     ov.row_end = (int)row_end;
     ov.t_begin = t_begin;
     ov.n_t = t_end - t_begin;
-    ov.tiles_m = (int)((row_end - row_begin + kBM - 1) / kBM);
+    ov.tiles_m = (int)((row_end - row_begin + kBM * p->CG - 1) / (kBM * p->CG));
     ov.n_tiles = tc_work_items(ov.n_t, ov.tiles_m, p->h_prob->tiles_n);
     ov.C_sum = C_sum;
     ov.Sq_sum = Sq_sum;
     rc = launch_tc(p->d_prob, 1, ov.n_tiles, ov, p->prec, p->BN, p->swizzle_bytes, p->stages,
                    p->smem_bytes, tc_var_bytes(p->NW, p->n_bins, p->n_lut, p->EW), p->n_bins,
-                   p->n_q, p->EW, p->d.deterministic, p->sm_count,
-                   p->d.static_schedule ? nullptr : p->counter, s);
+                   p->n_q, p->EW, p->d.deterministic, p->CG, p->sm_count,
+                   p->d.static_schedule || p->CG == 2 ? nullptr : p->counter, s);
     return rc ? rc : fix_end(p, t_begin, t_end, C_sum, Sq_sum, s);
 }
 
@@ -855,6 +863,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
                       "batched plans must share precision and tile width");
         ASD_CHECK_ARG(p->d.deterministic == p0->d.deterministic,
                       "batched plans must share the deterministic mode");
+        ASD_CHECK_ARG(p->CG == 1, "batched launches use one CTA per tile (cta_pair = 0)");
         ASD_CHECK_ARG(p->device == p0->device, "plans on different devices");
         ASD_CHECK_ARG(p->n_bins == 0 || (C_sum && C_sum[k]), "C_sum required");
         ASD_CHECK_ARG(p->n_q == 0 || (Sq_sum && Sq_sum[k]), "Sq_sum required");
@@ -969,7 +978,7 @@ int asd_pair_corr_batched(asd_corr_plan *const *plans, const float *const *trajs
     for (int k = 0; k < n; ++k) dyn = dyn && !plans[k]->d.static_schedule;
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(dbuf + kMaxProblems);
     int rc = launch_tc(dbuf, n, total, ov, p0->prec, p0->BN, p0->swizzle_bytes, stages, smem, vb,
-                       max_nb, max_nq, p0->EW, p0->d.deterministic, p0->sm_count,
+                       max_nb, max_nq, p0->EW, p0->d.deterministic, 1, p0->sm_count,
                        dyn ? ctr : nullptr, s);
     for (int k = 0; k < n && !rc; ++k)
         rc = fix_end(plans[k], 0, plans[k]->n_t, C_sum ? C_sum[k] : nullptr,

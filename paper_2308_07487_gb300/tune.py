@@ -1,8 +1,9 @@
 """Autotuner of the tensor-core pair-correlation launch.
 
 The launch knobs of a plan -- tile width (`tile_n`), epilogue warps (`epi_warps`), raster
-group height (`raster_m`) and pipeline stages (`stages`) -- change speed, and results only
-through the rounding order of the FP32 per-tile bin sums and of the FP64 accumulation.
+group height (`raster_m`), pipeline stages (`stages`) and CTA pairs (`cta_pair`, single
+problems only) -- change speed, and results only through the rounding order of the FP32
+per-tile bin sums and of the FP64 accumulation.
 (`k_chunks` also changes the tensor core's accumulation error, so it stays at the plan's
 accuracy-driven default and is not tuned.)
 The tuner times each valid candidate on a sample of the workload (a few displacements)
@@ -23,14 +24,16 @@ DEFAULT_SPACE = {
     "epi_warps": [4, 8],
     "raster_m": [8, 16, 32, 64],
     "stages": [0, 3],
+    "cta_pair": [False, True],
 }
 
 
-def candidates(space=None, n_q=0, N=None):
+def candidates(space=None, n_q=0, N=None, batch=False):
     """Valid combinations of the knobs (the plan's instantiated kernels): 128-wide tiles
     run with 4 epilogue warps; with phase weights (n_q > 0) the phase product takes 128
     TMEM columns beside the two accumulators, so tiles are at most 192 wide; tiles wider
-    than the problem are skipped."""
+    than the problem are skipped; CTA pairs need 192- or 256-wide tiles and a single
+    problem (not a batch)."""
     sp = dict(DEFAULT_SPACE if space is None else space)
     out = []
     keys = sorted(sp)
@@ -42,6 +45,8 @@ def candidates(space=None, n_q=0, N=None):
         if n_q > 0 and tn == 256:
             continue
         if N is not None and tn and tn > 128 and N <= 128:
+            continue
+        if c.get("cta_pair") and (batch or tn == 128):
             continue
         out.append(c)
     return out
@@ -152,5 +157,5 @@ class Tuner:
             finally:
                 for p in plans:
                     p.close()
-        return self.select(key, candidates(space, 0, min(l.n_sites for l, _, _ in problems)),
-                           run)
+        return self.select(key, candidates(space, 0, min(l.n_sites for l, _, _ in problems),
+                                           batch=True), run)

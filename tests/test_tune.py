@@ -14,6 +14,10 @@ def test_candidates_respect_the_instantiated_kernels():
     assert cq and {c["tile_n"] for c in cq} == {128, 192}
     assert {c["epi_warps"] for c in cq if c["tile_n"] == 192} == {4, 8}
     assert all(c["tile_n"] == 128 for c in tune.candidates(N=100))
+    # CTA pairs: 192- or 256-wide tiles, never for a batch
+    assert any(c.get("cta_pair") for c in cs)
+    assert all(c["tile_n"] != 128 for c in cs if c.get("cta_pair"))
+    assert not any(c.get("cta_pair") for c in tune.candidates(batch=True))
     # every combination appears once
     assert len({json.dumps(c, sort_keys=True) for c in cs}) == len(cs)
 
