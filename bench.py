@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--ncu", action="store_true", help="one step, nothing else (for ncu)")
     ap.add_argument("--mlp-depth", type=int, default=2, choices=[2, 3],
                     help="learned workload: hidden layers of the proposal network")
+    ap.add_argument("--cta-pair", action="store_true",
+                    help="CTA pairs (cta_group::2) for the timed contraction (tensor forms)")
     ap.add_argument("--nt-per-step", type=int, default=0,
                     help="displacements per step (0: the workload's default)")
     ap.add_argument("--workload", default="glass64",
@@ -304,7 +306,8 @@ def run_ours(args, W, ws, rank, local):
     sysm.thermalize(spins0, W["T"], W["sweeps"], asd.ASD_METROPOLIS, cone=0.0, adapt=True,
                     seed=23083 + rank)
     traj = torch.empty((N, 1, F, 3), dtype=torch.float32, device=dev)
-    plan = asd.CorrPlan.for_lattice(lat, F, T0, n_t, W["w"], nb, precision=args.form, q=q)
+    plan = asd.CorrPlan.for_lattice(lat, F, T0, n_t, W["w"], nb, precision=args.form, q=q,
+                                    cta_pair=args.cta_pair and args.form != "fp32")
     C_sum = torch.zeros((n_t, nb), dtype=torch.float64, device=dev)
     C = torch.zeros_like(C_sum)
     Sq_sum = torch.zeros((n_t, nq), dtype=torch.float64, device=dev) if nq else None
@@ -402,6 +405,7 @@ def run_ours(args, W, ws, rank, local):
            "config": {"workload": W["name"], "N": N, "F": F, "T0": T0, "n_t": n_t,
                       "n_t_per_step": nt_step, "n_bins": nb, "bin_width": W["w"], "n_q": nq,
                       "K": K, "form": args.form, "parallelism": f"replicas x{ws}",
+                      "cta_pair": bool(args.cta_pair and args.form != "fp32"),
                       "l2": "inputs larger than L2 (operand copies "
                             f"{plan.workspace_bytes() / 1e9:.1f} GB, trajectory "
                             f"{traj.numel() * 4 / 1e9:.2f} GB)"},
