@@ -2,7 +2,7 @@
 memory checker.  In a child process that loads it (ASD_CHECKED=1), every kernel path of
 the contraction runs on small cases -- lattice table and threshold paths, the branch-free
 position path, the private window with fallback bins, the tensor-core phase product with
-its sine part, K-chunks, the FP32 form, a batched launch -- with no index check failing
+its sine part, K-chunks, the FP32 form, CTA pairs, a batched launch -- with no index check failing
 (asd_sync_status == ASD_OK) and results at the parity bar of the oracle; the self-test
 makes one check fail on purpose (no memory is touched) and must read back ASD_EBOUNDS.
 In the normal build the self-test is refused.
@@ -67,6 +67,9 @@ case("window_fallback", synth.hypercubic(8, 3, False, jitter=0.1, seed=4, block=
 case("fp32_phase", glass, 32, 3, 0.5, 36, "fp32", q=synth.q_vectors_glass()[::9], sine=True)
 case("deterministic", glass, 32, 3, 0.5, 36, "split_bf16", q=synth.q_vectors_glass()[::9],
      deterministic=True)
+case("pair_phase", glass, 32, 3, 0.5, 36, "split_bf16", q=synth.q_vectors_glass()[::9],
+     rows=(40, 1700), cta_pair=True)
+case("pair_lattice", synth.hypercubic(17, 3, True), 20, 3, 0.5, 30, "split_bf16", cta_pair=True)
 lats = [synth.hypercubic(L, 2, True) for L in (30, 17)]
 plans = [asd.CorrPlan.for_lattice(l, 14, 12, 3, 1.0, 10, tile_n=256) for l in lats]
 trs = [torch.from_numpy(synth.traj_precess(l.n_sites, 14, seed=3)).cuda()
