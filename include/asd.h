@@ -101,8 +101,10 @@ typedef struct asd_corr_desc {
     int32_t k_chunks;       /* 0 = automatic (split-BF16: one per <= 1024 K elements;
                                other forms: 1), else partial accumulators per tile along K
                                (1..256): each starts from zero, which bounds the
-                               tensor-core FP32 accumulation error; the epilogue bins each
-                               one (FP32 within a tile, FP64 across tiles)               */
+                               tensor-core FP32 accumulation error; the chunks of a tile
+                               run back to back on one CTA and the epilogue adds each into
+                               the tile's private bins (FP32 within a tile, FP64 across
+                               tiles)                                                     */
     int32_t epi_warps;      /* 0 = automatic (8 for positions with 192- or 256-wide
                                tiles, else 4), 4 or 8 epilogue warps per CTA (8 needs
                                tile_n 192 or 256)                                         */

@@ -22,13 +22,14 @@
 // plan, so no transcendental is evaluated per pair (the register-spill problem of the
 // paper's OTF_REG variant).
 //
-// Persistent: one CTA per SM takes (problem, t, K chunk, row tile, column tile) work
-// items in grouped raster order (raster_m row tiles per group, 16 by default) so
-// concurrently running CTAs share A and B panels in L2; the TMA thread claims each item
-// from a global counter (or, static, takes every n-th) and passes its index to the other
-// roles.  Several problems (a batched ensemble) share the list.  Every wait is bounded: after
-// kTimeoutNs a role records an error in the device error word and stops; the CTA then
-// drains its own in-flight copies and MMAs, frees TMEM and exits.
+// Persistent: one CTA per SM (or one CTA pair per two SMs) takes (problem, t, row tile,
+// column tile) work items in grouped raster order (raster_m row tiles per group, 16 by
+// default) so concurrently running CTAs share A and B panels in L2; the TMA thread claims
+// each item from a global counter (or, static, takes every n-th) and passes its K chunks,
+// one sub-item each, to the other roles.  Several problems (a batched ensemble) share the
+// list.  Every wait is bounded: after kTimeoutNs a role records an error in the device
+// error word and stops; the CTA then drains its own in-flight copies and MMAs, frees TMEM
+// and exits.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -471,8 +472,8 @@ struct TileInfo {
     int kg0, kg1;  // K blocks [kg0, kg1) of the S * nkb blocks of a full row
 };
 
-// Work item `tau` -> (problem, t, K chunk, row tile, column tile).  K chunks split the
-// contraction so that each partial accumulator starts from zero.
+// Work item `tau` -> (problem, t, row tile, column tile), sub-item c -> its K chunk c.  K
+// chunks split the contraction so that each partial accumulator starts from zero.
 // Per-role walk over the work list.  A role visits its work items in increasing order,
 // so the problem of the next item is found by stepping forward from the current one, and
 // the fields that decoding needs stay in registers until the problem changes (a batched
@@ -750,8 +751,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     constexpr int kKSteps = SWB / 32;          // one MMA k-step covers 32 bytes of K
     constexpr int kBK = SWB / (kTF32 ? 4 : 2); // K elements per stage
     constexpr uint32_t kIdesc = idesc(kTF32, BN, kBM * CG);
-    // Phase weights on the tensor core (problems with n_q > 0; the plan picks BN <= 192 and
-    // 4 epilogue warps): after the epilogue has binned a tile it stores the tile's G, split
+    // Phase weights on the tensor core (problems with n_q > 0; the plan picks BN <= 192):
+    // after the epilogue has binned a K chunk of a tile it stores the chunk's G, split
     // into BF16 hi + lo, back over the accumulator's own columns (chunk of 32 columns ->
     // 16 columns of hi, then 16 of lo), and one pass of kPhaseQ q-vectors is the
     // 128 x 128 x BN product P = G W with W[c][o] = cos / sin(q_o . r_c) of the tile's
