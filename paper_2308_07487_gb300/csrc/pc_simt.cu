@@ -3,7 +3,9 @@
 // It is the accuracy and speed baseline of the tensor-core forms.  Each CTA owns a
 // 128 x 128 tile of G_t = A_t B^T for one displacement t (the paper's thread-block
 // tile, Section 3.3), accumulates it in registers (8 x 8 per thread), and reduces the
-// tile in place: distance bins through FP64 shared-memory atomics, phase weights
+// tile in place: distance bins through FP32 shared-memory atomics into one copy of the
+// bins per warp (summed across the warps in FP64 at the end of the tile; FP64 shared
+// atomics where the copies do not fit), phase weights
 // through cos(a-b) = cos a cos b + sin a sin b with warp shuffles (Section 3.3, the
 // shuffle + shared-memory + atomic reduction), then one FP64 global atomic per bin
 // (and per q) per tile.  In the deterministic mode the same sums are 64-bit fixed point
@@ -28,6 +30,7 @@ struct SimtParams {
     int N;
     int row_begin, row_end;
     int t_begin;      // displacement of grid slice blockIdx.z = 0
+    int warp_bins;    // per-warp FP32 bin copies after the FP64 arrays
     EpiParams e;
     int *err;         // device error word (index checks of a checked build)
 };
@@ -37,9 +40,10 @@ __global__ void __launch_bounds__(256, 2) simt_kernel(SimtParams P)
 {
     __shared__ __align__(16) float As[2][TK][TM];
     __shared__ __align__(16) float Bs[2][TK][TN];
-    extern __shared__ double red[];  // [n_bins] then [n_q][q_parts]
+    extern __shared__ double red[];  // [n_bins] then [n_q][q_parts], then [8][n_bins] FP32
     double *sbins = red;
     double *sq = red + P.e.n_bins;
+    float *wbins = reinterpret_cast<float *>(sq + P.e.n_q * P.e.q_parts);
     // deterministic mode: the same arrays as fixed point
     long long *sbins_i = reinterpret_cast<long long *>(sbins);
     long long *sq_i = reinterpret_cast<long long *>(sq);
@@ -51,6 +55,9 @@ __global__ void __launch_bounds__(256, 2) simt_kernel(SimtParams P)
     const int m0 = P.row_begin + blockIdx.x * TM;
     const int n0 = blockIdx.y * TN;
     for (int k = tid; k < P.e.n_bins + P.e.n_q * P.e.q_parts; k += 256) red[k] = 0.0;
+    const bool wb_on = P.warp_bins && fscale == 0.0;
+    if (wb_on)
+        for (int k = tid; k < 8 * P.e.n_bins; k += 256) wbins[k] = 0.f;
 
     // loader mapping: one row (or column) and 4 consecutive k per thread
     const int lr = tid >> 1, lk = (tid & 1) * 4;
@@ -121,6 +128,7 @@ __global__ void __launch_bounds__(256, 2) simt_kernel(SimtParams P)
         cj[u] = n0 + (u < 4 ? tx * 4 + u : 64 + tx * 4 + u - 4);
     }
     const EpiParams &e = P.e;
+    float *myb = wbins + (tid >> 5) * e.n_bins;
     if (e.n_bins > 0) {
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
@@ -138,6 +146,7 @@ __global__ void __launch_bounds__(256, 2) simt_kernel(SimtParams P)
                 const int b = bin_of_d2(d2, e.inv_w, e.n_bins, e.thr);
                 if (ok && b < e.n_bins && ASD_INB(b >= 0, BND_SIMT_BIN, P.err)) {
                     if (fscale != 0.0) add_fixed(&sbins_i[b], to_fixed((double)acc[r][c], fscale));
+                    else if (wb_on) atomicAdd(&myb[b], acc[r][c]);
                     else atomicAdd(&sbins[b], (double)acc[r][c]);
                 }
             }
@@ -189,8 +198,13 @@ __global__ void __launch_bounds__(256, 2) simt_kernel(SimtParams P)
             if (sq_i[o] != 0) add_fixed(&e.Sq_fix[(int64_t)t * e.n_q * e.q_parts + o], sq_i[o]);
         return;
     }
-    for (int b = tid; b < e.n_bins; b += 256)
-        if (sbins[b] != 0.0) atomicAdd(&e.C_sum[(int64_t)t * e.n_bins + b], sbins[b]);
+    for (int b = tid; b < e.n_bins; b += 256) {
+        double v = sbins[b];
+        if (wb_on)
+#pragma unroll
+            for (int w = 0; w < 8; ++w) v += (double)wbins[w * e.n_bins + b];
+        if (v != 0.0) atomicAdd(&e.C_sum[(int64_t)t * e.n_bins + b], v);
+    }
     for (int o = tid; o < e.n_q * e.q_parts; o += 256)
         if (sq[o] != 0.0) atomicAdd(&e.Sq_sum[(int64_t)t * e.n_q * e.q_parts + o], sq[o]);
 }
@@ -241,6 +255,9 @@ int launch_simt(asd_corr_plan *p, const float *traj, int64_t row_begin, int64_t 
         return ASD_EUNSUPPORTED;
     }
     size_t smem = sizeof(double) * (p->n_bins + p->n_q * p->q_parts);
+    // per-warp FP32 bin copies where they fit the default 48 KB of dynamic shared memory
+    P.warp_bins = !p->d.deterministic && smem + sizeof(float) * 8 * p->n_bins <= 48 * 1024;
+    if (P.warp_bins) smem += sizeof(float) * 8 * p->n_bins;
     simt_kernel<<<grid, 256, smem, s>>>(P);
     ASD_CUDA_TRY(cudaGetLastError());
     return ASD_OK;
