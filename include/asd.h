@@ -113,7 +113,8 @@ typedef struct asd_corr_desc {
                                part sum_ij sin(q.(r_i - r_j)) G_ij(t) (Eq. 3's imaginary
                                part is its negative)                                     */
     int32_t static_schedule;/* 0: work items claimed from a global counter (dynamic,
-                               the default); 1: static round-robin order                 */
+                               the default); 1: static order (round k of n CTAs: CTA c
+                               takes item k n + (c + k) mod n)                            */
     int32_t deterministic;  /* 0: sums across threads and tiles by FP32 / FP64 atomics
                                (the last bits depend on the schedule); 1: every such sum
                                in 64-bit fixed point (integer adds, any order gives the

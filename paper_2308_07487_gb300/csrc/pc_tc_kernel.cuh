@@ -884,14 +884,19 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
             // work items from the counter (dynamic schedule) or in a fixed order; both CTAs
             // of a pair walk the same fixed order (measured against handing each item from
             // the first CTA to the second: 542 against 506 TFLOP/s on the 26^3 lattice).
+            // The fixed order: in round k of n CTAs (pairs), CTA c takes item
+            // k n + (c + k) mod n.  Without the rotation a raster group of a multiple of n
+            // items would put every CTA on the same columns in every group, so the costly
+            // column tiles would always land on the same CTAs.
             int64_t tau = 0;
             int kci = 0, kch = 0;
             for (int64_t v = 0; ok; ++v) {
                 const int qs = (int)(v % kWQ);
                 // the next chunk of the current item, or the first of a new one
                 if (++kci >= kch) {
-                    tau = args.counter && CG == 1 ? (int64_t)atomicAdd(args.counter, 1ull)
-                                                  : cid + n_claimed * n_ctas;
+                    tau = args.counter && CG == 1
+                              ? (int64_t)atomicAdd(args.counter, 1ull)
+                              : n_claimed * n_ctas + (cid + n_claimed) % n_ctas;
                     ++n_claimed;
                     if (tau >= args.total_tiles) tau = -1;
                     kci = 0;
