@@ -461,7 +461,8 @@ __host__ __device__ inline EpiLayout epi_layout(uint32_t vb, int nb, int nq, int
     L.fb = take(o, (det ? 8u : 4u) * (nb > 0 ? nb : 1));
     L.colgeo = take(o, 16u * BN);
     L.colpk = take(o, 4u * BN);
-    L.boxred = take(o, 4u * ew * 12);
+    // per-warp row / column boxes, then the boxes of the tile's 32-column chunks (up to 8)
+    L.boxred = take(o, 4u * (ew * 12 + 8 * 6));
     L.var = take(o, vb);
     L.total = (o + 1023u) & ~1023u;
     return L;
@@ -743,6 +744,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     constexpr int kEpiThreads = 32 * EW;
     constexpr int kBinStride = bin_stride(EW);
     constexpr int kHalves = EW / 4;
+    constexpr int kChunks = BN / 32;                                 // 32-column chunks
+    constexpr int kColM = (BN + kEpiThreads - 1) / kEpiThreads;      // columns per thread
+    static_assert(kChunks <= 8 && kChunks <= 32, "chunk boxes of a tile");
     constexpr bool kTF32 = FORM == ASD_TF32;
     constexpr int kPlanes = FORM == ASD_SPLIT_BF16 ? 2 : 1;
     constexpr uint32_t kABytes = kBM * SWB;
@@ -1171,6 +1175,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         float4 *colgeo = reinterpret_cast<float4 *>(epi + EL.colgeo);
         uint32_t *colpk = reinterpret_cast<uint32_t *>(epi + EL.colpk);
         float *boxred = reinterpret_cast<float *>(epi + EL.boxred);
+        float *chbox = boxred + kEpiWarps * 12;
         float *thr_s = bins;
         for (int k = et; k < args.NB; k += kEpiThreads) {
             if (args.det) fbi[k] = 0;
@@ -1214,6 +1219,10 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
         float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
         int blo = 0, bhi_tile = 0;
         bool pos_fit = false;
+        // positions: a tile whose columns span two far-apart groups of sites may take two
+        // windows, private rows [0, n1) for bins blo + k (column chunks before `split`) and
+        // rows [n1, nwp) for bins blo2 + k - n1 (the chunks from `split` on)
+        int blo2 = 0, n1 = 0, split = 0, nwp = 0;
         // per-CTA FP64 sums of the current (problem, t), added to the outputs when it changes
         // (deterministic mode: fixed-point sums into the problem's fixed-point arrays)
         auto flush_acc = [&](int p, int t) {
@@ -1307,7 +1316,19 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 // column geometry of the tile (one load per column, which also feeds the
                 // column bounding box when the bins do not all fit the window)
                 float cl[3] = {3e38f, 3e38f, 3e38f}, ch[3] = {-3e38f, -3e38f, -3e38f};
-                for (int c = et; c < BN; c += kEpiThreads) {
+                // (and the box of each 32-column chunk this warp loads: chunk ew + m EW)
+                float cm[kColM][6];
+#pragma unroll
+                for (int m = 0; m < kColM; ++m)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        cm[m][a] = 3e38f;
+                        cm[m][3 + a] = -3e38f;
+                    }
+#pragma unroll
+                for (int m = 0; m < kColM; ++m) {
+                    const int c = et + m * kEpiThreads;
+                    if (c >= BN) break;
                     const int j = min(ti.n0 + c, P.N - 1);
                     float4 pj;
                     if (lattice) {
@@ -1323,6 +1344,8 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     cl[0] = fminf(cl[0], pj.x); ch[0] = fmaxf(ch[0], pj.x);
                     cl[1] = fminf(cl[1], pj.y); ch[1] = fmaxf(ch[1], pj.y);
                     cl[2] = fminf(cl[2], pj.z); ch[2] = fmaxf(ch[2], pj.z);
+                    cm[m][0] = pj.x; cm[m][1] = pj.y; cm[m][2] = pj.z;
+                    cm[m][3] = pj.x; cm[m][4] = pj.y; cm[m][5] = pj.z;
                 }
                 ri = E.coords[ic];
                 rp = lattice ? make_float4((float)ri.x, (float)ri.y, (float)ri.z, 0.f) : E.pos[ic];
@@ -1349,6 +1372,22 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         }
                     if (lane == 0)
                         for (int k = 0; k < 12; ++k) boxred[ew * 12 + k] = v6[k];
+                    if (!lattice) {
+#pragma unroll
+                        for (int m = 0; m < kColM; ++m) {
+                            const int chk = ew + m * kEpiWarps;  // warp-uniform
+                            if (chk >= kChunks) break;
+                            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) {
+                                    const float w = __shfl_xor_sync(0xffffffffu, cm[m][k], o);
+                                    cm[m][k] = k < 3 ? fminf(cm[m][k], w) : fmaxf(cm[m][k], w);
+                                }
+                            if (lane == 0)
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) chbox[chk * 6 + k] = cm[m][k];
+                        }
+                    }
                 }
                 epi_sync(kEpiThreads);  // colgeo / boxred ready; previous tile fully flushed
                 if (ti.p != cur_p || ti.t != cur_t) {
@@ -1357,6 +1396,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     cur_t = ti.t;
                 }
                 blo = 0;
+                n1 = E.NW;
+                split = kChunks;
+                nwp = E.n_bins;
                 // positions: whether every kept bin of the tile lies inside the private window
                 // [blo, blo + NW), from the largest distance between the two bounding boxes
                 pos_fit = !E.use_window;
@@ -1392,6 +1434,85 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                                        bin_of_d2_pair(d2max * 1.001f + 1e-30f, E.inv_w, E.n_bins,
                                                       thr2, args.err) + 1);
                         pos_fit = bhi_tile - blo < E.NW;
+                        nwp = bhi_tile - blo + 1;
+                        if (!pos_fit) {
+                            // bins of each 32-column chunk (lane c computes chunk c), then the
+                            // best split of the chunks into two windows that together fit
+                            int lo_c = 1 << 30, hi_c = -1;
+                            if (lane < kChunks) {
+                                float dmin = 0.f, dmax = 0.f;
+                                for (int a = 0; a < 3; ++a) {
+                                    float rl = 3e38f, rh = -3e38f;
+                                    for (int w = 0; w < kEpiWarps; ++w) {
+                                        rl = fminf(rl, boxred[w * 12 + a]);
+                                        rh = fmaxf(rh, boxred[w * 12 + 3 + a]);
+                                    }
+                                    const float cl = chbox[lane * 6 + a], ch = chbox[lane * 6 + 3 + a];
+                                    const float gap = fmaxf(0.f, fmaxf(cl - rh, rl - ch));
+                                    const float far = fmaxf(ch - rl, rh - cl);
+                                    dmin += gap * gap;
+                                    dmax += far * far;
+                                }
+                                lo_c = max(0, bin_of_d2_pair(dmin * 0.999f, E.inv_w, E.n_bins, thr2,
+                                                             args.err) - 1);
+                                hi_c = min(E.n_bins - 1,
+                                           bin_of_d2_pair(dmax * 1.001f + 1e-30f, E.inv_w,
+                                                          E.n_bins, thr2, args.err) + 1);
+                            }
+                            int lo[kChunks], hi[kChunks];
+#pragma unroll
+                            for (int c = 0; c < kChunks; ++c) {
+                                lo[c] = __shfl_sync(0xffffffffu, lo_c, c);
+                                hi[c] = __shfl_sync(0xffffffffu, hi_c, c);
+                            }
+                            // one window over the chunks' bins (narrower than the tile's
+                            // box); only when that does not fit, two windows, which are then
+                            // disjoint (two overlapping ones would span no more than their
+                            // sum), so no bin has two private rows
+                            int l0 = 1 << 30, h0 = -1;
+#pragma unroll
+                            for (int c = 0; c < kChunks; ++c) {
+                                l0 = min(l0, lo[c]);
+                                h0 = max(h0, hi[c]);
+                            }
+                            int best = E.NW + 1;
+                            if (h0 - l0 + 1 <= E.NW) {
+                                best = h0 - l0 + 1;
+                                blo = l0;
+                                n1 = E.NW;
+                                split = kChunks;
+                            }
+#pragma unroll
+                            for (int sp = 1; sp < kChunks && best > E.NW; ++sp) {
+                                int l1 = 1 << 30, h1 = -1, l2 = 1 << 30, h2 = -1;
+#pragma unroll
+                                for (int c = 0; c < kChunks; ++c) {
+                                    if (c < sp) { l1 = min(l1, lo[c]); h1 = max(h1, hi[c]); }
+                                    else { l2 = min(l2, lo[c]); h2 = max(h2, hi[c]); }
+                                }
+                                const int need = (h1 - l1 + 1) + (h2 - l2 + 1);
+                                if (need < best) {
+                                    best = need;
+                                    blo = l1;
+                                    n1 = h1 - l1 + 1;
+                                    blo2 = l2;
+                                    split = sp;
+                                }
+                            }
+                            if (best <= E.NW) {
+                                pos_fit = true;
+                                nwp = best;
+                            } else {
+                                blo = max(0, (tab ? bin_of_d2(d2min * 0.999f, E.inv_w, E.n_bins, E.thr)
+                                                  : bin_of_d2_pair(d2min * 0.999f, E.inv_w, E.n_bins,
+                                                                   thr2, args.err)) - 1);
+                                n1 = E.NW;
+                                split = kChunks;
+                            }
+                        } else {
+                            n1 = E.NW;
+                            split = kChunks;
+                        }
                     }
                 }
             }  // first chunk
@@ -1453,8 +1574,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     float *mb = bins + r + kBM * half;
                     const uint32_t trash_off = (uint32_t)E.NW * kBinStride;
                     const float2 *thr2 = reinterpret_cast<const float2 *>(thr_s);
-                    const int b0 = E.use_window ? blo : 0;
                     for (int ch = ch0; ch < ch1; ++ch) {
+                        // (private row of bin b: b - blo, or b - blo2 + n1 in a second window)
+                        const int b0 = !E.use_window ? 0 : ch < split ? blo : blo2 - n1;
                         uint32_t g[32], off[32];
                         tmem_ld32_issue(tbase + ch * 32, g);
                         if (E.thr_exact)
@@ -1513,7 +1635,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                 // private rows this tile may have written: with the branch-free position
                 // path only the tile's own bin range, else the whole window / bin set
                 const int NWp = !E.use_window ? E.n_bins
-                                : (!lattice && pos_fit ? min(E.NW, bhi_tile - blo + 1) : E.NW);
+                                : (!lattice && pos_fit ? min(E.NW, nwp) : E.NW);
                 // epilogue warp ew reduces bins b = 4 ew + u (mod 4 EW), four at a time (the
                 // four shuffle trees overlap): conflict-free loads, an FP32 tree over the
                 // stride, one FP64 add per bin (the FP64 pipe is narrow on this part, so
@@ -1539,8 +1661,9 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                     if (lane == 0)
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
-                            const int b = blo + b0 + u;
-                            if (b0 + u < NWp && b < E.n_bins &&
+                            const int k = b0 + u;
+                            const int b = k < n1 ? blo + k : blo2 + (k - n1);
+                            if (k < NWp && b < E.n_bins &&
                                 ASD_INB(b < args.NB, BND_CACC, args.err)) {
                                 if (fscale != 0.0) cacci[b] += to_fixed((double)v4[u], fscale);
                                 else cacc[b] += (double)v4[u];

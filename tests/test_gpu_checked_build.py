@@ -2,8 +2,8 @@
 memory checker.  In a child process that loads it (ASD_CHECKED=1), every kernel path of
 the contraction runs on small cases -- lattice table and threshold paths, the branch-free
 position path, the private window with fallback bins, the tensor-core phase product with
-its sine part, K-chunks, the FP32 form, CTA pairs, a batched launch -- with no index check failing
-(asd_sync_status == ASD_OK) and results at the parity bar of the oracle; the self-test
+its sine part, K-chunks, the FP32 form, CTA pairs, tiles binned through two windows, a
+batched launch -- with no index check failing (asd_sync_status == ASD_OK) and results at the parity bar of the oracle; the self-test
 makes one check fail on purpose (no memory is touched) and must read back ASD_EBOUNDS.
 In the normal build the self-test is refused.
 """
@@ -70,6 +70,9 @@ case("deterministic", glass, 32, 3, 0.5, 36, "split_bf16", q=synth.q_vectors_gla
 case("pair_phase", glass, 32, 3, 0.5, 36, "split_bf16", q=synth.q_vectors_glass()[::9],
      rows=(40, 1700), cta_pair=True)
 case("pair_lattice", synth.hypercubic(17, 3, True), 20, 3, 0.5, 30, "split_bf16", cta_pair=True)
+glass32 = synth.hypercubic(32, 3, False, pm_j=True, p=0.5, seed=7, block=(4, 4, 8), jitter=0.1)
+case("positions_two_windows", glass32, 32, 2, 0.5, 256, "split_bf16",
+     q=synth.q_vectors_glass()[::8], rows=(0, 256))
 lats = [synth.hypercubic(L, 2, True) for L in (30, 17)]
 plans = [asd.CorrPlan.for_lattice(l, 14, 12, 3, 1.0, 10, tile_n=256) for l in lats]
 trs = [torch.from_numpy(synth.traj_precess(l.n_sites, 14, seed=3)).cuda()

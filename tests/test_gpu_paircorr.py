@@ -111,6 +111,23 @@ def test_positions_with_phase(asd, form):
     assert_parity(got, ref, form, q=True)
 
 
+@pytest.mark.parametrize("form", ["split_bf16", "bf16"])
+def test_positions_two_windows(asd, form):
+    """32^3 jittered glass in 4 x 4 x 8 site blocks, 256 bins of 0.5, of which the private
+    window holds 81 (8 epilogue warps).  A 192-column tile that joins the last sites of one
+    row of blocks with the first sites of the next spans more bins than that, and is
+    binned through two windows, one per group of its 32-column chunks; each of the first
+    two row tiles meets one such tile.  Bins and 16 q-vectors against the oracle."""
+    lat = synth.hypercubic(32, 3, False, pm_j=True, p=0.5, seed=7, block=(4, 4, 8),
+                           jitter=0.1)
+    q = synth.q_vectors_glass()[::4]
+    tr = synth.traj_precess(lat.n_sites, 34, seed=9)
+    rows = (0, 256)
+    got = run_gpu(asd, lat, tr, 32, 2, 0.5, 256, form, q=q, rows=rows)
+    ref = oracle_ref(lat, tr, 32, 2, 0.5, 256, q=q, rows=rows)
+    assert_parity(got, ref, form, q=True)
+
+
 @pytest.mark.parametrize("form", ["split_bf16", "fp32"])
 def test_row_range(asd, form):
     lat = synth.hypercubic(20, 2, True)
