@@ -53,7 +53,7 @@ constexpr uint32_t kWBytes = 128u * 128u;     // one plane of a W stage: 128 row
 // through a ring of kWQ slots in shared memory.  With the dynamic schedule the TMA thread
 // claims each item from a global counter, so the items in flight across the grid stay
 // together whatever each item costs (L2 reuse of A / B panels, no drift, balanced tail);
-// the static schedule takes items cid, cid + gridDim.x, ...
+// the static schedule takes, in round k of n CTAs, item k n + (cid + k) mod n.
 constexpr int kWQ = 4;
 // Private bins are a [bin][128 * EW/4] array: epilogue thread (row r, column half h)
 // only ever touches column r + 128 h, i.e. bank r mod 32, so the per-pair accumulation
