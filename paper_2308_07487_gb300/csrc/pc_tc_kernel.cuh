@@ -746,7 +746,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
     constexpr int kHalves = EW / 4;
     constexpr int kChunks = BN / 32;                                 // 32-column chunks
     constexpr int kColM = (BN + kEpiThreads - 1) / kEpiThreads;      // columns per thread
-    static_assert(kChunks <= 8 && kChunks <= 32, "chunk boxes of a tile");
+    static_assert(kChunks <= 8, "chunk boxes of a tile (and one lane per chunk)");
     constexpr bool kTF32 = FORM == ASD_TF32;
     constexpr int kPlanes = FORM == ASD_SPLIT_BF16 ? 2 : 1;
     constexpr uint32_t kABytes = kBM * SWB;
@@ -1437,7 +1437,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1) pc_tc_kernel(const __grid_con
                         nwp = bhi_tile - blo + 1;
                         if (!pos_fit) {
                             // bins of each 32-column chunk (lane c computes chunk c), then the
-                            // best split of the chunks into two windows that together fit
+                            // first split of the chunks into two windows that together fit
                             int lo_c = 1 << 30, hi_c = -1;
                             if (lane < kChunks) {
                                 float dmin = 0.f, dmax = 0.f;
